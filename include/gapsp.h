@@ -1,0 +1,162 @@
+/*
+ * gapsp: all pairs of geodesic distances on a grey image, on one GB300 GPU.
+ *
+ * The operation is the one of Noyel, Angulo & Jeulin, "Fast computation of
+ * all pairs of geodesic distances":
+ *   - pixels are the vertices of a graph whose edges join 4- or 8-neighbours
+ *     (Sec. 2, eqs. "voisinage 1/2");
+ *   - an edge between neighbours p and q costs w(p,q) = f(p) + f(q) + 1, the
+ *     sum-of-grey-levels pseudo-metric of Sec. 2 (eq. "distance somme") plus
+ *     one so that every edge costs at least 1. Diagonal steps cost the same
+ *     as axial ones (a 3x3 neighbourhood, no Euclidean correction, Sec. 3);
+ *   - the distance d(p,q) is the minimum over paths of the summed edge costs
+ *     (Sec. 2, eqs. "temps" and "distance");
+ *   - the N x N array D is filled by geodesic propagations from chosen source
+ *     points plus Property 1 (Sec. 2): along the geodesic tree of a
+ *     propagation from s, d(a,b) = d(s,b) - d(s,a) for every ancestor a of b;
+ *   - sources are chosen in naive (raster) order, spiral order (Sec. 3.1,
+ *     Algorithm "spiral method") or by minimum filling rate with ties to the
+ *     greatest geodesic extremum (Sec. 3.4, Algorithm "method based on the
+ *     filling rate", with the extrema pre-pass of Sec. 3.3).
+ *
+ * An obstacle-mask variant is included: w = 2 between free pixels, obstacle
+ * pixels have no edges, and pairs that no path joins hold GAPSP_UNREACH.
+ *
+ * Data layout. Images are H x W, row-major, pixel p = r*W + c, N = H*W.
+ * D is row-major uint32 N x N: D[p*N + q] = d(p,q). D[p][p] = 0, D is
+ * symmetric, unreachable pairs hold GAPSP_UNREACH. D does not depend on the
+ * order or on B: only the counts in gapsp_stats do.
+ *
+ * Errors. Every call returns a status and never aborts, traps or hangs:
+ * device loops carry iteration limits and report GAPSP_E_NOT_CONVERGED /
+ * GAPSP_E_TIMEOUT through a status word instead.
+ *
+ * Threading. A handle is used by one host thread at a time. Calls are
+ * ordered on opts.stream (NULL = the legacy default stream) and return when
+ * their results are complete.
+ */
+#ifndef GAPSP_H
+#define GAPSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GAPSP_UNREACH 0xFFFFFFFFu
+
+/* Largest supported image side, and largest N = H*W. */
+#define GAPSP_MAX_SIDE 256
+#define GAPSP_MAX_N 65536
+
+typedef struct gapsp_handle gapsp_handle; /* opaque */
+
+typedef enum {
+    GAPSP_OK = 0,
+    GAPSP_E_INVALID = 1,        /* bad argument: sizes, pointers, sources, order */
+    GAPSP_E_NOMEM = 2,          /* a device or host allocation failed */
+    GAPSP_E_BUDGET = 3,         /* the call's footprint exceeds opts.mem_budget */
+    GAPSP_E_CUDA = 4,           /* a CUDA runtime call failed */
+    GAPSP_E_NOT_CONVERGED = 5,  /* a propagation hit its sweep limit */
+    GAPSP_E_TIMEOUT = 6,        /* a round loop hit its round limit */
+    GAPSP_E_CANCELLED = 7       /* reserved for cancellable calls */
+} gapsp_status;
+
+typedef enum {
+    GAPSP_NAIVE = 0,   /* raster order, filled points skipped (Sec. 1 with the tree) */
+    GAPSP_SPIRAL = 1,  /* Sec. 3.1, Algorithm "spiral method" */
+    GAPSP_MINFILL = 2  /* Sec. 3.4, Algorithm "method based on the filling rate" */
+} gapsp_order;
+
+typedef enum {
+    GAPSP_GREY = 0, /* w(p,q) = f(p) + f(q) + 1 */
+    GAPSP_MASK = 1  /* w = 2 between free pixels; obstacles have no edges */
+} gapsp_kind;
+
+typedef struct {
+    int conn;          /* 4 or 8 (0 = 8) */
+    gapsp_kind kind;   /* GAPSP_GREY or GAPSP_MASK */
+    int B;             /* sources per round, 1..1024 (0 = 32) */
+    uint64_t seed;     /* seed of the spiral order's draws */
+    size_t mem_budget; /* bytes of device memory a call may use (0 = no limit) */
+    int tile_h, tile_w;/* reserved (0) */
+    int checked;       /* reserved (0) */
+    void *stream;      /* cudaStream_t the calls run on (NULL = default stream) */
+} gapsp_opts;
+
+typedef struct {
+    uint64_t propagations;         /* sources propagated by the round loop */
+    uint64_t prepass_propagations; /* +2 for the extrema pre-pass (Sec. 3.3-3.4) */
+    uint64_t distance_ops;         /* sum over propagations of the depth of every reached vertex */
+    uint64_t new_pairs;            /* pairs filled by the tree fills */
+    uint64_t rounds;               /* rounds of the loop */
+    uint64_t prefilled_pairs;      /* pairs no path joins (mask variant), filled at init */
+    double ms_total;               /* device time of the call */
+    uint64_t *round_new;           /* optional, caller-owned host array: new pairs per
+                                      round (capacity round_new_cap), or NULL */
+    uint64_t round_new_cap;
+    int32_t *sources;              /* optional, caller-owned host array receiving the
+                                      sources in selection order (capacity sources_cap) */
+    uint64_t sources_cap;
+} gapsp_stats;
+
+/* Fills *opts with the defaults (conn 8, grey, B 32, seed 0, no budget). */
+void gapsp_default_opts(gapsp_opts *opts);
+
+/*
+ * Creates a handle for one image (Sec. 2: the image as a graph).
+ *   img  : H*W uint8 grey levels, row-major, host or device pointer; read
+ *          during the call only (copied).
+ *   mask : H*W uint8, 1 = free pixel, 0 = obstacle; host or device; required
+ *          for GAPSP_MASK and ignored for GAPSP_GREY.
+ *   H, W : 1..GAPSP_MAX_SIDE each, H*W <= GAPSP_MAX_N.
+ * The handle owns a device copy of the image, its per-line weight prefix
+ * sums and the bookkeeping arrays (marks, fill counts). On error *out is
+ * NULL and nothing is allocated.
+ */
+gapsp_status gapsp_create(const uint8_t *img, int H, int W, const uint8_t *mask,
+                          const gapsp_opts *opts, gapsp_handle **out);
+
+/*
+ * Fills the whole N x N array D (Sec. 2, eq. "A": all (N^2 - N)/2 pairs) by
+ * propagations from sources chosen in `order`, B per round, plus the
+ * geodesic-tree fill of Property 1.
+ *   D  : caller-owned uint32 N*N, device pointer or host pointer (a host
+ *        array is filled through a device buffer the call allocates).
+ *   st : may be NULL; otherwise receives the counts, which equal those of
+ *        the same order simulated on the CPU.
+ * Errors: GAPSP_E_INVALID (order, NULL D), GAPSP_E_BUDGET, GAPSP_E_NOMEM,
+ * GAPSP_E_NOT_CONVERGED, GAPSP_E_TIMEOUT, GAPSP_E_CUDA. On error the content
+ * of D is unspecified.
+ */
+gapsp_status gapsp_all_pairs(gapsp_handle *h, gapsp_order order, uint32_t *D,
+                             gapsp_stats *st);
+
+/*
+ * Single-source propagations (Sec. 1: "geodesic propagation"): out[k*N + q]
+ * = d(sources[k], q) for k < K. No tree, marks or selection.
+ *   sources : K int32 pixel indices, host or device pointer.
+ *   out     : caller-owned uint32 K*N, device or host pointer.
+ * Errors: GAPSP_E_INVALID (K < 0, a source outside [0, N), NULL pointers),
+ * GAPSP_E_BUDGET, GAPSP_E_NOMEM, GAPSP_E_NOT_CONVERGED, GAPSP_E_CUDA. With
+ * an invalid source nothing is written.
+ */
+gapsp_status gapsp_rows(gapsp_handle *h, const int32_t *sources, int K, uint32_t *out);
+
+/* Releases the handle and its device memory. NULL is accepted. */
+void gapsp_destroy(gapsp_handle *h);
+
+/* Static text for a status code. */
+const char *gapsp_strerror(gapsp_status s);
+
+/* Number of kernels the library launched on this handle since its creation
+ * (for launch accounting). */
+uint64_t gapsp_kernel_launches(const gapsp_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GAPSP_H */
