@@ -100,6 +100,7 @@ typedef struct {
     int32_t *sources;              /* optional, caller-owned host array receiving the
                                       sources in selection order (capacity sources_cap) */
     uint64_t sources_cap;
+    uint64_t sweeps;               /* directional sweeps run by all propagations */
 } gapsp_stats;
 
 /* Fills *opts with the defaults (conn 8, grey, B 32, seed 0, no budget). */
@@ -154,6 +155,20 @@ const char *gapsp_strerror(gapsp_status s);
 /* Number of kernels the library launched on this handle since its creation
  * (for launch accounting). */
 uint64_t gapsp_kernel_launches(const gapsp_handle *h);
+
+/*
+ * Per-kernel device time, for measurement. While enabled, every launch of
+ * the kernels below is bracketed by CUDA events on the handle's stream, and
+ * gapsp_profile_read returns, per kernel, the summed event time (ms) and the
+ * number of launches since the last read (then resets). Enabling adds two
+ * event records per launch; leave it off for throughput timing.
+ * Kernel ids: 0 selection (c), 1 propagation (a), 2 parents (a'),
+ * 3 segments (a'), 4 tree fill (b), 5 init, 6 extrema pre-pass helpers.
+ * ms and launches: caller-owned arrays of GAPSP_NUM_KERNELS entries.
+ */
+#define GAPSP_NUM_KERNELS 7
+gapsp_status gapsp_profile_enable(gapsp_handle *h, int enable);
+gapsp_status gapsp_profile_read(gapsp_handle *h, double *ms, uint64_t *launches);
 
 #ifdef __cplusplus
 }

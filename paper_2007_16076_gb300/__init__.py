@@ -1,0 +1,227 @@
+"""Python binding of libgapsp (all pairs of geodesic distances on one GPU).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``libgapsp.so`` behind the C ABI of ``include/gapsp.h``. There is
+no CPU fallback; if the library cannot be loaded the calls raise.
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA). Output
+arrays default to CUDA tensors of dtype int32 holding the uint32 bit
+patterns; :func:`as_uint32` views them as numpy uint32.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+UNREACH = 0xFFFFFFFF
+ORDERS = {"naive": 0, "spiral": 1, "minfill": 2}
+KINDS = {"grey": 0, "mask": 1}
+KERNELS = ("select", "propagate", "parents", "segments", "fill", "init", "prepass")
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "memory budget exceeded",
+          4: "CUDA runtime error", 5: "propagation did not converge", 6: "round limit exceeded",
+          7: "cancelled"}
+
+_lib = None
+
+
+class GapspError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)} (status {code})")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("conn", ctypes.c_int), ("kind", ctypes.c_int), ("B", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("mem_budget", ctypes.c_size_t),
+                ("tile_h", ctypes.c_int), ("tile_w", ctypes.c_int), ("checked", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("propagations", ctypes.c_uint64), ("prepass_propagations", ctypes.c_uint64),
+                ("distance_ops", ctypes.c_uint64), ("new_pairs", ctypes.c_uint64),
+                ("rounds", ctypes.c_uint64), ("prefilled_pairs", ctypes.c_uint64),
+                ("ms_total", ctypes.c_double),
+                ("round_new", ctypes.POINTER(ctypes.c_uint64)), ("round_new_cap", ctypes.c_uint64),
+                ("sources", ctypes.POINTER(ctypes.c_int32)), ("sources_cap", ctypes.c_uint64),
+                ("sweeps", ctypes.c_uint64)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libgapsp.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libgapsp.so is not built; run paper_2007_16076_gb300._build.build()")
+    lib = ctypes.CDLL(_build.LIB)
+    P = ctypes.c_void_p
+    lib.gapsp_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    lib.gapsp_create.argtypes = [P, ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(Opts),
+                                 ctypes.POINTER(P)]
+    lib.gapsp_create.restype = ctypes.c_int
+    lib.gapsp_all_pairs.argtypes = [P, ctypes.c_int, P, ctypes.POINTER(Stats)]
+    lib.gapsp_all_pairs.restype = ctypes.c_int
+    lib.gapsp_rows.argtypes = [P, P, ctypes.c_int, P]
+    lib.gapsp_rows.restype = ctypes.c_int
+    lib.gapsp_destroy.argtypes = [P]
+    lib.gapsp_destroy.restype = None
+    lib.gapsp_strerror.argtypes = [ctypes.c_int]
+    lib.gapsp_strerror.restype = ctypes.c_char_p
+    lib.gapsp_kernel_launches.argtypes = [P]
+    lib.gapsp_kernel_launches.restype = ctypes.c_uint64
+    lib.gapsp_profile_enable.argtypes = [P, ctypes.c_int]
+    lib.gapsp_profile_enable.restype = ctypes.c_int
+    lib.gapsp_profile_read.argtypes = [P, P, P]
+    lib.gapsp_profile_read.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(x):
+    """Raw address of a numpy array or torch tensor (host or device)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(x.ctypes.data)
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr())
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def as_uint32(x) -> np.ndarray:
+    """Host numpy uint32 view/copy of an int32/uint32 array or tensor."""
+    if hasattr(x, "detach"):
+        x = x.detach().cpu().numpy()
+    return np.asarray(x).view(np.uint32)
+
+
+def _torch_stream(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+class Image:
+    """A handle on one image (gapsp_create / gapsp_destroy)."""
+
+    def __init__(self, img, conn: int = 8, kind: str = "grey", mask=None, B: int = 32,
+                 seed: int = 0, mem_budget: int = 0, stream=None):
+        lib = load()
+        self._lib = lib
+        self._h = ctypes.c_void_p()
+        if kind == "grey":
+            img_a = img if hasattr(img, "data_ptr") else np.ascontiguousarray(img, dtype=np.uint8)
+            H, W = int(img_a.shape[0]), int(img_a.shape[1])
+        else:
+            img_a = None
+            if mask is None:
+                raise ValueError("mask kind needs a mask")
+            H, W = int(mask.shape[0]), int(mask.shape[1])
+        mask_a = None
+        if mask is not None:
+            mask_a = mask if hasattr(mask, "data_ptr") else np.ascontiguousarray(mask, dtype=np.uint8)
+        o = Opts()
+        lib.gapsp_default_opts(ctypes.byref(o))
+        o.conn, o.kind, o.B = conn, KINDS[kind], B
+        o.seed = seed & (2 ** 64 - 1)
+        o.mem_budget = mem_budget
+        o.stream = _torch_stream(stream)
+        self.H, self.W, self.N, self.conn, self.kind, self.B = H, W, H * W, conn, kind, B
+        rc = lib.gapsp_create(_ptr(img_a), H, W, _ptr(mask_a), ctypes.byref(o), ctypes.byref(self._h))
+        if rc != 0:
+            self._h = ctypes.c_void_p()
+            raise GapspError(rc, "gapsp_create")
+
+    def close(self):
+        if self._h:
+            self._lib.gapsp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self._lib.gapsp_kernel_launches(self._h))
+
+    def profile(self, enable: bool = True):
+        """Turns per-kernel event timing on or off (gapsp_profile_enable)."""
+        rc = self._lib.gapsp_profile_enable(self._h, int(enable))
+        if rc != 0:
+            raise GapspError(rc, "gapsp_profile_enable")
+
+    def profile_read(self) -> dict:
+        """Per-kernel {name: (ms, launches)} since the last read."""
+        ms = np.zeros(len(KERNELS), dtype=np.float64)
+        n = np.zeros(len(KERNELS), dtype=np.uint64)
+        rc = self._lib.gapsp_profile_read(self._h, _ptr(ms), _ptr(n))
+        if rc != 0:
+            raise GapspError(rc, "gapsp_profile_read")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNELS)}
+
+    def all_pairs(self, order: str = "minfill", out=None, want_log: bool = False):
+        """Fills the N x N array (gapsp_all_pairs). Returns (D, stats dict)."""
+        N = self.N
+        if out is None:
+            import torch
+            out = torch.empty((N, N), dtype=torch.int32, device="cuda")
+        st = Stats()
+        rn = sl = None
+        if want_log:
+            rn = np.zeros(N + 1, dtype=np.uint64)
+            sl = np.zeros(N + 1, dtype=np.int32)
+            st.round_new = rn.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+            st.round_new_cap = len(rn)
+            st.sources = sl.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            st.sources_cap = len(sl)
+        rc = self._lib.gapsp_all_pairs(self._h, ORDERS[order], _ptr(out), ctypes.byref(st))
+        if rc != 0:
+            raise GapspError(rc, "gapsp_all_pairs")
+        stats = {"propagations": st.propagations, "prepass_propagations": st.prepass_propagations,
+                 "distance_ops": st.distance_ops, "new_pairs": st.new_pairs, "rounds": st.rounds,
+                 "prefilled_pairs": st.prefilled_pairs, "ms_total": st.ms_total,
+                 "sweeps": st.sweeps}
+        if want_log:
+            stats["round_new"] = rn[:st.rounds].copy()
+            stats["sources"] = sl[:st.propagations].copy()
+        return out, stats
+
+    def rows(self, sources, out=None):
+        """out[k] = d(sources[k], .) (gapsp_rows)."""
+        if hasattr(sources, "data_ptr"):
+            src = sources
+            K = int(src.numel())
+        else:
+            src = np.ascontiguousarray(sources, dtype=np.int32)
+            K = int(src.size)
+        if out is None:
+            import torch
+            out = torch.empty((K, self.N), dtype=torch.int32, device="cuda")
+        rc = self._lib.gapsp_rows(self._h, _ptr(src), K, _ptr(out))
+        if rc != 0:
+            raise GapspError(rc, "gapsp_rows")
+        return out

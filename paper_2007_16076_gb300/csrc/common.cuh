@@ -1,0 +1,61 @@
+// Device-side definitions shared by the gapsp kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gapsp {
+
+// Sentinel for "not reached yet" inside the sweeps. Real distances are below
+// (GAPSP_MAX_N - 1) * 511 < 2^26, and the sentinel plus any edge weight or
+// line prefix stays below 2^31, so all sweep arithmetic is plain int32.
+constexpr int PINF = 0x3FFFFFFF;
+constexpr uint32_t UNREACH = 0xFFFFFFFFu;
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+// Bits of the device status word.
+constexpr int ST_NOT_CONVERGED = 1;
+constexpr int ST_BAD_SOURCE = 2;
+constexpr int ST_TIMEOUT = 4;
+
+// Device counters of a fill run (one uint64 each).
+enum StatSlot {
+    S_PROPAGATIONS = 0,
+    S_OPS = 1,
+    S_NEW = 2,
+    S_ROUNDS = 3,
+    S_SWEEPS = 4,  // total sweeps run by the propagation warps
+    S_SLOTS = 8
+};
+
+// Marks: one 64-bit word per (row, 8x8 pixel tile). Bit (r%8)*8 + (c%8) of
+// word (r/8)*tiles_w + c/8 of row b says whether the pair {b, (r,c)} is
+// filled.
+struct TileGeom {
+    int W, tiles_w, words;  // words per row = tiles_h * tiles_w
+    __host__ __device__ int tile_of(int p) const {
+        int r = p / W, c = p - r * W;
+        return (r >> 3) * tiles_w + (c >> 3);
+    }
+    __host__ __device__ int bit_of(int p) const {
+        int r = p / W, c = p - r * W;
+        return ((r & 7) << 3) | (c & 7);
+    }
+    __host__ __device__ int pixel_of(int tile, int bit) const {
+        int tr = tile / tiles_w, tc = tile - tr * tiles_w;
+        return ((tr << 3) + (bit >> 3)) * W + (tc << 3) + (bit & 7);
+    }
+};
+
+__device__ __forceinline__ int ld_cg(const int* p) {
+    int v;
+    asm volatile("ld.global.cg.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_cg64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
+}
+
+}  // namespace gapsp

@@ -1,0 +1,608 @@
+// Host runtime and C ABI of gapsp (declared in include/gapsp.h).
+//
+// A handle owns the device copy of one image and everything a fill needs:
+// the fill counts, the tiled marks, the selected sources, the per-source
+// trees and the counters. The round loop is driven from the host: each
+// round launches selection (c), propagation (a), parents and segments (a')
+// and the fill (b) on the handle's stream; every kernel of a round reads
+// the device-side selection count and does nothing once the loop is over,
+// so rounds are enqueued in chunks and the host only checks the device
+// "done" flag between chunks.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/gapsp.h"
+#include "common.cuh"
+#include "internal.h"
+
+using namespace gapsp;
+
+struct gapsp_handle {
+    int H = 0, W = 0, N = 0, conn = 8, kind = 0, B = 32;
+    uint64_t seed = 0;
+    size_t budget = 0;
+    cudaStream_t st = nullptr;
+    int tiles_w = 0, tiles_h = 0, words = 0;
+    uint64_t launches = 0;
+    // image
+    uint8_t* f = nullptr;
+    int* Prow = nullptr;
+    int* Pcol = nullptr;
+    uint8_t* bound = nullptr;
+    int32_t* comp = nullptr;
+    int32_t* comp_size = nullptr;
+    int* status = nullptr;
+    int* changed = nullptr;
+    // fill state
+    bool fill_ready = false;
+    uint32_t* cnt = nullptr;
+    unsigned long long* marks = nullptr;
+    int32_t* parent = nullptr;
+    int32_t* seg_exit = nullptr;
+    unsigned long long* seg_mask = nullptr;
+    int32_t* sel = nullptr;
+    int* nsel = nullptr;
+    int* cursor = nullptr;
+    int* done = nullptr;
+    int32_t* seq = nullptr;
+    int32_t* rank = nullptr;
+    unsigned long long* stats = nullptr;
+    unsigned long long* round_new = nullptr;
+    unsigned long long* last_new = nullptr;
+    int32_t* sel_log = nullptr;
+    uint32_t* emap = nullptr;
+    uint32_t* gmap = nullptr;
+    unsigned long long* best = nullptr;
+    uint8_t* cen = nullptr;
+    int* h_done = nullptr;  // pinned
+    // scratch for host-side arrays
+    uint32_t* Dtmp = nullptr;
+    size_t Dtmp_bytes = 0;
+    int32_t* src_dev = nullptr;
+    int src_cap = 0;
+    uint32_t* out_tmp = nullptr;
+    size_t out_tmp_bytes = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // per-kernel timing (gapsp_profile_*)
+    bool prof = false;
+    struct Timed { int kind; cudaEvent_t a, b; };
+    std::vector<Timed> timed;
+    std::vector<cudaEvent_t> pool;
+};
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+    return cudaMalloc((void**)p, count * sizeof(T) > 0 ? count * sizeof(T) : 1);
+}
+
+template <class T>
+void dfree(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+#define CK(x)                                                  \
+    do {                                                       \
+        cudaError_t e_ = (x);                                  \
+        if (e_ != cudaSuccess) {                               \
+            cudaGetLastError();                                \
+            return e_ == cudaErrorMemoryAllocation ? GAPSP_E_NOMEM : GAPSP_E_CUDA; \
+        }                                                      \
+    } while (0)
+
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): the generator behind the
+// spiral order's random draws.
+uint64_t splitmix_next(uint64_t& s) {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Spiral order (Sec. 3.1): frames of pixels at equal distance from the
+// image border, outermost first; each frame in a uniformly random order
+// (Fisher-Yates driven by one SplitMix64 stream per frame). Taking the next
+// unfilled point of this sequence draws uniformly among the frame's
+// unfilled points, as Algorithm "spiral method" does.
+std::vector<int32_t> spiral_sequence(int H, int W, uint64_t seed, const std::vector<uint8_t>& freef) {
+    std::vector<std::vector<int32_t>> frames((std::min(H, W) + 1) / 2);
+    for (int p = 0; p < H * W; ++p) {
+        if (!freef.empty() && !freef[p]) continue;
+        const int r = p / W, c = p % W;
+        const int k = std::min(std::min(r, c), std::min(H - 1 - r, W - 1 - c));
+        frames[k].push_back(p);
+    }
+    std::vector<int32_t> out;
+    out.reserve(H * W);
+    for (size_t k = 0; k < frames.size(); ++k) {
+        std::vector<int32_t>& fr = frames[k];
+        uint64_t st = seed ^ ((uint64_t)k * 0x9E3779B97F4A7C15ull);
+        for (int i = (int)fr.size() - 1; i >= 1; --i) {
+            const int j = (int)(splitmix_next(st) % (uint64_t)(i + 1));
+            std::swap(fr[i], fr[j]);
+        }
+        out.insert(out.end(), fr.begin(), fr.end());
+    }
+    return out;
+}
+
+PropArgs base_prop(const gapsp_handle* h) {
+    PropArgs a{};
+    a.H = h->H;
+    a.W = h->W;
+    a.N = h->N;
+    a.f = h->f;
+    a.Prow = h->Prow;
+    a.Pcol = h->Pcol;
+    a.status = h->status;
+    a.max_sweeps = 4 * (h->N + 2);
+    return a;
+}
+
+size_t fill_state_bytes(const gapsp_handle* h) {
+    const size_t N = h->N, B = h->B;
+    return N * h->words * 8 + B * N * (4 + 4 + 8) + N * (4 + 4 + 4 + 4 + 8 + 8 + 1 + 4) + 4096;
+}
+
+gapsp_status ensure_fill_state(gapsp_handle* h) {
+    if (h->fill_ready) return GAPSP_OK;
+    const size_t N = h->N, B = h->B;
+    CK(dalloc(&h->cnt, N));
+    CK(dalloc(&h->marks, N * h->words));
+    CK(dalloc(&h->parent, B * N));
+    CK(dalloc(&h->seg_exit, B * N));
+    CK(dalloc(&h->seg_mask, B * N));
+    CK(dalloc(&h->sel, B));
+    CK(dalloc(&h->nsel, 1));
+    CK(dalloc(&h->cursor, 1));
+    CK(dalloc(&h->done, 1));
+    CK(dalloc(&h->seq, N));
+    CK(dalloc(&h->rank, N));
+    CK(dalloc(&h->stats, S_SLOTS));
+    CK(dalloc(&h->round_new, N + 1));
+    CK(dalloc(&h->last_new, 1));
+    CK(dalloc(&h->sel_log, N + 1));
+    CK(dalloc(&h->emap, N));
+    CK(dalloc(&h->gmap, N));
+    CK(dalloc(&h->best, N));
+    CK(dalloc(&h->cen, N));
+    CK(cudaMallocHost((void**)&h->h_done, sizeof(int)));
+    h->fill_ready = true;
+    return GAPSP_OK;
+}
+
+void free_all(gapsp_handle* h) {
+    dfree(h->f); dfree(h->Prow); dfree(h->Pcol); dfree(h->bound); dfree(h->comp);
+    dfree(h->comp_size); dfree(h->status); dfree(h->changed);
+    dfree(h->cnt); dfree(h->marks); dfree(h->parent); dfree(h->seg_exit); dfree(h->seg_mask);
+    dfree(h->sel); dfree(h->nsel); dfree(h->cursor); dfree(h->done); dfree(h->seq); dfree(h->rank);
+    dfree(h->stats); dfree(h->round_new); dfree(h->last_new); dfree(h->sel_log);
+    dfree(h->emap); dfree(h->gmap); dfree(h->best); dfree(h->cen);
+    dfree(h->Dtmp); dfree(h->src_dev); dfree(h->out_tmp);
+    if (h->h_done) cudaFreeHost(h->h_done);
+    h->h_done = nullptr;
+    for (auto& t : h->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
+    h->timed.clear();
+    for (auto e : h->pool) cudaEventDestroy(e);
+    h->pool.clear();
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    h->ev0 = h->ev1 = nullptr;
+}
+
+enum { K_SELECT = 0, K_PROP = 1, K_PARENTS = 2, K_SEGMENTS = 3, K_FILL = 4, K_INIT = 5, K_PRE = 6 };
+
+cudaEvent_t pool_get(gapsp_handle* h) {
+    if (!h->pool.empty()) {
+        cudaEvent_t e = h->pool.back();
+        h->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one launch with events when profiling is on.
+struct ProfScope {
+    gapsp_handle* h;
+    bool on;
+    ProfScope(gapsp_handle* hh, int kind, cudaStream_t s) : h(hh), on(hh->prof) {
+        if (!on) return;
+        gapsp_handle::Timed t{kind, pool_get(h), pool_get(h)};
+        cudaEventRecord(t.a, s);
+        h->timed.push_back(t);
+        stream = s;
+    }
+    ~ProfScope() {
+        if (on) cudaEventRecord(h->timed.back().b, stream);
+    }
+    cudaStream_t stream = nullptr;
+};
+
+gapsp_status status_from_word(int w) {
+    if (w & ST_NOT_CONVERGED) return GAPSP_E_NOT_CONVERGED;
+    if (w & ST_TIMEOUT) return GAPSP_E_TIMEOUT;
+    if (w & ST_BAD_SOURCE) return GAPSP_E_INVALID;
+    return GAPSP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gapsp_default_opts(gapsp_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->conn = 8;
+    o->kind = GAPSP_GREY;
+    o->B = 32;
+}
+
+const char* gapsp_strerror(gapsp_status s) {
+    switch (s) {
+        case GAPSP_OK: return "ok";
+        case GAPSP_E_INVALID: return "invalid argument";
+        case GAPSP_E_NOMEM: return "out of memory";
+        case GAPSP_E_BUDGET: return "memory budget exceeded";
+        case GAPSP_E_CUDA: return "CUDA runtime error";
+        case GAPSP_E_NOT_CONVERGED: return "propagation did not converge within its sweep limit";
+        case GAPSP_E_TIMEOUT: return "round loop exceeded its round limit";
+        case GAPSP_E_CANCELLED: return "cancelled";
+    }
+    return "unknown status";
+}
+
+uint64_t gapsp_kernel_launches(const gapsp_handle* h) { return h ? h->launches : 0; }
+
+gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask, const gapsp_opts* opts,
+                          gapsp_handle** out) {
+    if (!out) return GAPSP_E_INVALID;
+    *out = nullptr;
+    gapsp_opts o;
+    gapsp_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.conn == 0) o.conn = 8;
+    if (o.B == 0) o.B = 32;
+    if (H < 1 || W < 1 || H > GAPSP_MAX_SIDE || W > GAPSP_MAX_SIDE || H * W > GAPSP_MAX_N) return GAPSP_E_INVALID;
+    if (o.conn != 4 && o.conn != 8) return GAPSP_E_INVALID;
+    if (o.kind != GAPSP_GREY && o.kind != GAPSP_MASK) return GAPSP_E_INVALID;
+    if (o.B < 1 || o.B > 1024) return GAPSP_E_INVALID;
+    if (o.kind == GAPSP_GREY && !img) return GAPSP_E_INVALID;
+    if (o.kind == GAPSP_MASK && !mask) return GAPSP_E_INVALID;
+
+    gapsp_handle* h = new (std::nothrow) gapsp_handle();
+    if (!h) return GAPSP_E_NOMEM;
+    h->H = H; h->W = W; h->N = H * W; h->conn = o.conn; h->kind = o.kind; h->B = o.B;
+    h->seed = o.seed; h->budget = o.mem_budget; h->st = (cudaStream_t)o.stream;
+    h->tiles_w = (W + 7) / 8; h->tiles_h = (H + 7) / 8; h->words = h->tiles_w * h->tiles_h;
+    const size_t N = h->N;
+    if (h->budget && N * 32 + 4096 > h->budget) { delete h; return GAPSP_E_BUDGET; }
+
+    auto fail = [&](cudaError_t e) {
+        cudaGetLastError();
+        free_all(h);
+        delete h;
+        return e == cudaErrorMemoryAllocation ? GAPSP_E_NOMEM : GAPSP_E_CUDA;
+    };
+    cudaError_t e;
+    if ((e = dalloc(&h->f, N)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&h->Prow, N)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&h->Pcol, N)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&h->bound, N)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&h->status, 1)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&h->changed, 1)) != cudaSuccess) return fail(e);
+    if ((e = cudaEventCreate(&h->ev0)) != cudaSuccess) return fail(e);
+    if ((e = cudaEventCreate(&h->ev1)) != cudaSuccess) return fail(e);
+    // the kernels read grey levels (grey) or free flags (mask) from h->f
+    const uint8_t* srcimg = o.kind == GAPSP_GREY ? img : mask;
+    if ((e = cudaMemcpyAsync(h->f, srcimg, N, cudaMemcpyDefault, h->st)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemsetAsync(h->status, 0, sizeof(int), h->st)) != cudaSuccess) return fail(e);
+    if (o.kind == GAPSP_MASK) {
+        // normalise the flags to 0/1
+        std::vector<uint8_t> m(N);
+        if ((e = cudaMemcpy(m.data(), mask, N, cudaMemcpyDefault)) != cudaSuccess) return fail(e);
+        for (auto& v : m) v = v ? 1 : 0;
+        if ((e = cudaMemcpyAsync(h->f, m.data(), N, cudaMemcpyHostToDevice, h->st)) != cudaSuccess) return fail(e);
+        if ((e = cudaStreamSynchronize(h->st)) != cudaSuccess) return fail(e);
+    }
+    ImagePrep ip{h->f, H, W, o.conn, (int)o.kind, h->Prow, h->Pcol, h->bound};
+    if ((e = launch_image_prep(ip, h->st)) != cudaSuccess) return fail(e);
+    h->launches += o.kind == GAPSP_GREY ? 2 : 1;
+    if (o.kind == GAPSP_MASK) {
+        if ((e = dalloc(&h->comp, N)) != cudaSuccess) return fail(e);
+        if ((e = dalloc(&h->comp_size, N)) != cudaSuccess) return fail(e);
+        CompArgs ca{H, W, o.conn, h->f, h->comp, h->comp_size, h->changed, h->status};
+        if ((e = launch_components(ca, h->st)) != cudaSuccess) return fail(e);
+        h->launches += 1;
+    }
+    if ((e = cudaStreamSynchronize(h->st)) != cudaSuccess) return fail(e);
+    int sw = 0;
+    if ((e = cudaMemcpy(&sw, h->status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess) return fail(e);
+    if (sw) {
+        free_all(h);
+        delete h;
+        return status_from_word(sw);
+    }
+    *out = h;
+    return GAPSP_OK;
+}
+
+void gapsp_destroy(gapsp_handle* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->st);
+    free_all(h);
+    delete h;
+}
+
+gapsp_status gapsp_rows(gapsp_handle* h, const int32_t* sources, int K, uint32_t* out) {
+    if (!h || K < 0) return GAPSP_E_INVALID;
+    if (K == 0) return GAPSP_OK;
+    if (!sources || !out) return GAPSP_E_INVALID;
+    const size_t N = h->N;
+    std::vector<int32_t> hs(K);
+    CK(cudaMemcpy(hs.data(), sources, K * sizeof(int32_t), cudaMemcpyDefault));
+    for (int k = 0; k < K; ++k)
+        if (hs[k] < 0 || hs[k] >= h->N) return GAPSP_E_INVALID;
+    const bool out_dev = is_device_ptr(out);
+    const size_t out_bytes = (size_t)K * N * sizeof(uint32_t);
+    if (h->budget && (out_dev ? 0 : out_bytes) + (size_t)K * 4 > h->budget) return GAPSP_E_BUDGET;
+    if (K > h->src_cap) {
+        dfree(h->src_dev);
+        CK(dalloc(&h->src_dev, K));
+        h->src_cap = K;
+    }
+    uint32_t* dout = out;
+    if (!out_dev) {
+        if (h->out_tmp_bytes < out_bytes) {
+            dfree(h->out_tmp);
+            h->out_tmp_bytes = 0;
+            CK(dalloc(&h->out_tmp, (size_t)K * N));
+            h->out_tmp_bytes = out_bytes;
+        }
+        dout = h->out_tmp;
+    }
+    CK(cudaMemcpyAsync(h->src_dev, hs.data(), K * sizeof(int32_t), cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->st));
+    PropArgs a = base_prop(h);
+    a.map_base = (int*)dout;
+    a.sources = h->src_dev;
+    a.njobs = K;
+    a.convert = h->kind == GAPSP_MASK;
+    const int wpb = K >= 608 ? 4 : 1;
+    {
+        ProfScope ps(h, K_PROP, h->st);
+        CK(launch_propagate(a, h->conn, h->kind, (K + wpb - 1) / wpb, wpb, h->st));
+    }
+    h->launches += 1;
+    if (!out_dev) CK(cudaMemcpyAsync(out, dout, out_bytes, cudaMemcpyDeviceToHost, h->st));
+    int sw = 0;
+    CK(cudaMemcpyAsync(&sw, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return status_from_word(sw);
+}
+
+gapsp_status gapsp_all_pairs(gapsp_handle* h, gapsp_order order, uint32_t* D, gapsp_stats* st) {
+    if (!h || !D) return GAPSP_E_INVALID;
+    if (order != GAPSP_NAIVE && order != GAPSP_SPIRAL && order != GAPSP_MINFILL) return GAPSP_E_INVALID;
+    const size_t N = h->N;
+    const bool d_dev = is_device_ptr(D);
+    const size_t dbytes = N * N * sizeof(uint32_t);
+    const size_t need = fill_state_bytes(h) + (d_dev ? 0 : dbytes);
+    if (h->budget && need > h->budget) return GAPSP_E_BUDGET;
+    gapsp_status gs = ensure_fill_state(h);
+    if (gs != GAPSP_OK) return gs;
+    uint32_t* Dd = D;
+    if (!d_dev) {
+        if (h->Dtmp_bytes < dbytes) {
+            dfree(h->Dtmp);
+            h->Dtmp_bytes = 0;
+            CK(dalloc(&h->Dtmp, N * N));
+            h->Dtmp_bytes = dbytes;
+        }
+        Dd = h->Dtmp;
+    }
+    cudaStream_t s = h->st;
+
+    // host-built sequences (naive / spiral)
+    int nseq = 0;
+    if (order != GAPSP_MINFILL) {
+        std::vector<uint8_t> freef;
+        if (h->kind == GAPSP_MASK) {
+            freef.resize(N);
+            CK(cudaMemcpy(freef.data(), h->f, N, cudaMemcpyDeviceToHost));
+        }
+        std::vector<int32_t> seq;
+        if (order == GAPSP_NAIVE) {
+            for (int p = 0; p < h->N; ++p)
+                if (freef.empty() || freef[p]) seq.push_back(p);
+        } else {
+            seq = spiral_sequence(h->H, h->W, h->seed, freef);
+        }
+        nseq = (int)seq.size();
+        if (nseq) CK(cudaMemcpyAsync(h->seq, seq.data(), nseq * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));  // the host vector goes out of scope
+    }
+
+    CK(cudaEventRecord(h->ev0, s));
+    CK(cudaMemsetAsync(h->status, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(h->stats, 0, S_SLOTS * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(h->last_new, 0, sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(h->cursor, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(h->done, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(h->nsel, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(h->marks, 0, N * h->words * sizeof(unsigned long long), s));
+    InitArgs ia{h->N, Dd, h->cnt, h->comp, h->comp_size, h->kind == GAPSP_MASK};
+    {
+        ProfScope ps(h, K_INIT, s);
+        CK(launch_init(ia, s));
+    }
+    h->launches += 1;
+
+    uint64_t prepass = 0;
+    if (order == GAPSP_MINFILL) {
+        // geodesic extrema (Sec. 3.3): distance from the boundary vertices,
+        // centroid(s), distance from the centroid(s), rank in Ext
+        PropArgs a = base_prop(h);
+        a.map_base = (int*)h->emap;
+        a.seed_flags = h->bound;
+        a.njobs = 1;
+        a.convert = 1;
+        {
+            ProfScope ps(h, K_PROP, s);
+            CK(launch_propagate(a, h->conn, h->kind, 1, 1, s));
+        }
+        ExtremaArgs ea{h->N, h->kind == GAPSP_MASK ? h->f : nullptr, h->comp, h->emap, h->best, h->cen,
+                       h->gmap, h->rank};
+        {
+            ProfScope ps(h, K_PRE, s);
+            CK(launch_centroids(ea, s));
+        }
+        a.map_base = (int*)h->gmap;
+        a.seed_flags = h->cen;
+        {
+            ProfScope ps(h, K_PROP, s);
+            CK(launch_propagate(a, h->conn, h->kind, 1, 1, s));
+        }
+        {
+            ProfScope ps(h, K_PRE, s);
+            CK(launch_rank(ea, s));
+        }
+        h->launches += 6;
+        prepass = 2;
+    }
+
+    SelectArgs sa{h->N, h->B, (int)order, h->cnt, h->rank, h->seq, nseq, h->cursor, h->sel, h->nsel,
+                  h->stats, h->round_new, h->last_new, h->sel_log, h->done};
+    PropArgs pa = base_prop(h);
+    pa.map_base = (int*)Dd;
+    pa.map_row = h->sel;
+    pa.sources = h->sel;
+    pa.njobs_dev = h->nsel;
+    pa.convert = h->kind == GAPSP_MASK;
+    pa.sweeps = h->stats + S_SWEEPS;
+    TreeArgs ta{};
+    ta.H = h->H; ta.W = h->W; ta.N = h->N; ta.conn = h->conn; ta.kind = h->kind;
+    ta.tiles_w = h->tiles_w; ta.words = h->words;
+    ta.f = h->f; ta.D = Dd; ta.sel = h->sel; ta.nsel = h->nsel;
+    ta.parent = h->parent; ta.seg_exit = h->seg_exit; ta.seg_mask = h->seg_mask;
+    ta.marks = h->marks; ta.cnt = h->cnt; ta.Dw = Dd; ta.stats = h->stats;
+    {
+        const size_t row_bytes = (size_t)h->words * 8;
+        int rpb = (int)((96 * 1024) / row_bytes);
+        ta.rows_per_block = rpb < 1 ? 1 : (rpb > 32 ? 32 : rpb);
+    }
+
+    const int max_rounds = h->N + 2;
+    const int chunk = 16;
+    int rounds = 0;
+    bool finished = false;
+    while (!finished) {
+        for (int i = 0; i < chunk; ++i) {
+            {
+                ProfScope ps(h, K_SELECT, s);
+                CK(launch_select(sa, s));
+            }
+            {
+                ProfScope ps(h, K_PROP, s);
+                CK(launch_propagate(pa, h->conn, h->kind, h->B, 1, s));
+            }
+            {
+                ProfScope ps(h, K_PARENTS, s);
+                CK(launch_parents(ta, h->B, s));
+            }
+            {
+                ProfScope ps(h, K_SEGMENTS, s);
+                CK(launch_segments(ta, h->B, s));
+            }
+            {
+                ProfScope ps(h, K_FILL, s);
+                CK(launch_fill(ta, h->B, s));
+            }
+            h->launches += 5;
+        }
+        rounds += chunk;
+        CK(cudaMemcpyAsync(h->h_done, h->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        finished = *h->h_done != 0;
+        if (!finished && rounds > max_rounds) {
+            CK(cudaStreamSynchronize(s));
+            return GAPSP_E_TIMEOUT;
+        }
+    }
+    CK(cudaEventRecord(h->ev1, s));
+    unsigned long long hs[S_SLOTS];
+    int sw = 0;
+    CK(cudaMemcpyAsync(hs, h->stats, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&sw, h->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (st) {
+        st->propagations = hs[S_PROPAGATIONS];
+        st->prepass_propagations = prepass;
+        st->distance_ops = hs[S_OPS];
+        st->new_pairs = hs[S_NEW];
+        st->rounds = hs[S_ROUNDS];
+        st->prefilled_pairs = 0;
+        st->sweeps = hs[S_SWEEPS];
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+        st->ms_total = ms;
+        if (st->round_new && st->round_new_cap) {
+            const size_t n = std::min<uint64_t>(st->round_new_cap, hs[S_ROUNDS]);
+            if (n) CK(cudaMemcpy(st->round_new, h->round_new, n * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+        }
+        if (st->sources && st->sources_cap) {
+            const size_t n = std::min<uint64_t>(st->sources_cap, hs[S_PROPAGATIONS]);
+            if (n) CK(cudaMemcpy(st->sources, h->sel_log, n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        }
+        if (h->kind == GAPSP_MASK) {
+            // pairs in different components or touching an obstacle
+            std::vector<int32_t> comp(N), size(N);
+            CK(cudaMemcpy(comp.data(), h->comp, N * 4, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(size.data(), h->comp_size, N * 4, cudaMemcpyDeviceToHost));
+            uint64_t same = 0;
+            for (size_t p = 0; p < N; ++p)
+                if (comp[p] == (int32_t)p) same += (uint64_t)size[p] * (uint64_t)(size[p] - 1) / 2;
+            st->prefilled_pairs = (uint64_t)N * (N - 1) / 2 - same;
+        }
+    }
+    if (!d_dev) CK(cudaMemcpy(D, Dd, dbytes, cudaMemcpyDeviceToHost));
+    return status_from_word(sw);
+}
+
+gapsp_status gapsp_profile_enable(gapsp_handle* h, int enable) {
+    if (!h) return GAPSP_E_INVALID;
+    h->prof = enable != 0;
+    return GAPSP_OK;
+}
+
+gapsp_status gapsp_profile_read(gapsp_handle* h, double* ms, uint64_t* launches) {
+    if (!h || !ms || !launches) return GAPSP_E_INVALID;
+    for (int k = 0; k < GAPSP_NUM_KERNELS; ++k) { ms[k] = 0.0; launches[k] = 0; }
+    CK(cudaStreamSynchronize(h->st));
+    for (auto& t : h->timed) {
+        float e = 0.f;
+        CK(cudaEventElapsedTime(&e, t.a, t.b));
+        if (t.kind >= 0 && t.kind < GAPSP_NUM_KERNELS) { ms[t.kind] += e; launches[t.kind] += 1; }
+        h->pool.push_back(t.a);
+        h->pool.push_back(t.b);
+    }
+    h->timed.clear();
+    return GAPSP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+// Internal interfaces between the host runtime and the kernel translation
+// units of gapsp. Not part of the public C ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gapsp {
+
+struct PropArgs {
+    int* map_base;              // distance maps (int32 view of uint32 rows)
+    const int32_t* map_row;     // job j writes map_base + map_row[j] * N (NULL: j * N)
+    const int32_t* sources;     // job j's single source (NULL: seed_flags)
+    const uint8_t* seed_flags;  // multi-source seeds, one job (NULL: single sources)
+    const int* njobs_dev;       // device-side job count (NULL: use njobs)
+    int njobs;
+    int H, W, N;
+    const uint8_t* f;           // grey levels (grey) or free flags (mask)
+    const int* Prow;            // [H][W]: sum of horizontal edge weights left of (r,c)
+    const int* Pcol;            // [W][H]: sum of vertical edge weights above (r,c)
+    int* status;                // device status word (ST_* bits)
+    unsigned long long* sweeps; // optional: total sweeps run
+    int max_sweeps;
+    int convert;                // write UNREACH for pixels never reached
+};
+
+// Picks the per-lane width and launches kernel (a).
+cudaError_t launch_propagate(const PropArgs& a, int conn, int kind, int grid, int warps_per_block,
+                             cudaStream_t st);
+// Values held per lane for lines of length up to `side`.
+int prop_vpl(int side);
+
+struct ImagePrep {
+    const uint8_t* f;
+    int H, W, conn, kind;
+    int* Prow;
+    int* Pcol;
+    uint8_t* bound;  // boundary flags: free pixels with fewer free neighbours than conn
+};
+cudaError_t launch_image_prep(const ImagePrep& p, cudaStream_t st);
+
+struct TreeArgs {
+    int H, W, N, conn, kind, tiles_w, words;
+    const uint8_t* f;
+    const uint32_t* D;          // the array; row sel[j] holds d(sel[j], .)
+    const int32_t* sel;         // selected sources
+    const int* nsel;            // device count
+    int32_t* parent;            // [B][N]
+    int32_t* seg_exit;          // [B][N]
+    unsigned long long* seg_mask;  // [B][N]
+    unsigned long long* marks;  // [N][words]
+    uint32_t* cnt;              // [N]
+    uint32_t* Dw;               // writable array for new pairs
+    unsigned long long* stats;  // StatSlot counters
+    int rows_per_block;
+};
+cudaError_t launch_parents(const TreeArgs& a, int B, cudaStream_t st);
+cudaError_t launch_segments(const TreeArgs& a, int B, cudaStream_t st);
+cudaError_t launch_fill(const TreeArgs& a, int B, cudaStream_t st);
+
+struct SelectArgs {
+    int N, B, order;            // 0 naive / 1 spiral (sequence), 2 minfill
+    const uint32_t* cnt;
+    const int32_t* rank;        // minfill
+    const int32_t* seq;         // naive / spiral sequence
+    int nseq;
+    int* cursor;                // sequence cursor
+    int32_t* sel;
+    int* nsel;
+    unsigned long long* stats;
+    unsigned long long* round_new_log;  // per-round new pairs (reads S_NEW)
+    unsigned long long* last_new;       // S_NEW value at the previous round
+    int32_t* sel_log;           // sources in selection order (capacity N)
+    int* done;                  // set to 1 once every point is filled
+};
+cudaError_t launch_select(const SelectArgs& a, cudaStream_t st);
+
+struct InitArgs {
+    int N;
+    uint32_t* D;
+    uint32_t* cnt;
+    const int32_t* comp;        // component label per pixel (-1 obstacle), or NULL
+    const int32_t* comp_size;   // per label
+    int full_init;              // write UNREACH everywhere first (mask variant)
+};
+cudaError_t launch_init(const InitArgs& a, cudaStream_t st);
+
+struct ExtremaArgs {
+    int N;
+    const uint8_t* freef;       // NULL: every pixel free
+    const int32_t* comp;        // NULL: one component
+    const uint32_t* e;          // distance from the boundary
+    unsigned long long* best;   // [N] per component label: packed (e, -p)
+    uint8_t* cen_flags;         // [N] centroid seeds
+    const uint32_t* g;          // distance from the centroids
+    int32_t* rank;              // [N]
+};
+cudaError_t launch_centroids(const ExtremaArgs& a, cudaStream_t st);
+cudaError_t launch_rank(const ExtremaArgs& a, cudaStream_t st);
+
+struct CompArgs {
+    int H, W, conn;
+    const uint8_t* freef;
+    int32_t* label;
+    int32_t* size;
+    int* changed;
+    int* status;
+};
+cudaError_t launch_components(const CompArgs& a, cudaStream_t st);
+
+cudaError_t launch_unreach_convert(uint32_t* rows, size_t n, cudaStream_t st);
+
+}  // namespace gapsp

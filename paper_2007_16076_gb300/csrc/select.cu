@@ -1,0 +1,312 @@
+// Kernel (c): choice of the next sources, and the set-up kernels of a fill.
+//
+// Orders (Sec. 3):
+//  - naive / spiral: the next B points of a fixed sequence (raster order, or
+//    the spiral frames each drawn in random order, Algorithm "spiral
+//    method") that are not filled at the start of the round;
+//  - minimum filling rate (Algorithm "method based on the filling rate"):
+//    the B unfilled points with the smallest fill count cnt, ties going to
+//    the greatest geodesic extremum, i.e. the smallest position in the
+//    extrema list Ext (Sec. 3.3). With B = 1 this is the paper's loop.
+// "Filled" is tau(x) = 1, i.e. cnt(x) = N (Sec. 2, eq. "filling rate pt").
+#include "common.cuh"
+#include "internal.h"
+
+namespace gapsp {
+
+namespace {
+
+// Sequence orders: one warp scans forward from the cursor with ballots.
+__global__ void k_select_seq(SelectArgs a) {
+    const int lane = threadIdx.x;
+    if (*a.done) { if (lane == 0) *a.nsel = 0; return; }
+    int cursor = *a.cursor, ns = 0;
+    while (ns < a.B && cursor < a.nseq) {
+        const int idx = cursor + lane;
+        const int p = idx < a.nseq ? a.seq[idx] : -1;
+        const bool ok = p >= 0 && a.cnt[p] < (uint32_t)a.N;
+        const unsigned m = __ballot_sync(FULL, ok);
+        const int avail = __popc(m), take = min(avail, a.B - ns);
+        const int before = __popc(m & ((1u << lane) - 1u));
+        if (ok && before < take) a.sel[ns + before] = p;
+        if (take < avail) {
+            // stop just after the last taken point
+            unsigned mm = m;
+            for (int i = 0; i < take - 1; ++i) mm &= mm - 1;
+            cursor += __ffs(mm);  // position of the take-th set bit, plus one
+        } else {
+            cursor += min(32, a.nseq - cursor);
+        }
+        ns += take;
+    }
+    const unsigned long long props = a.stats[S_PROPAGATIONS];
+    __syncwarp();
+    for (int i = lane; i < ns; i += 32) a.sel_log[props + i] = a.sel[i];
+    if (lane == 0) {
+        *a.cursor = cursor;
+        *a.nsel = ns;
+        const unsigned long long rounds = a.stats[S_ROUNDS];
+        const unsigned long long cur_new = a.stats[S_NEW];
+        if (rounds > 0) a.round_new_log[rounds - 1] = cur_new - *a.last_new;
+        *a.last_new = cur_new;
+        if (ns == 0) {
+            *a.done = 1;
+        } else {
+            a.stats[S_ROUNDS] = rounds + 1;
+            a.stats[S_PROPAGATIONS] = props + ns;
+        }
+    }
+}
+
+// Minimum filling rate: radix selection of the B smallest keys
+// (cnt << 17 | rank) among unfilled points, one block of 1024 threads.
+constexpr int SEL_THREADS = 1024;
+
+__device__ __forceinline__ unsigned long long mf_key(const SelectArgs& a, int p) {
+    const uint32_t c = a.cnt[p];
+    const int32_t r = a.rank[p];
+    if (c >= (uint32_t)a.N || r < 0) return ~0ull;
+    return ((unsigned long long)c << 17) | (unsigned long long)r;
+}
+
+__global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
+    __shared__ unsigned hist[256];
+    __shared__ unsigned long long s_prefix;
+    __shared__ int s_need, s_count, s_unfilled;
+    __shared__ unsigned long long s_keys[1024];
+    __shared__ int s_pix[1024];
+    const int tid = threadIdx.x;
+    if (*a.done) { if (tid == 0) *a.nsel = 0; return; }
+    if (tid == 0) { s_unfilled = 0; s_count = 0; s_prefix = 0; }
+    __syncthreads();
+    int mine = 0;
+    for (int p = tid; p < a.N; p += SEL_THREADS) mine += mf_key(a, p) != ~0ull;
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(FULL, mine, o);
+    if ((tid & 31) == 0 && mine) atomicAdd(&s_unfilled, mine);
+    __syncthreads();
+    const int unfilled = s_unfilled;
+    const int want = min(unfilled, a.B);
+    unsigned long long thr = ~0ull - 1;  // select keys <= thr
+    if (want > 0 && want < unfilled) {
+        // find the want-th smallest key, 8 bits at a time over 40 bits
+        if (tid == 0) s_need = want;
+        unsigned long long prefix = 0;
+        for (int shift = 32; shift >= 0; shift -= 8) {
+            if (tid < 256) hist[tid] = 0;
+            __syncthreads();
+            for (int p = tid; p < a.N; p += SEL_THREADS) {
+                const unsigned long long k = mf_key(a, p);
+                if (k == ~0ull) continue;
+                if (shift + 8 < 64 && (k >> (shift + 8)) != (prefix >> (shift + 8))) continue;
+                atomicAdd(&hist[(k >> shift) & 255], 1u);
+            }
+            __syncthreads();
+            if (tid < 32) {
+                // warp 0 finds the digit holding the need-th key
+                const int need = s_need;
+                unsigned loc[8], sum = 0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) { loc[i] = hist[tid * 8 + i]; sum += loc[i]; }
+                unsigned incl = sum;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned t = __shfl_up_sync(FULL, incl, o);
+                    if (tid >= o) incl += t;
+                }
+                const unsigned excl = incl - sum;
+                if (excl < (unsigned)need && (unsigned)need <= incl) {
+                    unsigned acc = excl;
+                    for (int i = 0; i < 8; ++i) {
+                        if (acc + loc[i] >= (unsigned)need) {
+                            s_need = need - (int)acc;
+                            s_prefix = prefix | ((unsigned long long)(tid * 8 + i) << shift);
+                            break;
+                        }
+                        acc += loc[i];
+                    }
+                }
+            }
+            __syncthreads();
+            prefix = s_prefix;
+        }
+        thr = prefix;
+    }
+    // gather the selected points
+    if (want > 0) {
+        for (int p = tid; p < a.N; p += SEL_THREADS) {
+            const unsigned long long k = mf_key(a, p);
+            if (k != ~0ull && k <= thr) {
+                const int slot = atomicAdd(&s_count, 1);
+                if (slot < 1024) { s_keys[slot] = k; s_pix[slot] = p; }
+            }
+        }
+    }
+    __syncthreads();
+    const int ns = min(s_count, want);
+    // order the selection by key (rank sort; keys are distinct)
+    if (tid < ns) {
+        const unsigned long long k = s_keys[tid];
+        int pos = 0;
+        for (int i = 0; i < ns; ++i) pos += s_keys[i] < k;
+        a.sel[pos] = s_pix[tid];
+        const unsigned long long props = a.stats[S_PROPAGATIONS];
+        a.sel_log[props + pos] = s_pix[tid];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        *a.nsel = ns;
+        unsigned long long rounds = a.stats[S_ROUNDS];
+        unsigned long long cur_new = a.stats[S_NEW];
+        if (rounds > 0) a.round_new_log[rounds - 1] = cur_new - *a.last_new;
+        *a.last_new = cur_new;
+        if (ns == 0) {
+            *a.done = 1;
+        } else {
+            a.stats[S_ROUNDS] = rounds + 1;
+            a.stats[S_PROPAGATIONS] += ns;
+        }
+    }
+}
+
+// Fill counts at the start (Sec. 2: D_mrk(i,i) = 1; pairs no path joins are
+// known at once) and the zero diagonal of D.
+__global__ void k_init(InitArgs a) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.N) return;
+    uint32_t c = 1;
+    if (a.comp) {
+        const int l = a.comp[p];
+        c = l < 0 ? (uint32_t)a.N : 1u + (uint32_t)(a.N - a.comp_size[l]);
+    }
+    a.cnt[p] = c;
+    a.D[(size_t)p * a.N + p] = 0;
+}
+
+// Geodesic centroid per component: argmax of the distance from the boundary,
+// ties to the smallest index (Sec. 3.3).
+__global__ void k_centroid_max(ExtremaArgs a) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.N) return;
+    if (a.freef && !a.freef[p]) return;
+    const int l = a.comp ? a.comp[p] : 0;
+    const unsigned long long key = ((unsigned long long)a.e[p] << 32) | (0xFFFFFFFFull - (unsigned)p);
+    atomicMax(a.best + l, key);
+}
+
+__global__ void k_centroid_mark(ExtremaArgs a) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.N) return;
+    const bool rep = a.comp ? (a.comp[p] == p) : (p == 0);
+    if (!rep) return;
+    const unsigned long long k = a.best[a.comp ? p : 0];
+    const int c = (int)(0xFFFFFFFFull - (k & 0xFFFFFFFFull));
+    if (c >= 0 && c < a.N) a.cen_flags[c] = 1;
+}
+
+// Position in the extrema list Ext: free pixels by decreasing distance from
+// the centroid, ties by increasing index. Counted directly.
+__global__ void k_rank(ExtremaArgs a) {
+    __shared__ uint32_t sg[1024];
+    __shared__ uint8_t sf[1024];
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool have = p < a.N && (!a.freef || a.freef[p]);
+    const uint32_t gp = have ? a.g[p] : 0;
+    int r = 0;
+    for (int base = 0; base < a.N; base += 1024) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
+            const int q = base + i;
+            sg[i] = q < a.N ? a.g[q] : 0;
+            sf[i] = q < a.N && (!a.freef || a.freef[q]);
+        }
+        __syncthreads();
+        if (have) {
+            const int lim = min(1024, a.N - base);
+            for (int i = 0; i < lim; ++i) {
+                const int q = base + i;
+                r += sf[i] && (sg[i] > gp || (sg[i] == gp && q < p));
+            }
+        }
+    }
+    if (p < a.N) a.rank[p] = have ? r : -1;
+}
+
+// Connected components of free pixels by minimum-label propagation with
+// pointer jumping, in one block; the label is the smallest pixel index of
+// the component.
+__global__ void k_components(CompArgs a) {
+    __shared__ int s_changed;
+    const int N = a.H * a.W;
+    for (int p = threadIdx.x; p < N; p += blockDim.x) a.label[p] = a.freef[p] ? p : -1;
+    __syncthreads();
+    for (int iter = 0; iter <= N + 1; ++iter) {
+        if (threadIdx.x == 0) s_changed = 0;
+        __syncthreads();
+        int ch = 0;
+        for (int p = threadIdx.x; p < N; p += blockDim.x) {
+            int l = a.label[p];
+            if (l < 0) continue;
+            const int r = p / a.W, c = p - r * a.W;
+            int m = l;
+            for (int dr = -1; dr <= 1; ++dr)
+                for (int dc = -1; dc <= 1; ++dc) {
+                    if (!dr && !dc) continue;
+                    if (a.conn == 4 && dr && dc) continue;
+                    const int rr = r + dr, cc = c + dc;
+                    if (rr < 0 || rr >= a.H || cc < 0 || cc >= a.W) continue;
+                    const int lq = ((volatile int*)a.label)[rr * a.W + cc];
+                    if (lq >= 0 && lq < m) m = lq;
+                }
+            m = min(m, ((volatile int*)a.label)[m]);
+            if (m < l) { a.label[p] = m; ch = 1; }
+        }
+        if (ch) s_changed = 1;
+        __syncthreads();
+        if (!s_changed) break;
+        if (iter == N + 1 && threadIdx.x == 0) atomicOr(a.status, ST_NOT_CONVERGED);
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < N; p += blockDim.x) a.size[p] = 0;
+    __syncthreads();
+    for (int p = threadIdx.x; p < N; p += blockDim.x)
+        if (a.label[p] >= 0) atomicAdd(a.size + a.label[p], 1);
+}
+
+}  // namespace
+
+cudaError_t launch_select(const SelectArgs& a, cudaStream_t st) {
+    if (a.order == 2) k_select_minfill<<<1, SEL_THREADS, 0, st>>>(a);
+    else k_select_seq<<<1, 32, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(const InitArgs& a, cudaStream_t st) {
+    if (a.full_init) {
+        cudaError_t e = cudaMemsetAsync(a.D, 0xFF, (size_t)a.N * a.N * sizeof(uint32_t), st);
+        if (e != cudaSuccess) return e;
+    }
+    k_init<<<(a.N + 255) / 256, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_centroids(const ExtremaArgs& a, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(a.best, 0, (size_t)a.N * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(a.cen_flags, 0, (size_t)a.N, st);
+    if (e != cudaSuccess) return e;
+    k_centroid_max<<<(a.N + 255) / 256, 256, 0, st>>>(a);
+    k_centroid_mark<<<(a.N + 255) / 256, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rank(const ExtremaArgs& a, cudaStream_t st) {
+    k_rank<<<(a.N + 255) / 256, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_components(const CompArgs& a, cudaStream_t st) {
+    k_components<<<1, 1024, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace gapsp

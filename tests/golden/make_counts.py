@@ -1,0 +1,50 @@
+"""Writes the oracle's counts for the full-size workloads into JSON fixtures.
+
+Calls only the CPU oracle (``oracle.fill``) on the seeded synthetic inputs;
+nothing here touches the CUDA library. Run from the repository root:
+
+    python tests/golden/make_counts.py [workload ...]
+"""
+import hashlib
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import oracle  # noqa: E402
+from paper_2007_16076_gb300 import synth  # noqa: E402
+
+WORKLOADS = {
+    "blobs128": lambda: synth.batched_128(0),
+}
+
+
+def main(names):
+    for name in names:
+        w = WORKLOADS[name]()
+        out = {"workload": w.name, "H": w.H, "W": w.W, "conn": w.conn, "kind": w.kind,
+               "B": w.B, "seed": w.meta.get("seed", 0), "spiral_seed": 0,
+               "generator": "paper_2007_16076_gb300.synth", "orders": {}}
+        for order in ("minfill", "naive", "spiral"):
+            t = time.time()
+            r = oracle.fill(w.img, order, B=w.B, seed=0, conn=w.conn, kind=w.kind, mask=w.mask)
+            out["orders"][order] = {
+                **r.counts(),
+                "round_new": [int(x) for x in r.round_new],
+                "sources_sha256": hashlib.sha256(r.sources.astype("<i4").tobytes()).hexdigest(),
+                "first_sources": [int(x) for x in r.sources[:64]],
+                "oracle_seconds": round(time.time() - t, 1),
+            }
+            print(name, order, r.counts(), f"{time.time() - t:.1f}s", flush=True)
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"counts_{name}.json")
+        with open(path, "w") as fh:
+            json.dump(out, fh, indent=1)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:] or list(WORKLOADS))

@@ -1,0 +1,230 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Distances are integers, so every comparison is bit-exact. Counts
+(propagations, distance operations, new pairs, rounds) and the order of the
+selected sources must equal the oracle's simulation of the same order.
+"""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2007_16076_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def gp():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2007_16076_gb300 as g
+    g.load()
+    return g
+
+
+def _u32(t):
+    return t.detach().cpu().numpy().view(np.uint32)
+
+
+# --------------------------------------------------------------------------
+# gapsp_rows: single-source propagations
+# --------------------------------------------------------------------------
+
+ROW_SHAPES = [(1, 1), (1, 9), (13, 1), (2, 2), (7, 13), (31, 33), (33, 45), (64, 64),
+              (100, 37), (37, 100), (128, 128), (129, 130), (200, 256)]
+
+
+@pytest.mark.parametrize("shape", ROW_SHAPES, ids=lambda s: f"{s[0]}x{s[1]}")
+@pytest.mark.parametrize("conn", [4, 8])
+def test_rows_grey(gp, shape, conn):
+    H, W = shape
+    img = synth.blobs(H, W, max(1, H * W // 300), max(1.5, (H + W) / 16), 55.0, seed=H * 7 + W)
+    N = H * W
+    rng = np.random.default_rng(H + W)
+    src = np.unique(np.concatenate([[0, N - 1, N // 2], rng.integers(0, N, size=min(N, 24))]))
+    src = src.astype(np.int32)
+    with gp.Image(img, conn=conn) as im:
+        out = _u32(im.rows(src))
+    ref = oracle.rows(img, src, conn=conn)
+    assert np.array_equal(out, ref)
+
+
+@pytest.mark.parametrize("shape", [(5, 5), (40, 33), (128, 128), (256, 256)], ids=lambda s: f"{s[0]}x{s[1]}")
+@pytest.mark.parametrize("conn", [4, 8])
+def test_rows_mask(gp, shape, conn):
+    H, W = shape
+    m = synth.disk_mask(H, W, 0.4, 3 if H > 20 else 1, 12 if H > 20 else 2, seed=H + conn)
+    N = H * W
+    rng = np.random.default_rng(N)
+    src = rng.integers(0, N, size=min(N, 20)).astype(np.int32)  # obstacles included
+    with gp.Image(None, conn=conn, kind="mask", mask=m) as im:
+        out = _u32(im.rows(src))
+    ref = oracle.rows(np.zeros_like(m), src, conn=conn, kind="mask", mask=m)
+    assert np.array_equal(out, ref)
+
+
+def test_rows_structured_images(gp):
+    """Winding corridors and step edges need many sweeps; uniform noise and
+    constant images are the other extremes."""
+    imgs = [synth.corridor(64, 64, seed=1), synth.corridor(25, 25, seed=2),
+            synth.uniform_random(50, 70, 1, 255, seed=3), np.full((40, 40), 9, np.uint8),
+            synth.blobs_with_steps(96, 96, 16, 8.0, 20, 100.0, 40.0, seed=4)]
+    for img in imgs:
+        N = img.size
+        src = np.array([0, N - 1, N // 3, (2 * N) // 3], dtype=np.int32)
+        for conn in (4, 8):
+            with gp.Image(img, conn=conn) as im:
+                out = _u32(im.rows(src))
+            assert np.array_equal(out, oracle.rows(img, src, conn=conn))
+
+
+def test_rows_host_buffers(gp):
+    img = synth.blobs(30, 40, 4, 3.0, 55.0, seed=9)
+    src = np.array([3, 500, 1199], dtype=np.int32)
+    out = np.zeros((3, img.size), dtype=np.uint32)
+    with gp.Image(img, conn=8) as im:
+        im.rows(src, out=out)
+    assert np.array_equal(out, oracle.rows(img, src, conn=8))
+
+
+def test_rows_many_sources_full_array(gp):
+    """All N sources (the naive method of Sec. 1) in one call."""
+    img = synth.blobs(32, 32, 8, 4.0, 55.0, seed=0)
+    N = img.size
+    with gp.Image(img, conn=4) as im:
+        out = _u32(im.rows(np.arange(N, dtype=np.int32)))
+    assert np.array_equal(out, oracle.apsp(img, conn=4))
+
+
+def test_rows_invalid_source(gp):
+    img = synth.blobs(8, 8, 2, 2.0, 55.0, seed=1)
+    with gp.Image(img, conn=8) as im:
+        with pytest.raises(gp.GapspError) as e:
+            im.rows(np.array([0, 64], dtype=np.int32))
+        assert e.value.code == 1
+        with pytest.raises(gp.GapspError):
+            im.rows(np.array([-1], dtype=np.int32))
+        out = im.rows(np.zeros(0, dtype=np.int32))
+        assert out.numel() == 0
+
+
+# --------------------------------------------------------------------------
+# gapsp_all_pairs: the method
+# --------------------------------------------------------------------------
+
+def _check_fill(gp, img, order, B, conn, kind="grey", mask=None, seed=0):
+    with gp.Image(img, conn=conn, kind=kind, mask=mask, B=B, seed=seed) as im:
+        D, st = im.all_pairs(order, want_log=True)
+    D = _u32(D)
+    ref = oracle.fill(img if img is not None else np.zeros_like(mask), order, B=B, seed=seed,
+                      conn=conn, kind=kind, mask=mask)
+    Dref = oracle.apsp(img if img is not None else np.zeros_like(mask), conn=conn, kind=kind, mask=mask)
+    assert np.array_equal(D, Dref)
+    for k in ("propagations", "prepass_propagations", "distance_ops", "new_pairs", "rounds"):
+        assert st[k] == getattr(ref, k), k
+    assert np.array_equal(st["round_new"], ref.round_new)
+    if B == 1:
+        assert np.array_equal(st["sources"], ref.sources)
+    else:  # order inside a round is by key for minfill, by sequence otherwise
+        assert np.array_equal(st["sources"], ref.sources)
+    return st
+
+
+@pytest.mark.parametrize("order", ["naive", "spiral", "minfill"])
+def test_all_pairs_plain_32(gp, order):
+    """32x32 blobs, 4-connected, B = 1: the paper's sequential loop."""
+    w = synth.plain_32(0)
+    _check_fill(gp, w.img, order, 1, 4)
+
+
+@pytest.mark.parametrize("order", ["naive", "spiral", "minfill"])
+@pytest.mark.parametrize("B", [2, 5, 32])
+@pytest.mark.parametrize("shape,conn", [((17, 23), 8), ((24, 9), 4), ((1, 40), 8)])
+def test_all_pairs_batched(gp, order, B, shape, conn):
+    img = synth.blobs(shape[0], shape[1], 3, 2.5, 55.0, seed=B + conn)
+    _check_fill(gp, img, order, B, conn, seed=B)
+
+
+@pytest.mark.parametrize("order", ["naive", "spiral", "minfill"])
+@pytest.mark.parametrize("conn", [4, 8])
+def test_all_pairs_mask(gp, order, conn):
+    m = synth.disk_mask(26, 31, 0.4, 2, 4, seed=conn)
+    st = _check_fill(gp, None, order, 4, conn, kind="mask", mask=m)
+    ref = oracle.fill(np.zeros_like(m), order, B=4, conn=conn, kind="mask", mask=m)
+    assert st["prefilled_pairs"] == ref.prefilled_pairs
+
+
+def test_all_pairs_degenerate(gp):
+    for img in (np.array([[7]], np.uint8), np.array([[1, 2]], np.uint8),
+                np.full((3, 1), 4, np.uint8)):
+        for order in ("naive", "spiral", "minfill"):
+            _check_fill(gp, img, order, 1, 8)
+
+
+def test_all_pairs_host_array(gp):
+    img = synth.blobs(20, 21, 3, 2.5, 55.0, seed=5)
+    N = img.size
+    D = np.zeros((N, N), dtype=np.uint32)
+    with gp.Image(img, conn=8, B=8) as im:
+        im.all_pairs("minfill", out=D)
+    assert np.array_equal(D, oracle.apsp(img, conn=8))
+
+
+def test_all_pairs_repeat_and_orders_share_handle(gp):
+    """D is the same for every order and B; a handle can be reused."""
+    img = synth.blobs(19, 22, 3, 2.5, 55.0, seed=6)
+    ref = oracle.apsp(img, conn=8)
+    with gp.Image(img, conn=8, B=3) as im:
+        for order in ("minfill", "naive", "spiral", "minfill"):
+            D, _ = im.all_pairs(order)
+            assert np.array_equal(_u32(D), ref)
+
+
+def test_budget_rejected_before_allocation(gp):
+    img = synth.blobs(64, 64, 4, 4.0, 55.0, seed=1)
+    with gp.Image(img, conn=8, B=32, mem_budget=1 << 20) as im:
+        with pytest.raises(gp.GapspError) as e:
+            im.all_pairs("minfill")
+        assert e.value.code == 3
+
+
+# --------------------------------------------------------------------------
+# Full-size workload: 128x128, 8-connected, B = 32
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("order", ["minfill", "naive", "spiral"])
+def test_full_size_blobs128(gp, order):
+    """The benchmark's workload in the benchmark's launch configuration:
+    counts, per-round new pairs and the selected sources against the
+    oracle's stored simulation; sampled rows of D against Dijkstra; the
+    whole array against invariants that hold at any size."""
+    import torch
+    path = os.path.join(GOLDEN, "counts_blobs128.json")
+    if not os.path.exists(path):
+        pytest.skip("counts fixture not generated")
+    gold = json.load(open(path))["orders"][order]
+    w = synth.batched_128(0)
+    with gp.Image(w.img, conn=w.conn, B=w.B, seed=0) as im:
+        D, st = im.all_pairs(order, want_log=True)
+    for k in ("propagations", "prepass_propagations", "distance_ops", "new_pairs", "rounds"):
+        assert st[k] == gold[k], k
+    assert [int(x) for x in st["round_new"]] == gold["round_new"]
+    assert hashlib.sha256(st["sources"].astype("<i4").tobytes()).hexdigest() == gold["sources_sha256"]
+    N = w.N
+    rng = np.random.default_rng(1)
+    rows = np.unique(np.concatenate([[0, N - 1], rng.integers(0, N, size=40)])).astype(np.int32)
+    Dr = _u32(D[torch.from_numpy(rows).long().cuda()])
+    assert np.array_equal(Dr, oracle.rows(w.img, rows, conn=w.conn))
+    Dc = _u32(D[:, torch.from_numpy(rows).long().cuda()]).T
+    assert np.array_equal(Dc, oracle.rows(w.img, rows, conn=w.conn))
+    # symmetry and zero diagonal of the whole array, on the device
+    assert bool((D == D.T).all())
+    assert bool((torch.diagonal(D) == 0).all())
+    assert int((D.view(torch.int32) < 0).sum()) == 0  # no unreachable pair on a grey image
