@@ -1,28 +1,31 @@
 // Kernel (a): geodesic propagation on the image graph.
 //
 // Computes d(s, .) = min over paths of the summed edge weights (Sec. 2, eqs.
-// "temps" and "distance"), the "geodesic time function" of Soille used by
-// the paper with a 3x3 neighbourhood (Sec. 3). Weights are w(p,q) = f(p) +
+// "temps" and "distance"), the "geodesic time function" of Soille that the
+// paper uses with a 3x3 neighbourhood (Sec. 3). Weights are w(p,q) = f(p) +
 // f(q) + 1 (grey) or 2 between free pixels (mask).
 //
-// One warp owns one source (or one multi-source seed set) and drives its map
-// to the exact fixpoint with directional sweeps. A sweep visits the lines of
-// the image in order (rows top-down, rows bottom-up, columns left-right,
-// columns right-left). For each line it
-//   1. relaxes every pixel from the already-final previous line (the 3
-//      neighbours above for 8-connectivity, 1 for 4), then
-//   2. closes the line in both directions at once: with P the prefix sum of
-//      the line's edge weights, the best value reachable along the line is
-//      min_c' v(c') + |P(c) - P(c')|, i.e. a prefix-min of v - P and a
-//      suffix-min of v + P (warp shuffles; skipped when a neighbour test
-//      shows the line is already closed).
-// A line of up to 32*VPL pixels lives in registers, lane j holding pixels
-// j, j+32, ... so that both row and column lines load without shared-memory
-// bank conflicts. All weights are >= 1 and integral, so the fixpoint is
-// unique and equal to the Dijkstra distances whatever the sweep schedule.
-// The warp stops when two sweeps that together test every edge direction
-// (down+up or right+left, or any three in a row) change nothing, and gives
-// up with a status bit after max_sweeps.
+// One block of four warps owns one source (or one multi-source seed set).
+// Its distance map sits in shared memory (global memory for images too
+// large), initialised to 0 at the seeds and "unreached" elsewhere. The four
+// warps sweep the map concurrently, each in its own direction: rows
+// top-down, rows bottom-up, columns left-right, columns right-left. For
+// each line a warp
+//   1. relaxes every pixel from the previous line it just finished (the
+//      three neighbours behind it for 8-connectivity, one for 4), then
+//   2. closes the line in both directions: with P the prefix sum of the
+//      line's edge weights, the best value along the line is
+//      min_c' v(c') + |P(c) - P(c')|, a prefix-min of v - P and a suffix-min
+//      of v + P. Lane j holds pixels VPL*j .. VPL*j+VPL-1, so the scans run
+//      inside the lane and need warp shuffles only when a boundary test
+//      shows that a value must cross from one lane to another,
+// and lowers the map with atomic minima. Every stored value is the cost of
+// a real path, so values only decrease towards the distances; the edge
+// weights are positive integers, so the fixpoint is unique and any schedule
+// reaches it. The block stops after a round (one sweep per warp) in which
+// no warp lowered anything: the map was then constant while every edge
+// direction was tested. Rounds are capped; hitting the cap sets a status
+// bit instead of looping on.
 #include "common.cuh"
 #include "internal.h"
 
@@ -30,50 +33,44 @@ namespace gapsp {
 
 namespace {
 
-// Where a warp keeps its distance map: shared memory (row pitch odd, so both
-// row lines and column lines hit 32 distinct banks), or global memory for
-// images too large for shared memory.
+constexpr int PWARPS = 4;                 // one warp per sweep direction
+constexpr int BIGX = PINF;                // identity of the prefix-min of v - P
+constexpr int BIGY = PINF + (1 << 18);    // identity of the suffix-min of v + P
+
 struct SmemMap {
     int* base;
     int pitch;
-    __device__ __forceinline__ int ld(int e_r, int e_c) const { return base[e_r * pitch + e_c]; }
-    __device__ __forceinline__ void st(int e_r, int e_c, int v) const { base[e_r * pitch + e_c] = v; }
+    __device__ __forceinline__ int ld(int r, int c) const {
+        return *((volatile const int*)(base + r * pitch + c));
+    }
+    __device__ __forceinline__ void lower(int r, int c, int v) const { atomicMin(base + r * pitch + c, v); }
 };
+
 struct GlobMap {
     int* base;
     int pitch;
-    __device__ __forceinline__ int ld(int e_r, int e_c) const { return ld_cg(base + e_r * pitch + e_c); }
-    __device__ __forceinline__ void st(int e_r, int e_c, int v) const { base[e_r * pitch + e_c] = v; }
+    __device__ __forceinline__ int ld(int r, int c) const { return ld_cg(base + r * pitch + c); }
+    __device__ __forceinline__ void lower(int r, int c, int v) const { atomicMin(base + r * pitch + c, v); }
 };
 
 template <int VPL>
 struct Line {
-    int o[VPL];  // value before this sweep
+    int o[VPL];  // map value when loaded
     int f[VPL];  // grey level (grey) or free flag (mask)
-    int p[VPL];  // line prefix of edge weights
+    int p[VPL];  // prefix of the line's edge weights
 };
 
 template <int KIND, int VPL, bool ROWS, class Map>
-__device__ __forceinline__ void load_line(const PropArgs& a, const Map& map, int src, bool first,
-                                          int l, int len, int lane, Line<VPL>& L) {
+__device__ __forceinline__ void load_line(const PropArgs& a, const Map& map, int l, int len, int lane,
+                                          Line<VPL>& L) {
 #pragma unroll
     for (int k = 0; k < VPL; ++k) {
-        int pos = lane + 32 * k;
+        const int pos = VPL * lane + k;
         if (pos < len) {
-            int e = ROWS ? l * a.W + pos : pos * a.W + l;
-            if (first) {
-                bool seed = a.seed_flags ? (a.seed_flags[e] != 0) : (e == src);
-                L.o[k] = seed ? 0 : PINF;
-            } else {
-                L.o[k] = ROWS ? map.ld(l, pos) : map.ld(pos, l);
-            }
+            const int e = ROWS ? l * a.W + pos : pos * a.W + l;
+            L.o[k] = ROWS ? map.ld(l, pos) : map.ld(pos, l);
             L.f[k] = __ldg(a.f + e);
-            if (KIND == 0) {
-                const int* P = ROWS ? a.Prow : a.Pcol;
-                L.p[k] = __ldg(P + l * len + pos);
-            } else {
-                L.p[k] = 2 * pos;
-            }
+            L.p[k] = KIND == 0 ? __ldg((ROWS ? a.Prow : a.Pcol) + l * len + pos) : 2 * pos;
         } else {
             L.o[k] = PINF;
             L.f[k] = 0;
@@ -82,41 +79,37 @@ __device__ __forceinline__ void load_line(const PropArgs& a, const Map& map, int
     }
 }
 
-// Value of the pixel one position before (UP) or after (!UP) each held pixel,
-// taken from another lane; `edge` fills the ends of the line.
-template <int VPL, bool UP>
-__device__ __forceinline__ void rotate(const int (&v)[VPL], int (&out)[VPL], int lane, int edge) {
-    int r[VPL];
-#pragma unroll
-    for (int k = 0; k < VPL; ++k) r[k] = __shfl_sync(FULL, v[k], UP ? (lane + 31) & 31 : (lane + 1) & 31);
-#pragma unroll
-    for (int k = 0; k < VPL; ++k) {
-        if (UP) out[k] = lane == 0 ? (k > 0 ? r[k - 1] : edge) : r[k];
-        else out[k] = lane == 31 ? (k + 1 < VPL ? r[k + 1] : edge) : r[k];
-    }
-}
-
+// One sweep over all lines in one direction; true if this warp lowered
+// (or may have lowered) some value.
 template <int CONN, int KIND, int VPL, bool ROWS, class Map>
-__device__ bool sweep(const PropArgs& a, const Map& map, int src, bool first, int dir, int lane) {
+__device__ bool sweep(const PropArgs& a, const Map& map, int dir, int lane) {
     const int nlines = ROWS ? a.H : a.W;
     const int len = ROWS ? a.W : a.H;
     int l = dir > 0 ? 0 : nlines - 1;
     Line<VPL> cur, nxt;
-    load_line<KIND, VPL, ROWS, Map>(a, map, src, first, l, len, lane, cur);
+    load_line<KIND, VPL, ROWS, Map>(a, map, l, len, lane, cur);
     int dp[VPL], fp[VPL];
 #pragma unroll
     for (int k = 0; k < VPL; ++k) { dp[k] = PINF; fp[k] = 0; }
     bool changed = false;
     for (int i = 0; i < nlines; ++i, l += dir) {
-        if (i + 1 < nlines) load_line<KIND, VPL, ROWS, Map>(a, map, src, first, l + dir, len, lane, nxt);
+        if (i + 1 < nlines) load_line<KIND, VPL, ROWS, Map>(a, map, l + dir, len, lane, nxt);
+        bool valid[VPL], freep[VPL];
+#pragma unroll
+        for (int k = 0; k < VPL; ++k) {
+            valid[k] = VPL * lane + k < len;
+            freep[k] = valid[k] && (KIND == 0 || cur.f[k] != 0);
+        }
         // 1. relax from the previous line
-        int dl[VPL], dr[VPL], fl[VPL], fr[VPL];
+        int dl0 = PINF, dr0 = PINF, fl0 = 0, fr0 = 0;
         if (CONN == 8) {
-            rotate<VPL, true>(dp, dl, lane, PINF);
-            rotate<VPL, false>(dp, dr, lane, PINF);
+            dl0 = __shfl_up_sync(FULL, dp[VPL - 1], 1);
+            dr0 = __shfl_down_sync(FULL, dp[0], 1);
+            if (lane == 0) dl0 = PINF;
+            if (lane == 31) dr0 = PINF;
             if (KIND == 0) {
-                rotate<VPL, true>(fp, fl, lane, 0);
-                rotate<VPL, false>(fp, fr, lane, 0);
+                fl0 = __shfl_up_sync(FULL, fp[VPL - 1], 1);
+                fr0 = __shfl_down_sync(FULL, fp[0], 1);
             }
         }
         int v[VPL];
@@ -124,101 +117,87 @@ __device__ bool sweep(const PropArgs& a, const Map& map, int src, bool first, in
         for (int k = 0; k < VPL; ++k) {
             int best = cur.o[k];
             if (KIND == 0) {
-                int fc1 = cur.f[k] + 1;
+                const int fc1 = cur.f[k] + 1;
                 best = min(best, dp[k] + fp[k] + fc1);
                 if (CONN == 8) {
-                    best = min(best, dl[k] + fl[k] + fc1);
-                    best = min(best, dr[k] + fr[k] + fc1);
+                    const int dl = k > 0 ? dp[k - 1] : dl0, fl = k > 0 ? fp[k - 1] : fl0;
+                    const int dr = k + 1 < VPL ? dp[k + 1] : dr0, fr = k + 1 < VPL ? fp[k + 1] : fr0;
+                    best = min(best, min(dl + fl, dr + fr) + fc1);
                 }
             } else {
                 best = min(best, dp[k] + 2);
-                if (CONN == 8) best = min(best, min(dl[k], dr[k]) + 2);
-                if (!cur.f[k]) best = PINF;  // obstacles keep no distance
-            }
-            v[k] = (lane + 32 * k < len) ? best : PINF;
-        }
-        // 2. close the line: prefix-min of v - P and suffix-min of v + P
-        int x[VPL], y[VPL];
-#pragma unroll
-        for (int k = 0; k < VPL; ++k) { x[k] = v[k] - cur.p[k]; y[k] = v[k] + cur.p[k]; }
-        unsigned ob[VPL];
-        if (KIND == 1) {
-#pragma unroll
-            for (int k = 0; k < VPL; ++k) ob[k] = __ballot_sync(FULL, !(lane + 32 * k < len && cur.f[k]));
-        }
-        bool need = false;
-        {
-            int xl[VPL], yr[VPL];
-            rotate<VPL, true>(x, xl, lane, PINF);
-            rotate<VPL, false>(y, yr, lane, PINF);
-#pragma unroll
-            for (int k = 0; k < VPL; ++k)
-                need |= (lane + 32 * k < len) && (KIND == 0 || cur.f[k]) && (xl[k] < x[k] || yr[k] < y[k]);
-        }
-        int d[VPL];
-        if (__any_sync(FULL, need)) {
-            int sx[VPL], sy[VPL];
-#pragma unroll
-            for (int k = 0; k < VPL; ++k) { sx[k] = x[k]; sy[k] = y[k]; }
-#pragma unroll
-            for (int delta = 1; delta < 32; delta <<= 1) {
-#pragma unroll
-                for (int k = 0; k < VPL; ++k) {
-                    int t = __shfl_up_sync(FULL, sx[k], delta);
-                    int u = __shfl_down_sync(FULL, sy[k], delta);
-                    bool okx = lane >= delta, oky = lane + delta < 32;
-                    if (KIND == 1) {
-                        // combine only inside a run of free pixels
-                        unsigned m = (1u << delta) - 1u;
-                        okx = okx && (((ob[k] >> (okx ? lane - delta : 0)) & m) == 0u);
-                        oky = oky && (((ob[k] >> (oky ? lane + 1 : 0)) & m) == 0u);
-                    }
-                    if (okx) sx[k] = min(sx[k], t);
-                    if (oky) sy[k] = min(sy[k], u);
+                if (CONN == 8) {
+                    const int dl = k > 0 ? dp[k - 1] : dl0;
+                    const int dr = k + 1 < VPL ? dp[k + 1] : dr0;
+                    best = min(best, min(dl, dr) + 2);
                 }
             }
-            // chain the 32-pixel chunks
-            int carry = PINF;
-#pragma unroll
-            for (int k = 0; k < VPL; ++k) {
-                bool ok = true;
-                if (KIND == 1)
-                    ok = k > 0 && !((ob[k - 1] >> 31) & 1u) && ((ob[k] & ((1u << lane) - 1u)) == 0u);
-                if (ok) sx[k] = min(sx[k], carry);
-                carry = __shfl_sync(FULL, sx[k], 31);
-            }
-            carry = PINF;
-#pragma unroll
-            for (int k = VPL - 1; k >= 0; --k) {
-                bool ok = true;
-                if (KIND == 1) {
-                    unsigned after = lane == 31 ? 0u : (ob[k] >> (lane + 1));
-                    ok = k + 1 < VPL && !(ob[k + 1] & 1u) && after == 0u;
-                }
-                if (ok) sy[k] = min(sy[k], carry);
-                carry = __shfl_sync(FULL, sy[k], 0);
-            }
-#pragma unroll
-            for (int k = 0; k < VPL; ++k) {
-                int r = min(v[k], min(sx[k] + cur.p[k], sy[k] - cur.p[k]));
-                if (KIND == 1 && !cur.f[k]) r = PINF;
-                d[k] = (lane + 32 * k < len) ? r : PINF;
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < VPL; ++k) d[k] = v[k];
+            v[k] = freep[k] ? best : PINF;
         }
-        // store what changed (everything on the first sweep)
+        // 2. close the line inside each lane
+        int sx[VPL], sy[VPL], d[VPL];
 #pragma unroll
         for (int k = 0; k < VPL; ++k) {
-            int pos = lane + 32 * k;
-            if (pos < len) {
-                bool ch = d[k] != cur.o[k];
-                changed |= ch;
-                if (ch || first) {
-                    if (ROWS) map.st(l, pos, d[k]);
-                    else map.st(pos, l, d[k]);
-                }
+            const int x = freep[k] ? v[k] - cur.p[k] : BIGX;
+            sx[k] = (KIND == 1 && !freep[k]) ? BIGX : min(k > 0 ? sx[k - 1] : BIGX, x);
+        }
+#pragma unroll
+        for (int k = VPL - 1; k >= 0; --k) {
+            const int y = freep[k] ? v[k] + cur.p[k] : BIGY;
+            sy[k] = (KIND == 1 && !freep[k]) ? BIGY : min(k + 1 < VPL ? sy[k + 1] : BIGY, y);
+        }
+#pragma unroll
+        for (int k = 0; k < VPL; ++k)
+            d[k] = freep[k] ? min(v[k], min(sx[k] + cur.p[k], sy[k] - cur.p[k])) : PINF;
+        // does a value have to cross a lane boundary?
+        const int xl = freep[VPL - 1] ? d[VPL - 1] - cur.p[VPL - 1] : BIGX;
+        const int yf = freep[0] ? d[0] + cur.p[0] : BIGY;
+        const int xl_left = __shfl_up_sync(FULL, xl, 1);
+        const int yf_right = __shfl_down_sync(FULL, yf, 1);
+        const bool need = (lane > 0 && freep[0] && xl_left < d[0] - cur.p[0]) ||
+                          (lane < 31 && freep[VPL - 1] && yf_right < d[VPL - 1] + cur.p[VPL - 1]);
+        if (__any_sync(FULL, need)) {
+            // exclusive prefix-min of the lane totals of v - P (suffix-min of
+            // v + P); on a mask, runs of free pixels are separate segments
+            int tx = sx[VPL - 1], ty = sy[0];
+            bool hx = false, hy = false;  // lane holds a segment start (mask)
+            int first_ob = VPL, last_ob = -1;
+            if (KIND == 1) {
+#pragma unroll
+                for (int k = VPL - 1; k >= 0; --k) if (!freep[k]) first_ob = k;
+#pragma unroll
+                for (int k = 0; k < VPL; ++k) if (!freep[k]) last_ob = k;
+                hx = hy = first_ob < VPL;
+            }
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int tx2 = __shfl_up_sync(FULL, tx, o);
+                const int ty2 = __shfl_down_sync(FULL, ty, o);
+                const bool hx2 = __shfl_up_sync(FULL, hx, o);
+                const bool hy2 = __shfl_down_sync(FULL, hy, o);
+                if (lane >= o && !hx) { tx = min(tx, tx2); hx = hx2; }
+                if (lane + o < 32 && !hy) { ty = min(ty, ty2); hy = hy2; }
+            }
+            int ex = __shfl_up_sync(FULL, tx, 1);
+            int ey = __shfl_down_sync(FULL, ty, 1);
+            if (lane == 0) ex = BIGX;
+            if (lane == 31) ey = BIGY;
+#pragma unroll
+            for (int k = 0; k < VPL; ++k) {
+                if (!freep[k]) continue;
+                const int px = (KIND == 1 && k > first_ob) ? sx[k] : min(ex, sx[k]);
+                const int py = (KIND == 1 && k < last_ob) ? sy[k] : min(ey, sy[k]);
+                d[k] = min(v[k], min(px + cur.p[k], py - cur.p[k]));
+            }
+        }
+        // lower the map where this line improved
+#pragma unroll
+        for (int k = 0; k < VPL; ++k) {
+            if (freep[k] && d[k] < cur.o[k]) {
+                changed = true;
+                const int pos = VPL * lane + k;
+                if (ROWS) map.lower(l, pos, d[k]);
+                else map.lower(pos, l, d[k]);
             }
             dp[k] = d[k];
             fp[k] = cur.f[k];
@@ -228,99 +207,112 @@ __device__ bool sweep(const PropArgs& a, const Map& map, int src, bool first, in
     return __any_sync(FULL, changed);
 }
 
-// Sweeps until the fixpoint; returns the number of sweeps.
 template <int CONN, int KIND, int VPL, class Map>
-__device__ int drive(const PropArgs& a, const Map& map, int src, int lane) {
-    int nsweep = 0, run = 0;
+__device__ void run_block(const PropArgs& a, const Map& map, int* s_flag, int* s_rounds) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int round = 0;
     for (;;) {
-        const bool first = nsweep == 0;
         bool ch;
-        switch (nsweep & 3) {
-            case 0: ch = sweep<CONN, KIND, VPL, true>(a, map, src, first, +1, lane); break;
-            case 1: ch = sweep<CONN, KIND, VPL, true>(a, map, src, first, -1, lane); break;
-            case 2: ch = sweep<CONN, KIND, VPL, false>(a, map, src, first, +1, lane); break;
-            default: ch = sweep<CONN, KIND, VPL, false>(a, map, src, first, -1, lane); break;
+        switch (warp) {
+            case 0: ch = sweep<CONN, KIND, VPL, true, Map>(a, map, +1, lane); break;
+            case 1: ch = sweep<CONN, KIND, VPL, true, Map>(a, map, -1, lane); break;
+            case 2: ch = sweep<CONN, KIND, VPL, false, Map>(a, map, +1, lane); break;
+            default: ch = sweep<CONN, KIND, VPL, false, Map>(a, map, -1, lane); break;
         }
-        __syncwarp();
-        run = (ch || first) ? 0 : run + 1;
-        ++nsweep;
-        // Two unchanged sweeps of an opposite pair (down+up, right+left) test
-        // every edge; for 4-connectivity any two distinct sweeps do. Three in
-        // a row always contain an opposite pair.
-        const bool done = CONN == 4 ? run >= 2 : (run >= 3 || (run >= 2 && ((nsweep - 1) & 1)));
-        if (done) break;
-        if (nsweep >= a.max_sweeps) {
-            if (lane == 0) atomicOr(a.status, ST_NOT_CONVERGED);
+        if (lane == 0 && ch) s_flag[round & 1] = 1;
+        __syncthreads();
+        const bool any = s_flag[round & 1] != 0;
+        if (threadIdx.x == 0) s_flag[(round + 1) & 1] = 0;
+        ++round;
+        if (!any) break;
+        if (round * PWARPS >= a.max_sweeps) {
+            if (threadIdx.x == 0) atomicOr(a.status, ST_NOT_CONVERGED);
             break;
         }
+        __syncthreads();
     }
-    return nsweep;
+    if (threadIdx.x == 0) *s_rounds = round;
 }
 
 __device__ __forceinline__ int finish(const PropArgs& a, int v) {
     return (a.convert && v >= PINF) ? (int)UNREACH : v;
 }
 
-// Map in shared memory: one warp per block.
+__device__ __forceinline__ bool is_seed(const PropArgs& a, int src, int p) {
+    return a.seed_flags ? a.seed_flags[p] != 0 : p == src;
+}
+
+// Map in shared memory; one block of PWARPS warps per job.
 template <int CONN, int KIND, int VPL>
-__global__ void __launch_bounds__(32) k_propagate_smem(PropArgs a, int pitch) {
+__global__ void __launch_bounds__(32 * PWARPS) k_propagate_smem(PropArgs a, int pitch) {
     extern __shared__ int smap[];
-    const int lane = threadIdx.x;
+    __shared__ int s_flag[2], s_rounds;
     const int j = blockIdx.x;
     const int njobs = a.njobs_dev ? *a.njobs_dev : a.njobs;
     if (j >= njobs) return;
     const int src = a.sources ? a.sources[j] : -1;
     int* out = a.map_base + (size_t)(a.map_row ? a.map_row[j] : j) * (size_t)a.N;
+    for (int p = threadIdx.x; p < a.N; p += blockDim.x) {
+        const int r = p / a.W, c = p - r * a.W;
+        smap[r * pitch + c] = is_seed(a, src, p) ? 0 : PINF;
+    }
+    if (threadIdx.x == 0) { s_flag[0] = 0; s_flag[1] = 0; }
+    __syncthreads();
     const SmemMap map{smap, pitch};
-    const int ns = drive<CONN, KIND, VPL>(a, map, src, lane);
-    if (lane == 0 && a.sweeps) atomicAdd(a.sweeps, (unsigned long long)ns);
-    // coalesced store of the finished row, four pixels per lane per step
+    run_block<CONN, KIND, VPL>(a, map, s_flag, &s_rounds);
+    __syncthreads();
+    if (threadIdx.x == 0 && a.sweeps) atomicAdd(a.sweeps, (unsigned long long)s_rounds * PWARPS);
+    // finished row: coalesced 128-bit stores
     if ((a.N & 3) == 0 && (a.W & 3) == 0) {
         int4* o4 = reinterpret_cast<int4*>(out);
-        for (int q = lane; q < a.N / 4; q += 32) {
+        for (int q = threadIdx.x; q < a.N / 4; q += blockDim.x) {
             const int p = 4 * q, r = p / a.W, c = p - r * a.W;
             const int* m = smap + r * pitch + c;
             o4[q] = make_int4(finish(a, m[0]), finish(a, m[1]), finish(a, m[2]), finish(a, m[3]));
         }
     } else {
-        for (int p = lane; p < a.N; p += 32) {
+        for (int p = threadIdx.x; p < a.N; p += blockDim.x) {
             const int r = p / a.W, c = p - r * a.W;
             out[p] = finish(a, smap[r * pitch + c]);
         }
     }
-    __syncwarp();
-    if (lane == 0 && a.convert && src >= 0 && KIND == 1 && !a.f[src]) out[src] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0 && a.convert && src >= 0 && KIND == 1 && !a.f[src]) out[src] = 0;
 }
 
-// Map in global memory (images too large for shared memory).
+// Map in global memory (the output row itself), for images whose map does
+// not fit in shared memory.
 template <int CONN, int KIND, int VPL>
-__global__ void k_propagate_glob(PropArgs a) {
-    const int lane = threadIdx.x & 31;
-    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+__global__ void __launch_bounds__(32 * PWARPS) k_propagate_glob(PropArgs a) {
+    __shared__ int s_flag[2], s_rounds;
+    const int j = blockIdx.x;
     const int njobs = a.njobs_dev ? *a.njobs_dev : a.njobs;
     if (j >= njobs) return;
     const int src = a.sources ? a.sources[j] : -1;
     int* map = a.map_base + (size_t)(a.map_row ? a.map_row[j] : j) * (size_t)a.N;
+    for (int p = threadIdx.x; p < a.N; p += blockDim.x) map[p] = is_seed(a, src, p) ? 0 : PINF;
+    if (threadIdx.x == 0) { s_flag[0] = 0; s_flag[1] = 0; }
+    __threadfence_block();
+    __syncthreads();
     const GlobMap gm{map, a.W};
-    const int ns = drive<CONN, KIND, VPL>(a, gm, src, lane);
-    if (lane == 0 && a.sweeps) atomicAdd(a.sweeps, (unsigned long long)ns);
+    run_block<CONN, KIND, VPL>(a, gm, s_flag, &s_rounds);
+    __syncthreads();
+    if (threadIdx.x == 0 && a.sweeps) atomicAdd(a.sweeps, (unsigned long long)s_rounds * PWARPS);
     if (a.convert) {
-        for (int p = lane; p < a.N; p += 32) {
-            int v = ld_cg(map + p);
+        for (int p = threadIdx.x; p < a.N; p += blockDim.x) {
+            const int v = ld_cg(map + p);
             if (v >= PINF) map[p] = (int)UNREACH;
         }
-        __syncwarp();
-        if (lane == 0 && src >= 0 && KIND == 1 && !a.f[src]) map[src] = 0;
+        __syncthreads();
+        if (threadIdx.x == 0 && src >= 0 && KIND == 1 && !a.f[src]) map[src] = 0;
     }
 }
 
 constexpr int SMEM_MAP_LIMIT = 200 * 1024;
 
-int smem_pitch(int W) { return W | 1; }
-
 template <int CONN, int KIND, int VPL>
-cudaError_t launch_one(const PropArgs& a, int grid, int wpb, cudaStream_t st) {
-    const int pitch = smem_pitch(a.W);
+cudaError_t launch_one(const PropArgs& a, int jobs, cudaStream_t st) {
+    const int pitch = a.W | 1;  // odd pitch: row and column lines avoid bank conflicts
     const size_t smem = (size_t)a.H * pitch * sizeof(int);
     if (smem <= (size_t)SMEM_MAP_LIMIT) {
         static bool attr = false;
@@ -329,22 +321,20 @@ cudaError_t launch_one(const PropArgs& a, int grid, int wpb, cudaStream_t st) {
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_MAP_LIMIT);
             attr = true;
         }
-        // one warp (one job) per block
-        const int jobs = grid * wpb;
-        k_propagate_smem<CONN, KIND, VPL><<<jobs, 32, smem, st>>>(a, pitch);
+        k_propagate_smem<CONN, KIND, VPL><<<jobs, 32 * PWARPS, smem, st>>>(a, pitch);
     } else {
-        k_propagate_glob<CONN, KIND, VPL><<<grid, 32 * wpb, 0, st>>>(a);
+        k_propagate_glob<CONN, KIND, VPL><<<jobs, 32 * PWARPS, 0, st>>>(a);
     }
     return cudaGetLastError();
 }
 
 template <int CONN, int KIND>
-cudaError_t launch_vpl(const PropArgs& a, int vpl, int grid, int wpb, cudaStream_t st) {
+cudaError_t launch_vpl(const PropArgs& a, int vpl, int jobs, cudaStream_t st) {
     switch (vpl) {
-        case 1: return launch_one<CONN, KIND, 1>(a, grid, wpb, st);
-        case 2: return launch_one<CONN, KIND, 2>(a, grid, wpb, st);
-        case 4: return launch_one<CONN, KIND, 4>(a, grid, wpb, st);
-        case 8: return launch_one<CONN, KIND, 8>(a, grid, wpb, st);
+        case 1: return launch_one<CONN, KIND, 1>(a, jobs, st);
+        case 2: return launch_one<CONN, KIND, 2>(a, jobs, st);
+        case 4: return launch_one<CONN, KIND, 4>(a, jobs, st);
+        case 8: return launch_one<CONN, KIND, 8>(a, jobs, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -360,10 +350,11 @@ int prop_vpl(int side) {
 }
 
 cudaError_t launch_propagate(const PropArgs& a, int conn, int kind, int grid, int wpb, cudaStream_t st) {
-    int vpl = prop_vpl(a.H > a.W ? a.H : a.W);
-    if (grid <= 0) return cudaSuccess;
-    if (conn == 8) return kind == 0 ? launch_vpl<8, 0>(a, vpl, grid, wpb, st) : launch_vpl<8, 1>(a, vpl, grid, wpb, st);
-    return kind == 0 ? launch_vpl<4, 0>(a, vpl, grid, wpb, st) : launch_vpl<4, 1>(a, vpl, grid, wpb, st);
+    const int vpl = prop_vpl(a.H > a.W ? a.H : a.W);
+    const int jobs = grid * wpb;  // one block per job
+    if (jobs <= 0) return cudaSuccess;
+    if (conn == 8) return kind == 0 ? launch_vpl<8, 0>(a, vpl, jobs, st) : launch_vpl<8, 1>(a, vpl, jobs, st);
+    return kind == 0 ? launch_vpl<4, 0>(a, vpl, jobs, st) : launch_vpl<4, 1>(a, vpl, jobs, st);
 }
 
 // ---------------------------------------------------------------------------
