@@ -40,6 +40,8 @@ def _args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--side", type=int, default=128, help="image side (128 = the workload)")
     ap.add_argument("--no-extras", action="store_true", help="skip the side measurements")
+    ap.add_argument("--timed-only", action="store_true",
+                    help="warm-up and timed steps only (for profiler runs); prints no JSON")
     return ap.parse_args()
 
 
@@ -213,6 +215,12 @@ def run_ours(a):
         step_ms.append((e0, e1))
     ev_b.record(stream)
     barrier()
+    if a.timed_only:
+        clocks.stop()
+        im.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return
     total_ms = ev_a.elapsed_time(ev_b)
     launches = im.kernel_launches - l0
     clk = clocks.stop()

@@ -81,7 +81,8 @@ typedef struct {
     int B;             /* sources per round, 1..1024 (0 = 32) */
     uint64_t seed;     /* seed of the spiral order's draws */
     size_t mem_budget; /* bytes of device memory a call may use (0 = no limit) */
-    int tile_h, tile_w;/* reserved (0) */
+    int sweep_phases;  /* warps per sweep direction in a propagation: 0 = auto, 1 or 2 */
+    int reserved;      /* 0 */
     int checked;       /* reserved (0) */
     void *stream;      /* cudaStream_t the calls run on (NULL = default stream) */
 } gapsp_opts;
@@ -101,6 +102,8 @@ typedef struct {
                                       sources in selection order (capacity sources_cap) */
     uint64_t sources_cap;
     uint64_t sweeps;               /* directional sweeps run by all propagations */
+    uint64_t lines;                /* image lines those sweeps processed (the rest were
+                                      skipped as unchanged) */
 } gapsp_stats;
 
 /* Fills *opts with the defaults (conn 8, grey, B 32, seed 0, no budget). */
@@ -162,13 +165,19 @@ uint64_t gapsp_kernel_launches(const gapsp_handle *h);
  * gapsp_profile_read returns, per kernel, the summed event time (ms) and the
  * number of launches since the last read (then resets). Enabling adds two
  * event records per launch; leave it off for throughput timing.
- * Kernel ids: 0 selection (c), 1 propagation (a), 2 parents (a'),
- * 3 segments (a'), 4 tree fill (b), 5 init, 6 extrema pre-pass helpers.
+ * Kernel ids: 0 selection (c), 1 propagation (a), 2 tree: parents,
+ * segments and depths (a'), 3 unused, 4 tree fill (b), 5 init, 6 extrema
+ * pre-pass helpers, 7 unused, 8 fill-count update.
  * ms and launches: caller-owned arrays of GAPSP_NUM_KERNELS entries.
  */
-#define GAPSP_NUM_KERNELS 7
+#define GAPSP_NUM_KERNELS 9
 gapsp_status gapsp_profile_enable(gapsp_handle *h, int enable);
 gapsp_status gapsp_profile_read(gapsp_handle *h, double *ms, uint64_t *launches);
+/* Like gapsp_profile_read, and also returns the individual launches in
+ * launch order: kind[i] (kernel id) and dur_ms[i], for i < min(cap, count);
+ * *count receives the number of launches recorded. */
+gapsp_status gapsp_profile_trace(gapsp_handle *h, double *ms, uint64_t *launches,
+                                 int32_t *kind, float *dur_ms, uint64_t cap, uint64_t *count);
 
 #ifdef __cplusplus
 }

@@ -20,7 +20,7 @@ from . import _build
 UNREACH = 0xFFFFFFFF
 ORDERS = {"naive": 0, "spiral": 1, "minfill": 2}
 KINDS = {"grey": 0, "mask": 1}
-KERNELS = ("select", "propagate", "parents", "segments", "fill", "init", "prepass")
+KERNELS = ("select", "propagate", "tree", "unused3", "fill", "init", "prepass", "unused7", "recount")
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "memory budget exceeded",
           4: "CUDA runtime error", 5: "propagation did not converge", 6: "round limit exceeded",
           7: "cancelled"}
@@ -37,7 +37,7 @@ class GapspError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("conn", ctypes.c_int), ("kind", ctypes.c_int), ("B", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("mem_budget", ctypes.c_size_t),
-                ("tile_h", ctypes.c_int), ("tile_w", ctypes.c_int), ("checked", ctypes.c_int),
+                ("sweep_phases", ctypes.c_int), ("reserved", ctypes.c_int), ("checked", ctypes.c_int),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -48,7 +48,7 @@ class Stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double),
                 ("round_new", ctypes.POINTER(ctypes.c_uint64)), ("round_new_cap", ctypes.c_uint64),
                 ("sources", ctypes.POINTER(ctypes.c_int32)), ("sources_cap", ctypes.c_uint64),
-                ("sweeps", ctypes.c_uint64)]
+                ("sweeps", ctypes.c_uint64), ("lines", ctypes.c_uint64)]
 
 
 def library_path() -> str:
@@ -84,6 +84,8 @@ def load(build_if_missing: bool = True):
     lib.gapsp_profile_enable.restype = ctypes.c_int
     lib.gapsp_profile_read.argtypes = [P, P, P]
     lib.gapsp_profile_read.restype = ctypes.c_int
+    lib.gapsp_profile_trace.argtypes = [P, P, P, P, P, ctypes.c_uint64, P]
+    lib.gapsp_profile_trace.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -120,7 +122,7 @@ class Image:
     """A handle on one image (gapsp_create / gapsp_destroy)."""
 
     def __init__(self, img, conn: int = 8, kind: str = "grey", mask=None, B: int = 32,
-                 seed: int = 0, mem_budget: int = 0, stream=None):
+                 seed: int = 0, mem_budget: int = 0, stream=None, sweep_phases: int = 0):
         lib = load()
         self._lib = lib
         self._h = ctypes.c_void_p()
@@ -140,6 +142,7 @@ class Image:
         o.conn, o.kind, o.B = conn, KINDS[kind], B
         o.seed = seed & (2 ** 64 - 1)
         o.mem_budget = mem_budget
+        o.sweep_phases = sweep_phases
         o.stream = _torch_stream(stream)
         self.H, self.W, self.N, self.conn, self.kind, self.B = H, W, H * W, conn, kind, B
         rc = lib.gapsp_create(_ptr(img_a), H, W, _ptr(mask_a), ctypes.byref(o), ctypes.byref(self._h))
@@ -183,6 +186,20 @@ class Image:
             raise GapspError(rc, "gapsp_profile_read")
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNELS)}
 
+    def profile_trace(self, cap: int = 1 << 16):
+        """Per-launch (kernel name, ms) in launch order, since the last read."""
+        ms = np.zeros(len(KERNELS), dtype=np.float64)
+        n = np.zeros(len(KERNELS), dtype=np.uint64)
+        kind = np.zeros(cap, dtype=np.int32)
+        dur = np.zeros(cap, dtype=np.float32)
+        cnt = np.zeros(1, dtype=np.uint64)
+        rc = self._lib.gapsp_profile_trace(self._h, _ptr(ms), _ptr(n), _ptr(kind), _ptr(dur),
+                                           cap, _ptr(cnt))
+        if rc != 0:
+            raise GapspError(rc, "gapsp_profile_trace")
+        m = min(int(cnt[0]), cap)
+        return [(KERNELS[int(kind[i])], float(dur[i])) for i in range(m)]
+
     def all_pairs(self, order: str = "minfill", out=None, want_log: bool = False):
         """Fills the N x N array (gapsp_all_pairs). Returns (D, stats dict)."""
         N = self.N
@@ -204,7 +221,7 @@ class Image:
         stats = {"propagations": st.propagations, "prepass_propagations": st.prepass_propagations,
                  "distance_ops": st.distance_ops, "new_pairs": st.new_pairs, "rounds": st.rounds,
                  "prefilled_pairs": st.prefilled_pairs, "ms_total": st.ms_total,
-                 "sweeps": st.sweeps}
+                 "sweeps": st.sweeps, "lines": st.lines}
         if want_log:
             stats["round_new"] = rn[:st.rounds].copy()
             stats["sources"] = sl[:st.propagations].copy()

@@ -14,7 +14,7 @@
 #include <new>
 #include <vector>
 
-#include "../../include/gapsp.h"
+#include "gapsp.h"
 #include "common.cuh"
 #include "internal.h"
 
@@ -26,6 +26,7 @@ struct gapsp_handle {
     size_t budget = 0;
     cudaStream_t st = nullptr;
     int tiles_w = 0, tiles_h = 0, words = 0;
+    int sweep_phases = 0;
     uint64_t launches = 0;
     // image
     uint8_t* f = nullptr;
@@ -39,10 +40,13 @@ struct gapsp_handle {
     // fill state
     bool fill_ready = false;
     uint32_t* cnt = nullptr;
+    uint32_t* cnt_base = nullptr;
+    uint8_t* dirty = nullptr;
     unsigned long long* marks = nullptr;
     int32_t* parent = nullptr;
-    int32_t* seg_exit = nullptr;
-    unsigned long long* seg_mask = nullptr;
+    ulonglong2* seg = nullptr;
+    int32_t* jmp = nullptr;
+    int32_t* acc = nullptr;
     int32_t* sel = nullptr;
     int* nsel = nullptr;
     int* cursor = nullptr;
@@ -150,22 +154,26 @@ PropArgs base_prop(const gapsp_handle* h) {
     a.Pcol = h->Pcol;
     a.status = h->status;
     a.max_sweeps = 4 * (h->N + 2);
+    a.phases = h->sweep_phases ? h->sweep_phases : 2;
     return a;
 }
 
 size_t fill_state_bytes(const gapsp_handle* h) {
     const size_t N = h->N, B = h->B;
-    return N * h->words * 8 + B * N * (4 + 4 + 8) + N * (4 + 4 + 4 + 4 + 8 + 8 + 1 + 4) + 4096;
+    return N * h->words * 8 + B * N * (4 + 16 + 16) + N * (4 + 4 + 4 + 4 + 8 + 8 + 1 + 4) + 4096;
 }
 
 gapsp_status ensure_fill_state(gapsp_handle* h) {
     if (h->fill_ready) return GAPSP_OK;
     const size_t N = h->N, B = h->B;
     CK(dalloc(&h->cnt, N));
+    CK(dalloc(&h->cnt_base, N));
+    CK(dalloc(&h->dirty, N));
     CK(dalloc(&h->marks, N * h->words));
     CK(dalloc(&h->parent, B * N));
-    CK(dalloc(&h->seg_exit, B * N));
-    CK(dalloc(&h->seg_mask, B * N));
+    CK(dalloc(&h->seg, B * N));
+    CK(dalloc(&h->jmp, 2 * B * N));
+    CK(dalloc(&h->acc, 2 * B * N));
     CK(dalloc(&h->sel, B));
     CK(dalloc(&h->nsel, 1));
     CK(dalloc(&h->cursor, 1));
@@ -188,7 +196,7 @@ gapsp_status ensure_fill_state(gapsp_handle* h) {
 void free_all(gapsp_handle* h) {
     dfree(h->f); dfree(h->Prow); dfree(h->Pcol); dfree(h->bound); dfree(h->comp);
     dfree(h->comp_size); dfree(h->status); dfree(h->changed);
-    dfree(h->cnt); dfree(h->marks); dfree(h->parent); dfree(h->seg_exit); dfree(h->seg_mask);
+    dfree(h->cnt); dfree(h->cnt_base); dfree(h->dirty); dfree(h->marks); dfree(h->parent); dfree(h->seg); dfree(h->jmp); dfree(h->acc);
     dfree(h->sel); dfree(h->nsel); dfree(h->cursor); dfree(h->done); dfree(h->seq); dfree(h->rank);
     dfree(h->stats); dfree(h->round_new); dfree(h->last_new); dfree(h->sel_log);
     dfree(h->emap); dfree(h->gmap); dfree(h->best); dfree(h->cen);
@@ -204,7 +212,7 @@ void free_all(gapsp_handle* h) {
     h->ev0 = h->ev1 = nullptr;
 }
 
-enum { K_SELECT = 0, K_PROP = 1, K_PARENTS = 2, K_SEGMENTS = 3, K_FILL = 4, K_INIT = 5, K_PRE = 6 };
+enum { K_SELECT = 0, K_PROP = 1, K_TREE = 2, K_FILL = 4, K_INIT = 5, K_PRE = 6, K_RECOUNT = 8 };
 
 cudaEvent_t pool_get(gapsp_handle* h) {
     if (!h->pool.empty()) {
@@ -282,6 +290,7 @@ gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask,
     if (o.conn != 4 && o.conn != 8) return GAPSP_E_INVALID;
     if (o.kind != GAPSP_GREY && o.kind != GAPSP_MASK) return GAPSP_E_INVALID;
     if (o.B < 1 || o.B > 1024) return GAPSP_E_INVALID;
+    if (o.sweep_phases < 0 || o.sweep_phases > 2) return GAPSP_E_INVALID;
     if (o.kind == GAPSP_GREY && !img) return GAPSP_E_INVALID;
     if (o.kind == GAPSP_MASK && !mask) return GAPSP_E_INVALID;
 
@@ -289,6 +298,7 @@ gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask,
     if (!h) return GAPSP_E_NOMEM;
     h->H = H; h->W = W; h->N = H * W; h->conn = o.conn; h->kind = o.kind; h->B = o.B;
     h->seed = o.seed; h->budget = o.mem_budget; h->st = (cudaStream_t)o.stream;
+    h->sweep_phases = o.sweep_phases;
     h->tiles_w = (W + 7) / 8; h->tiles_h = (H + 7) / 8; h->words = h->tiles_w * h->tiles_h;
     const size_t N = h->N;
     if (h->budget && N * 32 + 4096 > h->budget) { delete h; return GAPSP_E_BUDGET; }
@@ -383,7 +393,8 @@ gapsp_status gapsp_rows(gapsp_handle* h, const int32_t* sources, int K, uint32_t
     a.sources = h->src_dev;
     a.njobs = K;
     a.convert = h->kind == GAPSP_MASK;
-    const int wpb = K >= 608 ? 4 : 1;
+    if (!h->sweep_phases) a.phases = K > 304 ? 1 : 2;  // latency-bound when few sources
+    const int wpb = 1;
     {
         ProfScope ps(h, K_PROP, h->st);
         CK(launch_propagate(a, h->conn, h->kind, (K + wpb - 1) / wpb, wpb, h->st));
@@ -451,6 +462,8 @@ gapsp_status gapsp_all_pairs(gapsp_handle* h, gapsp_order order, uint32_t* D, ga
         ProfScope ps(h, K_INIT, s);
         CK(launch_init(ia, s));
     }
+    CK(cudaMemcpyAsync(h->cnt_base, h->cnt, N * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(h->dirty, 0, N, s));
     h->launches += 1;
 
     uint64_t prepass = 0;
@@ -499,8 +512,9 @@ gapsp_status gapsp_all_pairs(gapsp_handle* h, gapsp_order order, uint32_t* D, ga
     ta.H = h->H; ta.W = h->W; ta.N = h->N; ta.conn = h->conn; ta.kind = h->kind;
     ta.tiles_w = h->tiles_w; ta.words = h->words;
     ta.f = h->f; ta.D = Dd; ta.sel = h->sel; ta.nsel = h->nsel;
-    ta.parent = h->parent; ta.seg_exit = h->seg_exit; ta.seg_mask = h->seg_mask;
+    ta.parent = h->parent; ta.seg = h->seg; ta.jmp = h->jmp; ta.acc = h->acc;
     ta.marks = h->marks; ta.cnt = h->cnt; ta.Dw = Dd; ta.stats = h->stats;
+    ta.cnt_base = h->cnt_base; ta.dirty = h->dirty;
     {
         const size_t row_bytes = (size_t)h->words * 8;
         int rpb = (int)((96 * 1024) / row_bytes);
@@ -522,16 +536,16 @@ gapsp_status gapsp_all_pairs(gapsp_handle* h, gapsp_order order, uint32_t* D, ga
                 CK(launch_propagate(pa, h->conn, h->kind, h->B, 1, s));
             }
             {
-                ProfScope ps(h, K_PARENTS, s);
-                CK(launch_parents(ta, h->B, s));
-            }
-            {
-                ProfScope ps(h, K_SEGMENTS, s);
-                CK(launch_segments(ta, h->B, s));
+                ProfScope ps(h, K_TREE, s);
+                CK(launch_tree(ta, h->B, s));
             }
             {
                 ProfScope ps(h, K_FILL, s);
                 CK(launch_fill(ta, h->B, s));
+            }
+            {
+                ProfScope ps(h, K_RECOUNT, s);
+                CK(launch_recount(ta, s));
             }
             h->launches += 5;
         }
@@ -558,6 +572,7 @@ gapsp_status gapsp_all_pairs(gapsp_handle* h, gapsp_order order, uint32_t* D, ga
         st->rounds = hs[S_ROUNDS];
         st->prefilled_pairs = 0;
         st->sweeps = hs[S_SWEEPS];
+        st->lines = hs[S_LINES];
         float ms = 0.f;
         cudaEventElapsedTime(&ms, h->ev0, h->ev1);
         st->ms_total = ms;
@@ -590,19 +605,28 @@ gapsp_status gapsp_profile_enable(gapsp_handle* h, int enable) {
     return GAPSP_OK;
 }
 
-gapsp_status gapsp_profile_read(gapsp_handle* h, double* ms, uint64_t* launches) {
+gapsp_status gapsp_profile_trace(gapsp_handle* h, double* ms, uint64_t* launches, int32_t* kind,
+                                 float* dur_ms, uint64_t cap, uint64_t* count) {
     if (!h || !ms || !launches) return GAPSP_E_INVALID;
     for (int k = 0; k < GAPSP_NUM_KERNELS; ++k) { ms[k] = 0.0; launches[k] = 0; }
     CK(cudaStreamSynchronize(h->st));
+    uint64_t i = 0;
     for (auto& t : h->timed) {
         float e = 0.f;
         CK(cudaEventElapsedTime(&e, t.a, t.b));
         if (t.kind >= 0 && t.kind < GAPSP_NUM_KERNELS) { ms[t.kind] += e; launches[t.kind] += 1; }
+        if (kind && dur_ms && i < cap) { kind[i] = t.kind; dur_ms[i] = e; }
+        ++i;
         h->pool.push_back(t.a);
         h->pool.push_back(t.b);
     }
+    if (count) *count = i;
     h->timed.clear();
     return GAPSP_OK;
+}
+
+gapsp_status gapsp_profile_read(gapsp_handle* h, double* ms, uint64_t* launches) {
+    return gapsp_profile_trace(h, ms, launches, nullptr, nullptr, 0, nullptr);
 }
 
 }  // extern "C"

@@ -22,6 +22,7 @@ struct PropArgs {
     unsigned long long* sweeps; // optional: total sweeps run
     int max_sweeps;
     int convert;                // write UNREACH for pixels never reached
+    int phases;                 // warps per sweep direction (1 or 2)
 };
 
 // Picks the per-lane width and launches kernel (a).
@@ -46,17 +47,20 @@ struct TreeArgs {
     const int32_t* sel;         // selected sources
     const int* nsel;            // device count
     int32_t* parent;            // [B][N]
-    int32_t* seg_exit;          // [B][N]
-    unsigned long long* seg_mask;  // [B][N]
+    ulonglong2* seg;            // [B][N]: x = mask of the tile segment, y = exit vertex (+1)
+    int32_t* jmp;               // [2][B][N] scratch for the depth pointer jumping
+    int32_t* acc;               // [2][B][N] scratch for the depth pointer jumping
     unsigned long long* marks;  // [N][words]
     uint32_t* cnt;              // [N]
+    const uint32_t* cnt_base;   // [N] fill count at the start (1 + pairs no path joins)
+    uint8_t* dirty;             // [N] rows that gained marks this round
     uint32_t* Dw;               // writable array for new pairs
     unsigned long long* stats;  // StatSlot counters
     int rows_per_block;
 };
-cudaError_t launch_parents(const TreeArgs& a, int B, cudaStream_t st);
-cudaError_t launch_segments(const TreeArgs& a, int B, cudaStream_t st);
+cudaError_t launch_tree(const TreeArgs& a, int B, cudaStream_t st);
 cudaError_t launch_fill(const TreeArgs& a, int B, cudaStream_t st);
+cudaError_t launch_recount(const TreeArgs& a, cudaStream_t st);
 
 struct SelectArgs {
     int N, B, order;            // 0 naive / 1 spiral (sequence), 2 minfill

@@ -5,27 +5,32 @@
 // paper uses with a 3x3 neighbourhood (Sec. 3). Weights are w(p,q) = f(p) +
 // f(q) + 1 (grey) or 2 between free pixels (mask).
 //
-// One block of four warps owns one source (or one multi-source seed set).
-// Its distance map sits in shared memory (global memory for images too
-// large), initialised to 0 at the seeds and "unreached" elsewhere. The four
-// warps sweep the map concurrently, each in its own direction: rows
-// top-down, rows bottom-up, columns left-right, columns right-left. For
-// each line a warp
+// One block owns one source (or one multi-source seed set). Its distance
+// map sits in shared memory (global memory for images too large), set to 0
+// at the seeds and "unreached" elsewhere, next to two copies of the image
+// (row-major and column-major). Warps sweep the map concurrently, each in
+// its own direction (rows top-down, rows bottom-up, columns left-right,
+// columns right-left), one or two warps per direction starting half an
+// image apart. For each line a warp
 //   1. relaxes every pixel from the previous line it just finished (the
 //      three neighbours behind it for 8-connectivity, one for 4), then
 //   2. closes the line in both directions: with P the prefix sum of the
 //      line's edge weights, the best value along the line is
 //      min_c' v(c') + |P(c) - P(c')|, a prefix-min of v - P and a suffix-min
 //      of v + P. Lane j holds pixels VPL*j .. VPL*j+VPL-1, so the scans run
-//      inside the lane and need warp shuffles only when a boundary test
+//      inside the lane and use warp shuffles only when a boundary test
 //      shows that a value must cross from one lane to another,
-// and lowers the map with atomic minima. Every stored value is the cost of
-// a real path, so values only decrease towards the distances; the edge
-// weights are positive integers, so the fixpoint is unique and any schedule
-// reaches it. The block stops after a round (one sweep per warp) in which
-// no warp lowered anything: the map was then constant while every edge
-// direction was tested. Rounds are capped; hitting the cap sets a status
-// bit instead of looping on.
+// and lowers the map with atomic minima, flagging every line that a lowered
+// pixel belongs to (its own line and the crossing one). After the first
+// rounds most lines stop changing, and a warp skips a line when neither it
+// nor the line before it was flagged in the previous round.
+//
+// Every stored value is the cost of a real path, so values only decrease
+// towards the distances; weights are positive integers, so the fixpoint is
+// unique and any schedule reaches it. The block stops after a round (one
+// pass per warp) in which no warp lowered anything: the map was constant
+// while every edge direction was tested. Rounds are capped; hitting the cap
+// sets a status bit instead of looping on.
 #include "common.cuh"
 #include "internal.h"
 
@@ -33,7 +38,7 @@ namespace gapsp {
 
 namespace {
 
-constexpr int PWARPS = 4;                 // one warp per sweep direction
+constexpr int MAXWARPS = 8;               // 4 directions x up to 2 phases
 constexpr int BIGX = PINF;                // identity of the prefix-min of v - P
 constexpr int BIGY = PINF + (1 << 18);    // identity of the suffix-min of v + P
 
@@ -53,114 +58,137 @@ struct GlobMap {
     __device__ __forceinline__ void lower(int r, int c, int v) const { atomicMin(base + r * pitch + c, v); }
 };
 
-template <int VPL>
-struct Line {
-    int o[VPL];  // map value when loaded
-    int f[VPL];  // grey level (grey) or free flag (mask)
-    int p[VPL];  // prefix of the line's edge weights
+// Shared state of one block besides the map.
+struct Shared {
+    const uint8_t* fR;  // image, row-major
+    const uint8_t* fC;  // image, column-major
+    uint8_t* chR;       // [3][H]: row line lowered during round t (slot t % 3)
+    uint8_t* chC;       // [3][W]: column line lowered during round t
+    const int* Pb;      // [H + W][32]: prefix of the line's edge weights at each lane's first pixel
 };
 
-template <int KIND, int VPL, bool ROWS, class Map>
-__device__ __forceinline__ void load_line(const PropArgs& a, const Map& map, int l, int len, int lane,
-                                          Line<VPL>& L) {
-#pragma unroll
-    for (int k = 0; k < VPL; ++k) {
-        const int pos = VPL * lane + k;
-        if (pos < len) {
-            const int e = ROWS ? l * a.W + pos : pos * a.W + l;
-            L.o[k] = ROWS ? map.ld(l, pos) : map.ld(pos, l);
-            L.f[k] = __ldg(a.f + e);
-            L.p[k] = KIND == 0 ? __ldg((ROWS ? a.Prow : a.Pcol) + l * len + pos) : 2 * pos;
-        } else {
-            L.o[k] = PINF;
-            L.f[k] = 0;
-            L.p[k] = 0;
-        }
-    }
-}
-
-// One sweep over all lines in one direction; true if this warp lowered
-// (or may have lowered) some value.
+// One pass over all lines in one direction during round `round`; true if
+// this warp lowered some value. A line is skipped when neither it nor the
+// line before it was lowered during the previous round: by induction over
+// rounds, the last result of this warp on it still satisfies every edge
+// this direction tests (the flags of a round are read only after the
+// block barrier that ends it).
 template <int CONN, int KIND, int VPL, bool ROWS, class Map>
-__device__ bool sweep(const PropArgs& a, const Map& map, int dir, int lane) {
+__device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int dir, int start, int lane,
+                      int round, int& nproc) {
     const int nlines = ROWS ? a.H : a.W;
     const int len = ROWS ? a.W : a.H;
-    int l = dir > 0 ? 0 : nlines - 1;
-    Line<VPL> cur, nxt;
-    load_line<KIND, VPL, ROWS, Map>(a, map, l, len, lane, cur);
-    int dp[VPL], fp[VPL];
+    const uint8_t* f_line = ROWS ? sh.fR : sh.fC;
+    uint8_t* ch_own = (ROWS ? sh.chR : sh.chC) + (round % 3) * nlines;
+    uint8_t* ch_x = (ROWS ? sh.chC : sh.chR) + (round % 3) * len;
+    const uint8_t* prev_own = (ROWS ? sh.chR : sh.chC) + ((round + 2) % 3) * nlines;
+    const int wrap_at = dir > 0 ? 0 : nlines - 1;  // a sweep restarts here
+    const int* Pb = sh.Pb + (ROWS ? 0 : a.H * 32);
+    // gp[k]: cost of leaving the previous line's pixel, d + f (grey) or d (mask)
+    int gp[VPL];
 #pragma unroll
-    for (int k = 0; k < VPL; ++k) { dp[k] = PINF; fp[k] = 0; }
+    for (int k = 0; k < VPL; ++k) gp[k] = PINF;
+    bool pred_changed = false;  // the previous line changed (it must be relaxed from)
     bool changed = false;
-    for (int i = 0; i < nlines; ++i, l += dir) {
-        if (i + 1 < nlines) load_line<KIND, VPL, ROWS, Map>(a, map, l + dir, len, lane, nxt);
-        bool valid[VPL], freep[VPL];
+    int l = start;
+    for (int i = 0; i < nlines; ++i) {
+        if (i > 0 && l == wrap_at) {  // restart: no previous line
+            pred_changed = false;
+#pragma unroll
+            for (int k = 0; k < VPL; ++k) gp[k] = PINF;
+        }
+        // lowered in the previous round, or already in this one (seen so far)
+        const bool own_changed =
+            round == 0 || prev_own[l] != 0 || *((volatile const uint8_t*)(ch_own + l)) != 0;
+        const bool skip = !own_changed && !((i > 0 && l != wrap_at) ? pred_changed : false);
+        int fc[VPL];
 #pragma unroll
         for (int k = 0; k < VPL; ++k) {
-            valid[k] = VPL * lane + k < len;
-            freep[k] = valid[k] && (KIND == 0 || cur.f[k] != 0);
+            const int pos = VPL * lane + k;
+            fc[k] = pos < len ? f_line[l * len + pos] : 0;
+        }
+        if (skip) {
+#pragma unroll
+            for (int k = 0; k < VPL; ++k) {
+                const int pos = VPL * lane + k;
+                const int dv = pos < len ? (ROWS ? map.ld(l, pos) : map.ld(pos, l)) : PINF;
+                gp[k] = KIND == 0 ? dv + fc[k] : dv;
+            }
+            pred_changed = false;
+            l += dir;
+            if (l < 0) l += nlines;
+            if (l >= nlines) l -= nlines;
+            continue;
+        }
+        int o[VPL], p[VPL];
+        bool freep[VPL];
+#pragma unroll
+        for (int k = 0; k < VPL; ++k) {
+            const int pos = VPL * lane + k;
+            const bool valid = pos < len;
+            o[k] = valid ? (ROWS ? map.ld(l, pos) : map.ld(pos, l)) : PINF;
+            freep[k] = valid && (KIND == 0 || fc[k] != 0);
+        }
+        if (KIND == 0) {
+            // prefix of the line's edge weights f(c) + f(c+1) + 1: the lane's
+            // base from the table, then the lane's own pixels
+            int acc = Pb[l * 32 + lane];
+#pragma unroll
+            for (int k = 0; k < VPL; ++k) {
+                p[k] = acc;
+                if (k + 1 < VPL) acc += fc[k] + fc[k + 1] + 1;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < VPL; ++k) p[k] = 2 * (VPL * lane + k);
         }
         // 1. relax from the previous line
-        int dl0 = PINF, dr0 = PINF, fl0 = 0, fr0 = 0;
+        int gl0 = PINF, gr0 = PINF;
         if (CONN == 8) {
-            dl0 = __shfl_up_sync(FULL, dp[VPL - 1], 1);
-            dr0 = __shfl_down_sync(FULL, dp[0], 1);
-            if (lane == 0) dl0 = PINF;
-            if (lane == 31) dr0 = PINF;
-            if (KIND == 0) {
-                fl0 = __shfl_up_sync(FULL, fp[VPL - 1], 1);
-                fr0 = __shfl_down_sync(FULL, fp[0], 1);
-            }
+            gl0 = __shfl_up_sync(FULL, gp[VPL - 1], 1);
+            gr0 = __shfl_down_sync(FULL, gp[0], 1);
+            if (lane == 0) gl0 = PINF;
+            if (lane == 31) gr0 = PINF;
         }
         int v[VPL];
 #pragma unroll
         for (int k = 0; k < VPL; ++k) {
-            int best = cur.o[k];
-            if (KIND == 0) {
-                const int fc1 = cur.f[k] + 1;
-                best = min(best, dp[k] + fp[k] + fc1);
-                if (CONN == 8) {
-                    const int dl = k > 0 ? dp[k - 1] : dl0, fl = k > 0 ? fp[k - 1] : fl0;
-                    const int dr = k + 1 < VPL ? dp[k + 1] : dr0, fr = k + 1 < VPL ? fp[k + 1] : fr0;
-                    best = min(best, min(dl + fl, dr + fr) + fc1);
-                }
-            } else {
-                best = min(best, dp[k] + 2);
-                if (CONN == 8) {
-                    const int dl = k > 0 ? dp[k - 1] : dl0;
-                    const int dr = k + 1 < VPL ? dp[k + 1] : dr0;
-                    best = min(best, min(dl, dr) + 2);
-                }
+            int g = gp[k];
+            if (CONN == 8) {
+                const int gl = k > 0 ? gp[k - 1] : gl0;
+                const int gr = k + 1 < VPL ? gp[k + 1] : gr0;
+                g = min(g, min(gl, gr));
             }
+            const int best = min(o[k], g + (KIND == 0 ? fc[k] + 1 : 2));
             v[k] = freep[k] ? best : PINF;
         }
         // 2. close the line inside each lane
         int sx[VPL], sy[VPL], d[VPL];
 #pragma unroll
         for (int k = 0; k < VPL; ++k) {
-            const int x = freep[k] ? v[k] - cur.p[k] : BIGX;
+            const int x = freep[k] ? v[k] - p[k] : BIGX;
             sx[k] = (KIND == 1 && !freep[k]) ? BIGX : min(k > 0 ? sx[k - 1] : BIGX, x);
         }
 #pragma unroll
         for (int k = VPL - 1; k >= 0; --k) {
-            const int y = freep[k] ? v[k] + cur.p[k] : BIGY;
+            const int y = freep[k] ? v[k] + p[k] : BIGY;
             sy[k] = (KIND == 1 && !freep[k]) ? BIGY : min(k + 1 < VPL ? sy[k + 1] : BIGY, y);
         }
 #pragma unroll
         for (int k = 0; k < VPL; ++k)
-            d[k] = freep[k] ? min(v[k], min(sx[k] + cur.p[k], sy[k] - cur.p[k])) : PINF;
+            d[k] = freep[k] ? min(v[k], min(sx[k] + p[k], sy[k] - p[k])) : PINF;
         // does a value have to cross a lane boundary?
-        const int xl = freep[VPL - 1] ? d[VPL - 1] - cur.p[VPL - 1] : BIGX;
-        const int yf = freep[0] ? d[0] + cur.p[0] : BIGY;
+        const int xl = freep[VPL - 1] ? d[VPL - 1] - p[VPL - 1] : BIGX;
+        const int yf = freep[0] ? d[0] + p[0] : BIGY;
         const int xl_left = __shfl_up_sync(FULL, xl, 1);
         const int yf_right = __shfl_down_sync(FULL, yf, 1);
-        const bool need = (lane > 0 && freep[0] && xl_left < d[0] - cur.p[0]) ||
-                          (lane < 31 && freep[VPL - 1] && yf_right < d[VPL - 1] + cur.p[VPL - 1]);
+        const bool need = (lane > 0 && freep[0] && xl_left < d[0] - p[0]) ||
+                          (lane < 31 && freep[VPL - 1] && yf_right < d[VPL - 1] + p[VPL - 1]);
         if (__any_sync(FULL, need)) {
             // exclusive prefix-min of the lane totals of v - P (suffix-min of
             // v + P); on a mask, runs of free pixels are separate segments
             int tx = sx[VPL - 1], ty = sy[0];
-            bool hx = false, hy = false;  // lane holds a segment start (mask)
+            bool hx = false, hy = false;
             int first_ob = VPL, last_ob = -1;
             if (KIND == 1) {
 #pragma unroll
@@ -170,13 +198,13 @@ __device__ bool sweep(const PropArgs& a, const Map& map, int dir, int lane) {
                 hx = hy = first_ob < VPL;
             }
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int tx2 = __shfl_up_sync(FULL, tx, o);
-                const int ty2 = __shfl_down_sync(FULL, ty, o);
-                const bool hx2 = __shfl_up_sync(FULL, hx, o);
-                const bool hy2 = __shfl_down_sync(FULL, hy, o);
-                if (lane >= o && !hx) { tx = min(tx, tx2); hx = hx2; }
-                if (lane + o < 32 && !hy) { ty = min(ty, ty2); hy = hy2; }
+            for (int off = 1; off < 32; off <<= 1) {
+                const int tx2 = __shfl_up_sync(FULL, tx, off);
+                const int ty2 = __shfl_down_sync(FULL, ty, off);
+                const bool hx2 = __shfl_up_sync(FULL, (int)hx, off);
+                const bool hy2 = __shfl_down_sync(FULL, (int)hy, off);
+                if (lane >= off && !hx) { tx = min(tx, tx2); hx = hx2; }
+                if (lane + off < 32 && !hy) { ty = min(ty, ty2); hy = hy2; }
             }
             int ex = __shfl_up_sync(FULL, tx, 1);
             int ey = __shfl_down_sync(FULL, ty, 1);
@@ -187,51 +215,72 @@ __device__ bool sweep(const PropArgs& a, const Map& map, int dir, int lane) {
                 if (!freep[k]) continue;
                 const int px = (KIND == 1 && k > first_ob) ? sx[k] : min(ex, sx[k]);
                 const int py = (KIND == 1 && k < last_ob) ? sy[k] : min(ey, sy[k]);
-                d[k] = min(v[k], min(px + cur.p[k], py - cur.p[k]));
+                d[k] = min(v[k], min(px + p[k], py - p[k]));
             }
         }
-        // lower the map where this line improved
+        // lower the map where this line improved, then bump the versions of
+        // this line and of every crossing line that changed
+        bool mine = false;
 #pragma unroll
         for (int k = 0; k < VPL; ++k) {
-            if (freep[k] && d[k] < cur.o[k]) {
-                changed = true;
+            if (freep[k] && d[k] < o[k]) {
+                mine = true;
                 const int pos = VPL * lane + k;
                 if (ROWS) map.lower(l, pos, d[k]);
                 else map.lower(pos, l, d[k]);
             }
-            dp[k] = d[k];
-            fp[k] = cur.f[k];
+            gp[k] = KIND == 0 ? d[k] + fc[k] : d[k];
         }
-        if (i + 1 < nlines) cur = nxt;
+        ++nproc;
+        if (mine) {
+#pragma unroll
+            for (int k = 0; k < VPL; ++k)
+                if (freep[k] && d[k] < o[k]) ch_x[VPL * lane + k] = 1;
+            ch_own[l] = 1;
+            changed = true;
+        }
+        pred_changed = own_changed || __any_sync(FULL, mine);
+        l += dir;
+        if (l < 0) l += nlines;
+        if (l >= nlines) l -= nlines;
     }
-    return __any_sync(FULL, changed);
+    return changed;
 }
 
 template <int CONN, int KIND, int VPL, class Map>
-__device__ void run_block(const PropArgs& a, const Map& map, int* s_flag, int* s_rounds) {
+__device__ void run_block(const PropArgs& a, const Map& map, const Shared& sh, int* s_flag, int* s_rounds) {
+    const int nr = a.H, nc = a.W;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int round = 0;
+    const int dirk = warp & 3, phase = warp >> 2;
+    const bool rows = dirk < 2;
+    const int dir = (dirk & 1) ? -1 : +1;
+    const int nlines = rows ? a.H : a.W;
+    int start = dir > 0 ? 0 : nlines - 1;
+    if (phase) start = dir > 0 ? nlines / 2 : (nlines / 2 - 1 + nlines) % nlines;
+    int round = 0, nproc = 0;
     for (;;) {
+        // clear the flag slot the next round will write (last used two rounds ago)
+        const int nx = (round + 1) % 3;
+        for (int i = threadIdx.x; i < nr; i += blockDim.x) sh.chR[nx * nr + i] = 0;
+        for (int i = threadIdx.x; i < nc; i += blockDim.x) sh.chC[nx * nc + i] = 0;
         bool ch;
-        switch (warp) {
-            case 0: ch = sweep<CONN, KIND, VPL, true, Map>(a, map, +1, lane); break;
-            case 1: ch = sweep<CONN, KIND, VPL, true, Map>(a, map, -1, lane); break;
-            case 2: ch = sweep<CONN, KIND, VPL, false, Map>(a, map, +1, lane); break;
-            default: ch = sweep<CONN, KIND, VPL, false, Map>(a, map, -1, lane); break;
-        }
+        if (rows) ch = sweep<CONN, KIND, VPL, true, Map>(a, map, sh, dir, start, lane, round, nproc);
+        else ch = sweep<CONN, KIND, VPL, false, Map>(a, map, sh, dir, start, lane, round, nproc);
+        ch = __any_sync(FULL, ch);
         if (lane == 0 && ch) s_flag[round & 1] = 1;
         __syncthreads();
         const bool any = s_flag[round & 1] != 0;
         if (threadIdx.x == 0) s_flag[(round + 1) & 1] = 0;
         ++round;
         if (!any) break;
-        if (round * PWARPS >= a.max_sweeps) {
+        if (round * 4 >= a.max_sweeps) {
             if (threadIdx.x == 0) atomicOr(a.status, ST_NOT_CONVERGED);
             break;
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) *s_rounds = round;
+    if (lane == 0 && a.sweeps) atomicAdd(a.sweeps + (S_LINES - S_SWEEPS), (unsigned long long)nproc);
 }
 
 __device__ __forceinline__ int finish(const PropArgs& a, int v) {
@@ -242,9 +291,59 @@ __device__ __forceinline__ bool is_seed(const PropArgs& a, int src, int p) {
     return a.seed_flags ? a.seed_flags[p] != 0 : p == src;
 }
 
-// Map in shared memory; one block of PWARPS warps per job.
+// Lays out the non-map shared state after `base` and initialises it.
+template <int KIND, int VPL>
+__device__ Shared setup_shared(const PropArgs& a, char* base) {
+    Shared sh;
+    uint8_t* bp = reinterpret_cast<uint8_t*>(base);
+    sh.chR = bp;
+    sh.chC = bp + 3 * a.H;
+    uint8_t* fR = bp + 3 * (a.H + a.W);
+    uint8_t* fC = fR + a.N;
+    for (int p = threadIdx.x; p < a.N; p += blockDim.x) {
+        const uint8_t v = a.f[p];
+        const int r = p / a.W, c = p - r * a.W;
+        fR[p] = v;
+        fC[c * a.H + r] = v;
+    }
+    for (int i = threadIdx.x; i < 3 * (a.H + a.W); i += blockDim.x) bp[i] = 0;
+    sh.fR = fR;
+    sh.fC = fC;
+    // lane bases of the line prefixes (grey): one warp per line
+    int* Pb = reinterpret_cast<int*>(bp + ((3 * (a.H + a.W) + 2 * a.N + 15) & ~15));
+    sh.Pb = Pb;
+    if (KIND == 0) {
+        const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int l = threadIdx.x >> 5; l < a.H + a.W; l += nw) {
+            const bool rows = l < a.H;
+            const int line = rows ? l : l - a.H, len = rows ? a.W : a.H;
+            int t = 0;
+            for (int k = 0; k < VPL; ++k) {
+                const int c = VPL * lane + k;
+                if (c + 1 < len) {
+                    const int e0 = rows ? line * a.W + c : c * a.W + line;
+                    const int e1 = rows ? e0 + 1 : e0 + a.W;
+                    t += a.f[e0] + a.f[e1] + 1;
+                }
+            }
+            int incl = t;
+            for (int off = 1; off < 32; off <<= 1) {
+                const int u = __shfl_up_sync(FULL, incl, off);
+                if (lane >= off) incl += u;
+            }
+            Pb[l * 32 + lane] = incl - t;
+        }
+    }
+    return sh;
+}
+
+__host__ __device__ inline size_t shared_state_bytes(int H, int W) {
+    return (((3 * (size_t)(H + W) + 2 * (size_t)H * W) + 15) & ~(size_t)15) + (size_t)(H + W) * 32 * sizeof(int);
+}
+
+// Map in shared memory; one block per job.
 template <int CONN, int KIND, int VPL>
-__global__ void __launch_bounds__(32 * PWARPS) k_propagate_smem(PropArgs a, int pitch) {
+__global__ void __launch_bounds__(32 * MAXWARPS) k_propagate_smem(PropArgs a, int pitch) {
     extern __shared__ int smap[];
     __shared__ int s_flag[2], s_rounds;
     const int j = blockIdx.x;
@@ -256,12 +355,13 @@ __global__ void __launch_bounds__(32 * PWARPS) k_propagate_smem(PropArgs a, int 
         const int r = p / a.W, c = p - r * a.W;
         smap[r * pitch + c] = is_seed(a, src, p) ? 0 : PINF;
     }
+    const Shared sh = setup_shared<KIND, VPL>(a, reinterpret_cast<char*>(smap + a.H * pitch));
     if (threadIdx.x == 0) { s_flag[0] = 0; s_flag[1] = 0; }
     __syncthreads();
     const SmemMap map{smap, pitch};
-    run_block<CONN, KIND, VPL>(a, map, s_flag, &s_rounds);
+    run_block<CONN, KIND, VPL>(a, map, sh, s_flag, &s_rounds);
     __syncthreads();
-    if (threadIdx.x == 0 && a.sweeps) atomicAdd(a.sweeps, (unsigned long long)s_rounds * PWARPS);
+    if (threadIdx.x == 0 && a.sweeps) atomicAdd(a.sweeps, (unsigned long long)s_rounds * (blockDim.x >> 5));
     // finished row: coalesced 128-bit stores
     if ((a.N & 3) == 0 && (a.W & 3) == 0) {
         int4* o4 = reinterpret_cast<int4*>(out);
@@ -283,7 +383,8 @@ __global__ void __launch_bounds__(32 * PWARPS) k_propagate_smem(PropArgs a, int 
 // Map in global memory (the output row itself), for images whose map does
 // not fit in shared memory.
 template <int CONN, int KIND, int VPL>
-__global__ void __launch_bounds__(32 * PWARPS) k_propagate_glob(PropArgs a) {
+__global__ void __launch_bounds__(32 * MAXWARPS) k_propagate_glob(PropArgs a) {
+    extern __shared__ int sbuf[];
     __shared__ int s_flag[2], s_rounds;
     const int j = blockIdx.x;
     const int njobs = a.njobs_dev ? *a.njobs_dev : a.njobs;
@@ -291,13 +392,14 @@ __global__ void __launch_bounds__(32 * PWARPS) k_propagate_glob(PropArgs a) {
     const int src = a.sources ? a.sources[j] : -1;
     int* map = a.map_base + (size_t)(a.map_row ? a.map_row[j] : j) * (size_t)a.N;
     for (int p = threadIdx.x; p < a.N; p += blockDim.x) map[p] = is_seed(a, src, p) ? 0 : PINF;
+    const Shared sh = setup_shared<KIND, VPL>(a, reinterpret_cast<char*>(sbuf));
     if (threadIdx.x == 0) { s_flag[0] = 0; s_flag[1] = 0; }
     __threadfence_block();
     __syncthreads();
     const GlobMap gm{map, a.W};
-    run_block<CONN, KIND, VPL>(a, gm, s_flag, &s_rounds);
+    run_block<CONN, KIND, VPL>(a, gm, sh, s_flag, &s_rounds);
     __syncthreads();
-    if (threadIdx.x == 0 && a.sweeps) atomicAdd(a.sweeps, (unsigned long long)s_rounds * PWARPS);
+    if (threadIdx.x == 0 && a.sweeps) atomicAdd(a.sweeps, (unsigned long long)s_rounds * (blockDim.x >> 5));
     if (a.convert) {
         for (int p = threadIdx.x; p < a.N; p += blockDim.x) {
             const int v = ld_cg(map + p);
@@ -308,22 +410,28 @@ __global__ void __launch_bounds__(32 * PWARPS) k_propagate_glob(PropArgs a) {
     }
 }
 
-constexpr int SMEM_MAP_LIMIT = 200 * 1024;
+constexpr int SMEM_LIMIT = 220 * 1024;
 
 template <int CONN, int KIND, int VPL>
 cudaError_t launch_one(const PropArgs& a, int jobs, cudaStream_t st) {
-    const int pitch = a.W | 1;  // odd pitch: row and column lines avoid bank conflicts
-    const size_t smem = (size_t)a.H * pitch * sizeof(int);
-    if (smem <= (size_t)SMEM_MAP_LIMIT) {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_propagate_smem<CONN, KIND, VPL>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_MAP_LIMIT);
-            attr = true;
-        }
-        k_propagate_smem<CONN, KIND, VPL><<<jobs, 32 * PWARPS, smem, st>>>(a, pitch);
+    const int pitch = a.W | 1;  // odd pitch: row and column lines spread over the banks
+    const size_t state = shared_state_bytes(a.H, a.W);
+    const size_t smem = (size_t)a.H * pitch * sizeof(int) + state;
+    const int threads = 32 * 4 * (a.phases == 2 ? 2 : 1);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_propagate_smem<CONN, KIND, VPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             SMEM_LIMIT);
+        cudaFuncSetAttribute(k_propagate_glob<CONN, KIND, VPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             SMEM_LIMIT);
+        attr = true;
+    }
+    if (smem <= (size_t)SMEM_LIMIT) {
+        k_propagate_smem<CONN, KIND, VPL><<<jobs, threads, smem, st>>>(a, pitch);
+    } else if (state <= (size_t)SMEM_LIMIT) {
+        k_propagate_glob<CONN, KIND, VPL><<<jobs, threads, state, st>>>(a);
     } else {
-        k_propagate_glob<CONN, KIND, VPL><<<jobs, 32 * PWARPS, 0, st>>>(a);
+        return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }

@@ -10,14 +10,17 @@
 // d(a,b) = d(s,b) - d(s,a) (Property 1). The pair is written into D (both
 // triangles) the first time it is seen, and the fill counts cnt (Sec. 2, eq.
 // "filling rate pt": tau(x) = (cnt(x) - 1)/(N - 1)) go up by one at both
-// ends. "Distance operations" count every (ancestor, vertex) pair visited.
+// ends (the counts are recomputed from the marks of the rows that changed).
+// "Distance operations" count every (ancestor, vertex) pair visited.
 //
 // To avoid visiting ancestors one by one, each tree path is cut into
-// segments that stay inside one 8x8 pixel tile: for every vertex a,
-// seg_mask(a) holds the bits of a and of its ancestors up to the first one
-// outside a's tile, and seg_exit(a) is that first outside ancestor. The
-// marks use the same tiling (one 64-bit word per row and tile), so one
-// segment is tested against row b's marks with a single AND.
+// segments that stay inside one 8x8 pixel tile: for every vertex a, the
+// segment record holds the bits of a and of its ancestors up to the first
+// one outside a's tile, and that first outside ancestor. The marks use the
+// same tiling (one 64-bit word per row and tile), so one segment is tested
+// against row b's marks with a single AND. The operation count (every
+// ancestor pair, marked or not) comes from the tree depths instead, so rows
+// already filled are not walked at all.
 #include "common.cuh"
 #include "internal.h"
 
@@ -29,132 +32,236 @@ __device__ __forceinline__ int edge_w(const TreeArgs& a, int p, int q) {
     return a.kind == 0 ? (int)a.f[p] + (int)a.f[q] + 1 : 2;
 }
 
-// parent[j][b] (-1 for the root and for unreached vertices).
-__global__ void k_parents(TreeArgs a) {
-    const int j = blockIdx.y;
-    if (j >= *a.nsel) return;
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= a.N) return;
-    const int s = a.sel[j];
-    const uint32_t* drow = a.D + (size_t)s * a.N;
+// Canonical parent of b in the tree of s (-1 for the root and unreached).
+__device__ __forceinline__ int canonical_parent(const TreeArgs& a, const uint32_t* drow, int s, int b) {
     const uint32_t db = drow[b];
-    int par = -1;
-    if (b != s && db != UNREACH) {
-        const int r = b / a.W, c = b - r * a.W;
-        // neighbours in increasing linear index
-        for (int dr = -1; dr <= 1 && par < 0; ++dr)
-            for (int dc = -1; dc <= 1; ++dc) {
-                if (!dr && !dc) continue;
-                if (a.conn == 4 && dr && dc) continue;
-                const int rr = r + dr, cc = c + dc;
-                if (rr < 0 || rr >= a.H || cc < 0 || cc >= a.W) continue;
-                const int q = rr * a.W + cc;
-                if (a.kind == 1 && !a.f[q]) continue;
-                const uint32_t dq = drow[q];
-                if (dq != UNREACH && dq + (uint32_t)edge_w(a, q, b) == db) { par = q; break; }
-            }
-    }
-    a.parent[(size_t)j * a.N + b] = par;
+    if (b == s || db == UNREACH) return -1;
+    const int r = b / a.W, c = b - r * a.W;
+    // neighbours in increasing linear index
+    for (int dr = -1; dr <= 1; ++dr)
+        for (int dc = -1; dc <= 1; ++dc) {
+            if (!dr && !dc) continue;
+            if (a.conn == 4 && dr && dc) continue;
+            const int rr = r + dr, cc = c + dc;
+            if (rr < 0 || rr >= a.H || cc < 0 || cc >= a.W) continue;
+            const int q = rr * a.W + cc;
+            if (a.kind == 1 && !a.f[q]) continue;
+            const uint32_t dq = drow[q];
+            if (dq != UNREACH && dq + (uint32_t)edge_w(a, q, b) == db) return q;
+        }
+    return -1;
 }
 
-// seg_mask / seg_exit of every vertex of every selected tree.
-__global__ void k_segments(TreeArgs a) {
-    const int j = blockIdx.y;
+// The tree of one selected source, one block per source:
+//  1. parent[j][b]: the canonical parent;
+//  2. seg[j][v]: x = bits of v and of its ancestors up to the first one
+//     outside v's 8x8 tile, y = that first outside ancestor + 1 (0 past the
+//     root);
+//  3. the distance operations of the tree: the sum over reached b != s of
+//     depth(b), the number of proper ancestors of b. With acc(v) = number of
+//     vertices from v up to the root, depth(b) = acc(parent(b)); acc is
+//     summed along the segment chain by pointer jumping. When N <= 16384
+//     (SMALL) the parents and the jumping arrays are 16-bit shared arrays;
+//     otherwise they live in global scratch.
+template <bool SMALL>
+__global__ void __launch_bounds__(1024) k_tree(TreeArgs a) {
+    extern __shared__ uint16_t sdep[];
+    __shared__ int s_any[2];
+    const int j = blockIdx.x, B = gridDim.x;
     if (j >= *a.nsel) return;
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= a.N) return;
+    const int N = a.N, s = a.sel[j];
+    const uint32_t* drow = a.D + (size_t)s * N;
+    int32_t* par = a.parent + (size_t)j * N;
+    ulonglong2* seg = a.seg + (size_t)j * N;
     const TileGeom tg{a.W, a.tiles_w, a.words};
-    const int32_t* par = a.parent + (size_t)j * a.N;
-    const int t = tg.tile_of(v);
-    unsigned long long m = 1ull << tg.bit_of(v);
-    int x = par[v];
-    for (int guard = 0; x >= 0 && guard < 64 && tg.tile_of(x) == t; ++guard) {
-        m |= 1ull << tg.bit_of(x);
-        x = par[x];
+    uint16_t* spar = sdep + 4 * N;  // parent + 1 (SMALL)
+    for (int b = threadIdx.x; b < N; b += blockDim.x) {
+        const int pb = canonical_parent(a, drow, s, b);
+        par[b] = pb;
+        if (SMALL) spar[b] = (uint16_t)(pb + 1);
     }
-    a.seg_mask[(size_t)j * a.N + v] = m;
-    a.seg_exit[(size_t)j * a.N + v] = x;
+    __syncthreads();
+    for (int v = threadIdx.x; v < N; v += blockDim.x) {
+        const int t = tg.tile_of(v);
+        unsigned long long m = 1ull << tg.bit_of(v);
+        int x = SMALL ? (int)spar[v] - 1 : __ldcg(par + v);
+        for (int guard = 0; x >= 0 && guard < 64 && tg.tile_of(x) == t; ++guard) {
+            m |= 1ull << tg.bit_of(x);
+            x = SMALL ? (int)spar[x] - 1 : __ldcg(par + x);
+        }
+        const bool reached = drow[v] != UNREACH;
+        seg[v] = make_ulonglong2(m, (unsigned long long)(x + 1));
+        if (SMALL) {
+            sdep[v] = reached ? (uint16_t)__popcll(m) : 0;                 // acc, buffer 0
+            sdep[2 * N + v] = reached ? (uint16_t)(x + 1) : 0;            // jmp + 1, buffer 0
+        } else {
+            a.acc[(size_t)j * N + v] = reached ? __popcll(m) : 0;
+            a.jmp[(size_t)j * N + v] = reached ? x : -1;
+        }
+    }
+    if (threadIdx.x == 0) { s_any[0] = 0; s_any[1] = 0; }
+    __syncthreads();
+    // pointer jumping: acc(v) += acc(jmp(v)); jmp(v) = jmp(jmp(v))
+    int cur = 0;
+    for (int pass = 0; pass < 32; ++pass) {
+        const int nx = cur ^ 1;
+        int any = 0;
+        for (int v = threadIdx.x; v < N; v += blockDim.x) {
+            int j1, c;
+            if (SMALL) {
+                j1 = (int)sdep[2 * N + cur * N + v] - 1;
+                c = sdep[cur * N + v];
+            } else {
+                j1 = __ldcg(a.jmp + (size_t)(cur * B + j) * N + v);
+                c = __ldcg(a.acc + (size_t)(cur * B + j) * N + v);
+            }
+            int j2 = -1;
+            if (j1 >= 0) {
+                if (SMALL) {
+                    j2 = (int)sdep[2 * N + cur * N + j1] - 1;
+                    c += sdep[cur * N + j1];
+                } else {
+                    j2 = __ldcg(a.jmp + (size_t)(cur * B + j) * N + j1);
+                    c += __ldcg(a.acc + (size_t)(cur * B + j) * N + j1);
+                }
+            }
+            any |= j2 >= 0;
+            if (SMALL) {
+                sdep[nx * N + v] = (uint16_t)c;
+                sdep[2 * N + nx * N + v] = (uint16_t)(j2 + 1);
+            } else {
+                a.acc[(size_t)(nx * B + j) * N + v] = c;
+                a.jmp[(size_t)(nx * B + j) * N + v] = j2;
+            }
+        }
+        if (any) s_any[pass & 1] = 1;
+        __syncthreads();
+        const bool more = s_any[pass & 1] != 0;
+        if (threadIdx.x == 0) s_any[(pass + 1) & 1] = 0;
+        cur = nx;
+        if (!more) break;
+        __syncthreads();
+    }
+    unsigned long long ops = 0;
+    for (int b = threadIdx.x; b < N; b += blockDim.x) {
+        const int pb = SMALL ? (int)spar[b] - 1 : __ldcg(par + b);
+        if (pb >= 0)
+            ops += SMALL ? (unsigned long long)sdep[cur * N + pb]
+                         : (unsigned long long)__ldcg(a.acc + (size_t)(cur * B + j) * N + pb);
+    }
+    for (int o = 16; o > 0; o >>= 1) ops += __shfl_down_sync(FULL, ops, o);
+    if ((threadIdx.x & 31) == 0 && ops) atomicAdd(a.stats + S_OPS, ops);
 }
 
-// One block owns rows [b0, b0 + rows) of the marks, copied to shared memory,
-// and walks, for each selected source, the tree path of each of its rows.
+// One block owns up to 32 consecutive rows of the marks. Rows already
+// filled (cnt = N) hold every pair and are skipped; the others are copied
+// to shared memory, and for each selected source the block walks the tree
+// path of each of its rows, one tile segment at a time.
 __global__ void k_fill(TreeArgs a) {
     extern __shared__ unsigned long long srow[];
+    __shared__ int s_rows[32];
+    __shared__ int s_nu;
     const int nsel = *a.nsel;
     if (nsel == 0) return;
     const int b0 = blockIdx.x * a.rows_per_block;
     const int nrows = min(a.rows_per_block, a.N - b0);
-    const TileGeom tg{a.W, a.tiles_w, a.words};
-    const unsigned long long* grow = a.marks + (size_t)b0 * a.words;
-    for (int i = threadIdx.x; i < nrows * a.words; i += blockDim.x) srow[i] = ld_cg64(grow + i);
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const bool open = lane < nrows && __ldcg(a.cnt + b0 + lane) < (uint32_t)a.N;
+        const unsigned m = __ballot_sync(FULL, open);
+        if (open) s_rows[__popc(m & ((1u << lane) - 1u))] = b0 + lane;
+        if (lane == 0) s_nu = __popc(m);
+    }
     __syncthreads();
-    unsigned long long ops = 0, fresh = 0;
-    const int items = nrows * nsel;
+    const int nu = s_nu;
+    if (nu == 0) return;
+    const TileGeom tg{a.W, a.tiles_w, a.words};
+    for (int i = threadIdx.x; i < nu * a.words; i += blockDim.x) {
+        const int r = i / a.words, w = i - r * a.words;
+        srow[i] = ld_cg64(a.marks + (size_t)s_rows[r] * a.words + w);
+    }
+    __syncthreads();
+    unsigned long long fresh = 0;
+    const int items = nu * nsel;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
-        const int j = it / nrows, bl = it - j * nrows, b = b0 + bl;
+        const int j = it / nu, bl = it - j * nu, b = s_rows[bl];
         const int s = a.sel[j];
         const uint32_t* drow = a.D + (size_t)s * a.N;
         const uint32_t db = drow[b];
         if (b == s || db == UNREACH) continue;
-        const bool filled = *((volatile const uint32_t*)(a.cnt + b)) == (uint32_t)a.N;
-        const int32_t* sexit = a.seg_exit + (size_t)j * a.N;
-        const unsigned long long* smask = a.seg_mask + (size_t)j * a.N;
+        const ulonglong2* seg = a.seg + (size_t)j * a.N;
         unsigned long long* myrow = srow + (size_t)bl * a.words;
+        unsigned fresh_b = 0;
         int v = a.parent[(size_t)j * a.N + b];
         for (int guard = 0; v >= 0 && guard <= a.N; ++guard) {
-            const unsigned long long m = smask[v];
-            const int nx = sexit[v];
-            ops += __popcll(m);
-            if (!filled) {
-                const int t = tg.tile_of(v);
-                unsigned long long nb = m & ~myrow[t];
-                while (nb) {
-                    const int bit = __ffsll((long long)nb) - 1;
-                    nb &= nb - 1;
-                    const int ap = tg.pixel_of(t, bit);
-                    // The pair {ap, b} is claimed on its canonical bit: row
-                    // min(ap, b), column max(ap, b). The first claimant fills it.
-                    const int lo = min(ap, b), hi = max(ap, b);
-                    const unsigned long long cbit = 1ull << tg.bit_of(hi);
-                    const unsigned long long old =
-                        atomicOr(a.marks + (size_t)lo * a.words + tg.tile_of(hi), cbit);
-                    if (!(old & cbit)) {
-                        atomicOr(a.marks + (size_t)hi * a.words + tg.tile_of(lo), 1ull << tg.bit_of(lo));
-                        atomicAdd(a.cnt + ap, 1u);
-                        atomicAdd(a.cnt + b, 1u);
-                        const uint32_t val = db - drow[ap];
-                        a.Dw[(size_t)ap * a.N + b] = val;
-                        a.Dw[(size_t)b * a.N + ap] = val;
-                        ++fresh;
-                    }
-                    atomicOr(myrow + t, 1ull << bit);
+            const ulonglong2 g = seg[v];
+            const int t = tg.tile_of(v);
+            unsigned long long nb = g.x & ~myrow[t];
+            while (nb) {
+                const int bit = __ffsll((long long)nb) - 1;
+                nb &= nb - 1;
+                const int ap = tg.pixel_of(t, bit);
+                // The pair {ap, b} is claimed on its canonical bit: row
+                // min(ap, b), column max(ap, b). The first claimant fills it.
+                const int lo = min(ap, b), hi = max(ap, b);
+                const unsigned long long cbit = 1ull << tg.bit_of(hi);
+                const unsigned long long old = atomicOr(a.marks + (size_t)lo * a.words + tg.tile_of(hi), cbit);
+                if (!(old & cbit)) {
+                    atomicOr(a.marks + (size_t)hi * a.words + tg.tile_of(lo), 1ull << tg.bit_of(lo));
+                    a.dirty[ap] = 1;
+                    ++fresh_b;
+                    const uint32_t val = db - drow[ap];
+                    a.Dw[(size_t)ap * a.N + b] = val;
+                    a.Dw[(size_t)b * a.N + ap] = val;
                 }
+                atomicOr(myrow + t, 1ull << bit);
             }
-            v = nx;
+            v = (int)g.y - 1;
+        }
+        if (fresh_b) {
+            a.dirty[b] = 1;
+            fresh += fresh_b;
         }
     }
-    // block totals
-    for (int o = 16; o > 0; o >>= 1) {
-        ops += __shfl_down_sync(FULL, ops, o);
-        fresh += __shfl_down_sync(FULL, fresh, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (ops) atomicAdd(a.stats + S_OPS, ops);
-        if (fresh) atomicAdd(a.stats + S_NEW, fresh);
+    for (int o = 16; o > 0; o >>= 1) fresh += __shfl_down_sync(FULL, fresh, o);
+    if ((threadIdx.x & 31) == 0 && fresh) atomicAdd(a.stats + S_NEW, fresh);
+}
+
+// Fill counts of the rows that gained marks: cnt(x) = cnt at the start +
+// the number of marked pairs of row x (both bits of a pair are set, so row
+// x holds every filled pair {x, y}). One warp per row.
+__global__ void k_recount(TreeArgs a) {
+    const int x = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (x >= a.N || !a.dirty[x]) return;
+    const unsigned long long* row = a.marks + (size_t)x * a.words;
+    unsigned c = 0;
+    for (int w = lane; w < a.words; w += 32) c += __popcll(__ldcg(row + w));
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(FULL, c, o);
+    if (lane == 0) {
+        a.cnt[x] = a.cnt_base[x] + c;
+        a.dirty[x] = 0;
     }
 }
 
 }  // namespace
 
-cudaError_t launch_parents(const TreeArgs& a, int B, cudaStream_t st) {
-    dim3 grid((a.N + 255) / 256, B);
-    k_parents<<<grid, 256, 0, st>>>(a);
+cudaError_t launch_recount(const TreeArgs& a, cudaStream_t st) {
+    k_recount<<<(a.N + 7) / 8, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_segments(const TreeArgs& a, int B, cudaStream_t st) {
-    dim3 grid((a.N + 255) / 256, B);
-    k_segments<<<grid, 256, 0, st>>>(a);
+cudaError_t launch_tree(const TreeArgs& a, int B, cudaStream_t st) {
+    if (a.N <= 16384) {
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_tree<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+            attr = true;
+        }
+        k_tree<true><<<B, 1024, (size_t)a.N * 5 * sizeof(uint16_t), st>>>(a);
+    } else {
+        k_tree<false><<<B, 1024, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
