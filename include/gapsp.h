@@ -81,7 +81,7 @@ typedef struct {
     int B;             /* sources per round, 1..1024 (0 = 32) */
     uint64_t seed;     /* seed of the spiral order's draws */
     size_t mem_budget; /* bytes of device memory a call may use (0 = no limit) */
-    int sweep_phases;  /* warps per sweep direction in a propagation: 0 = auto, 1 or 2 */
+    int sweep_phases;  /* warps per sweep direction in a propagation: 0 = auto, 1, 2 or 4 */
     int reserved;      /* 0 */
     int checked;       /* reserved (0) */
     void *stream;      /* cudaStream_t the calls run on (NULL = default stream) */

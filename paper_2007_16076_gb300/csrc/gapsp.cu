@@ -149,6 +149,8 @@ PropArgs base_prop(const gapsp_handle* h) {
     a.H = h->H;
     a.W = h->W;
     a.N = h->N;
+    a.conn = h->conn;
+    a.kind_mask = h->kind == GAPSP_MASK;
     a.f = h->f;
     a.Prow = h->Prow;
     a.Pcol = h->Pcol;
@@ -290,7 +292,7 @@ gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask,
     if (o.conn != 4 && o.conn != 8) return GAPSP_E_INVALID;
     if (o.kind != GAPSP_GREY && o.kind != GAPSP_MASK) return GAPSP_E_INVALID;
     if (o.B < 1 || o.B > 1024) return GAPSP_E_INVALID;
-    if (o.sweep_phases < 0 || o.sweep_phases > 2) return GAPSP_E_INVALID;
+    if (o.sweep_phases < 0 || o.sweep_phases > 4 || o.sweep_phases == 3) return GAPSP_E_INVALID;
     if (o.kind == GAPSP_GREY && !img) return GAPSP_E_INVALID;
     if (o.kind == GAPSP_MASK && !mask) return GAPSP_E_INVALID;
 

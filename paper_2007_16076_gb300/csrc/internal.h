@@ -14,7 +14,7 @@ struct PropArgs {
     const uint8_t* seed_flags;  // multi-source seeds, one job (NULL: single sources)
     const int* njobs_dev;       // device-side job count (NULL: use njobs)
     int njobs;
-    int H, W, N;
+    int H, W, N, conn, kind_mask;
     const uint8_t* f;           // grey levels (grey) or free flags (mask)
     const int* Prow;            // [H][W]: sum of horizontal edge weights left of (r,c)
     const int* Pcol;            // [W][H]: sum of vertical edge weights above (r,c)
@@ -22,7 +22,7 @@ struct PropArgs {
     unsigned long long* sweeps; // optional: total sweeps run
     int max_sweeps;
     int convert;                // write UNREACH for pixels never reached
-    int phases;                 // warps per sweep direction (1 or 2)
+    int phases;                 // warps per sweep direction (1, 2 or 4)
 };
 
 // Picks the per-lane width and launches kernel (a).

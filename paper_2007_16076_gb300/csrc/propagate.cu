@@ -38,7 +38,7 @@ namespace gapsp {
 
 namespace {
 
-constexpr int MAXWARPS = 8;               // 4 directions x up to 2 phases
+constexpr int MAXWARPS = 16;              // 4 directions x up to 4 phases
 constexpr int BIGX = PINF;                // identity of the prefix-min of v - P
 constexpr int BIGY = PINF + (1 << 18);    // identity of the suffix-min of v + P
 
@@ -97,9 +97,9 @@ __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int d
 #pragma unroll
             for (int k = 0; k < VPL; ++k) gp[k] = PINF;
         }
-        // lowered in the previous round, or already in this one (seen so far)
-        const bool own_changed =
-            round == 0 || prev_own[l] != 0 || *((volatile const uint8_t*)(ch_own + l)) != 0;
+        // lowered in the previous round, or already in this one (seen so far);
+        // before the first round the lines holding a seed count as lowered
+        const bool own_changed = prev_own[l] != 0 || *((volatile const uint8_t*)(ch_own + l)) != 0;
         const bool skip = !own_changed && !((i > 0 && l != wrap_at) ? pred_changed : false);
         int fc[VPL];
 #pragma unroll
@@ -251,12 +251,13 @@ template <int CONN, int KIND, int VPL, class Map>
 __device__ void run_block(const PropArgs& a, const Map& map, const Shared& sh, int* s_flag, int* s_rounds) {
     const int nr = a.H, nc = a.W;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int dirk = warp & 3, phase = warp >> 2;
+    const int dirk = warp & 3, phase = warp >> 2, nph = blockDim.x >> 7;
     const bool rows = dirk < 2;
     const int dir = (dirk & 1) ? -1 : +1;
     const int nlines = rows ? a.H : a.W;
-    int start = dir > 0 ? 0 : nlines - 1;
-    if (phase) start = dir > 0 ? nlines / 2 : (nlines / 2 - 1 + nlines) % nlines;
+    // phases of one direction start evenly spaced over the lines
+    const int off = (phase * nlines) / nph;
+    const int start = dir > 0 ? off : (nlines - 1 - off);
     int round = 0, nproc = 0;
     for (;;) {
         // clear the flag slot the next round will write (last used two rounds ago)
@@ -337,6 +338,24 @@ __device__ Shared setup_shared(const PropArgs& a, char* base) {
     return sh;
 }
 
+// Before the first round, the lines that hold a seed are the only ones
+// whose values differ from "unreached" (flag slot 2 is the one round 0
+// reads as "previous round").
+__device__ void flag_seed_lines(const PropArgs& a, const Shared& sh, int src) {
+    if (a.seed_flags) {
+        for (int p = threadIdx.x; p < a.N; p += blockDim.x)
+            if (a.seed_flags[p]) {
+                const int r = p / a.W, c = p - r * a.W;
+                sh.chR[2 * a.H + r] = 1;
+                sh.chC[2 * a.W + c] = 1;
+            }
+    } else if (threadIdx.x == 0 && src >= 0) {
+        const int r = src / a.W, c = src - r * a.W;
+        sh.chR[2 * a.H + r] = 1;
+        sh.chC[2 * a.W + c] = 1;
+    }
+}
+
 __host__ __device__ inline size_t shared_state_bytes(int H, int W) {
     return (((3 * (size_t)(H + W) + 2 * (size_t)H * W) + 15) & ~(size_t)15) + (size_t)(H + W) * 32 * sizeof(int);
 }
@@ -357,6 +376,8 @@ __global__ void __launch_bounds__(32 * MAXWARPS) k_propagate_smem(PropArgs a, in
     }
     const Shared sh = setup_shared<KIND, VPL>(a, reinterpret_cast<char*>(smap + a.H * pitch));
     if (threadIdx.x == 0) { s_flag[0] = 0; s_flag[1] = 0; }
+    __syncthreads();
+    flag_seed_lines(a, sh, src);
     __syncthreads();
     const SmemMap map{smap, pitch};
     run_block<CONN, KIND, VPL>(a, map, sh, s_flag, &s_rounds);
@@ -396,6 +417,8 @@ __global__ void __launch_bounds__(32 * MAXWARPS) k_propagate_glob(PropArgs a) {
     if (threadIdx.x == 0) { s_flag[0] = 0; s_flag[1] = 0; }
     __threadfence_block();
     __syncthreads();
+    flag_seed_lines(a, sh, src);
+    __syncthreads();
     const GlobMap gm{map, a.W};
     run_block<CONN, KIND, VPL>(a, gm, sh, s_flag, &s_rounds);
     __syncthreads();
@@ -417,7 +440,7 @@ cudaError_t launch_one(const PropArgs& a, int jobs, cudaStream_t st) {
     const int pitch = a.W | 1;  // odd pitch: row and column lines spread over the banks
     const size_t state = shared_state_bytes(a.H, a.W);
     const size_t smem = (size_t)a.H * pitch * sizeof(int) + state;
-    const int threads = 32 * 4 * (a.phases == 2 ? 2 : 1);
+    const int threads = 32 * 4 * (a.phases == 4 ? 4 : a.phases == 2 ? 2 : 1);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_propagate_smem<CONN, KIND, VPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,

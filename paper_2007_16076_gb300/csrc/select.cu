@@ -69,7 +69,11 @@ __device__ __forceinline__ unsigned long long mf_key(const SelectArgs& a, int p)
     return ((unsigned long long)c << 17) | (unsigned long long)r;
 }
 
+// Keys of the unfilled points are cached in shared memory when N <= 16384
+// (CACHED), and read from the counts otherwise.
+template <bool CACHED>
 __global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
+    extern __shared__ unsigned long long skeys[];
     __shared__ unsigned hist[256];
     __shared__ unsigned long long s_prefix;
     __shared__ int s_need, s_count, s_unfilled;
@@ -80,24 +84,32 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
     if (tid == 0) { s_unfilled = 0; s_count = 0; s_prefix = 0; }
     __syncthreads();
     int mine = 0;
-    for (int p = tid; p < a.N; p += SEL_THREADS) mine += mf_key(a, p) != ~0ull;
+    for (int p = tid; p < a.N; p += SEL_THREADS) {
+        const unsigned long long k = mf_key(a, p);
+        if (CACHED) skeys[p] = k;
+        mine += k != ~0ull;
+    }
     for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(FULL, mine, o);
     if ((tid & 31) == 0 && mine) atomicAdd(&s_unfilled, mine);
     __syncthreads();
+    auto key = [&](int p) -> unsigned long long { return CACHED ? skeys[p] : mf_key(a, p); };
     const int unfilled = s_unfilled;
     const int want = min(unfilled, a.B);
     unsigned long long thr = ~0ull - 1;  // select keys <= thr
     if (want > 0 && want < unfilled) {
-        // find the want-th smallest key, 8 bits at a time over 40 bits
+        // the want-th smallest key, 8 bits at a time from the top bit a key
+        // can have (rank in the low 17 bits, count above)
+        int top = 17;
+        for (int n = a.N - 1; n > 0; n >>= 1) ++top;
         if (tid == 0) s_need = want;
         unsigned long long prefix = 0;
-        for (int shift = 32; shift >= 0; shift -= 8) {
+        for (int shift = ((top - 1) / 8) * 8; shift >= 0; shift -= 8) {
             if (tid < 256) hist[tid] = 0;
             __syncthreads();
             for (int p = tid; p < a.N; p += SEL_THREADS) {
-                const unsigned long long k = mf_key(a, p);
+                const unsigned long long k = key(p);
                 if (k == ~0ull) continue;
-                if (shift + 8 < 64 && (k >> (shift + 8)) != (prefix >> (shift + 8))) continue;
+                if ((k >> (shift + 8)) != (prefix >> (shift + 8))) continue;
                 atomicAdd(&hist[(k >> shift) & 255], 1u);
             }
             __syncthreads();
@@ -134,7 +146,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
     // gather the selected points
     if (want > 0) {
         for (int p = tid; p < a.N; p += SEL_THREADS) {
-            const unsigned long long k = mf_key(a, p);
+            const unsigned long long k = key(p);
             if (k != ~0ull && k <= thr) {
                 const int slot = atomicAdd(&s_count, 1);
                 if (slot < 1024) { s_keys[slot] = k; s_pix[slot] = p; }
@@ -275,7 +287,19 @@ __global__ void k_components(CompArgs a) {
 }  // namespace
 
 cudaError_t launch_select(const SelectArgs& a, cudaStream_t st) {
-    if (a.order == 2) k_select_minfill<<<1, SEL_THREADS, 0, st>>>(a);
+    if (a.order == 2) {
+        if (a.N <= 16384) {
+            static bool attr = false;
+            if (!attr) {
+                cudaFuncSetAttribute(k_select_minfill<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     16384 * 8);
+                attr = true;
+            }
+            k_select_minfill<true><<<1, SEL_THREADS, (size_t)a.N * 8, st>>>(a);
+        } else {
+            k_select_minfill<false><<<1, SEL_THREADS, 0, st>>>(a);
+        }
+    }
     else k_select_seq<<<1, 32, 0, st>>>(a);
     return cudaGetLastError();
 }

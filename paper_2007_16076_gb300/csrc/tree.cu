@@ -211,8 +211,10 @@ __global__ void k_fill(TreeArgs a) {
                     a.dirty[ap] = 1;
                     ++fresh_b;
                     const uint32_t val = db - drow[ap];
-                    a.Dw[(size_t)ap * a.N + b] = val;
-                    a.Dw[(size_t)b * a.N + ap] = val;
+                    // streaming stores: D is far larger than L2, keep the
+                    // trees and marks resident instead
+                    __stcs(a.Dw + (size_t)ap * a.N + b, val);
+                    __stcs(a.Dw + (size_t)b * a.N + ap, val);
                 }
                 atomicOr(myrow + t, 1ull << bit);
             }

@@ -21,16 +21,18 @@ from paper_2007_16076_gb300 import synth  # noqa: E402
 
 WORKLOADS = {
     "blobs128": lambda: synth.batched_128(0),
+    "steps256": lambda: synth.steps_256(0),
+    "mask256": lambda: synth.mask_256(0),
 }
 
 
-def main(names):
+def main(names, orders=("minfill", "naive", "spiral")):
     for name in names:
         w = WORKLOADS[name]()
         out = {"workload": w.name, "H": w.H, "W": w.W, "conn": w.conn, "kind": w.kind,
                "B": w.B, "seed": w.meta.get("seed", 0), "spiral_seed": 0,
                "generator": "paper_2007_16076_gb300.synth", "orders": {}}
-        for order in ("minfill", "naive", "spiral"):
+        for order in orders:
             t = time.time()
             r = oracle.fill(w.img, order, B=w.B, seed=0, conn=w.conn, kind=w.kind, mask=w.mask)
             out["orders"][order] = {
@@ -47,4 +49,6 @@ def main(names):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or list(WORKLOADS))
+    args = [x for x in sys.argv[1:] if not x.startswith("--orders=")]
+    ords = [x.split("=", 1)[1].split(",") for x in sys.argv[1:] if x.startswith("--orders=")]
+    main(args or ["blobs128"], *(ords[:1] or []))
