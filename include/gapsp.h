@@ -179,6 +179,35 @@ gapsp_status gapsp_profile_read(gapsp_handle *h, double *ms, uint64_t *launches)
 gapsp_status gapsp_profile_trace(gapsp_handle *h, double *ms, uint64_t *launches,
                                  int32_t *kind, float *dur_ms, uint64_t cap, uint64_t *count);
 
+/*
+ * Rows without any allocation. The paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory when they call
+ * (an engine that owns the device through its own fixed pool, code where an
+ * allocation would stall the device or a latency budget, a host whose
+ * allocator is not the CUDA runtime's). It computes the same rows as
+ * gapsp_rows, needs no handle and allocates nothing: its only scratch (the
+ * device copy of the source list and a status word) is one fixed array of
+ * GAPSP_NOALLOC_MAX_SOURCES * 4 + 256 bytes that every GPU loading the
+ * library holds until the process exits.
+ *   img     : H*W uint8, DEVICE pointer: grey levels (GAPSP_GREY) or free
+ *             flags, nonzero = free (GAPSP_MASK).
+ *   sources : K int32 pixel indices, host or device pointer.
+ *   out     : caller-owned DEVICE uint32 K*N; out[k*N + q] = d(sources[k], q).
+ *   stream  : cudaStream_t the work runs on (NULL = default stream); the call
+ *             returns when the rows are complete.
+ * Limits: 0 <= K <= GAPSP_NOALLOC_MAX_SOURCES; H, W and N as gapsp_create.
+ * Errors: GAPSP_E_INVALID for sizes beyond the limits, a NULL pointer or a
+ * source outside [0, N) (nothing is written then); GAPSP_E_NOT_CONVERGED;
+ * GAPSP_E_CUDA.
+ * Every call shares the one array and it keeps the last call's contents:
+ * calls that overlap on the GPU race, so order them on one stream. The first
+ * call on a device looks up the array's address on that device; make it
+ * before any stream capture.
+ */
+#define GAPSP_NOALLOC_MAX_SOURCES 4096
+gapsp_status gapsp_rows_noalloc(const uint8_t *img, int H, int W, int conn, gapsp_kind kind,
+                                const int32_t *sources, int K, uint32_t *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

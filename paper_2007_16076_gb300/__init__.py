@@ -86,6 +86,9 @@ def load(build_if_missing: bool = True):
     lib.gapsp_profile_read.restype = ctypes.c_int
     lib.gapsp_profile_trace.argtypes = [P, P, P, P, P, ctypes.c_uint64, P]
     lib.gapsp_profile_trace.restype = ctypes.c_int
+    lib.gapsp_rows_noalloc.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       P, ctypes.c_int, P, P]
+    lib.gapsp_rows_noalloc.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -116,6 +119,27 @@ def _torch_stream(stream):
     if stream is None:
         return None
     return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+NOALLOC_MAX_SOURCES = 4096
+
+
+def rows_noalloc(img, sources, out, conn: int = 8, kind: str = "grey", stream=None):
+    """gapsp_rows_noalloc: rows d(sources[k], .) into `out` with no allocation.
+
+    `img` (uint8, H x W; free flags for the mask kind) and `out` (K x N) must
+    be CUDA tensors the caller owns; `sources` is host or device int32. For
+    callers that cannot allocate device memory at call time; calls share one
+    fixed scratch array, so order them on one stream.
+    """
+    lib = load()
+    H, W = int(img.shape[0]), int(img.shape[1])
+    K = int(sources.numel()) if hasattr(sources, "numel") else int(np.asarray(sources).size)
+    rc = lib.gapsp_rows_noalloc(_ptr(img), H, W, conn, KINDS[kind], _ptr(sources), K, _ptr(out),
+                                _torch_stream(stream))
+    if rc != 0:
+        raise GapspError(rc, "gapsp_rows_noalloc")
+    return out
 
 
 class Image:
