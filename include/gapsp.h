@@ -82,9 +82,11 @@ typedef struct {
     uint64_t seed;     /* seed of the spiral order's draws */
     size_t mem_budget; /* bytes of device memory a call may use (0 = no limit) */
     int sweep_phases;  /* warps per sweep direction in a propagation: 0 = auto, 1, 2 or 4 */
-    int reserved;      /* 0 */
+    int fill_rows;     /* rows of marks per tree-fill block: 0 = auto, else 1..32 */
     int checked;       /* reserved (0) */
     void *stream;      /* cudaStream_t the calls run on (NULL = default stream) */
+    int prop_blocks;   /* blocks (row strips, one thread-block cluster) per propagation:
+                          0 = auto, 1, 2 or 4 */
 } gapsp_opts;
 
 typedef struct {

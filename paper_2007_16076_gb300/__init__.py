@@ -37,8 +37,8 @@ class GapspError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("conn", ctypes.c_int), ("kind", ctypes.c_int), ("B", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("mem_budget", ctypes.c_size_t),
-                ("sweep_phases", ctypes.c_int), ("reserved", ctypes.c_int), ("checked", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("sweep_phases", ctypes.c_int), ("fill_rows", ctypes.c_int), ("checked", ctypes.c_int),
+                ("stream", ctypes.c_void_p), ("prop_blocks", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -146,7 +146,8 @@ class Image:
     """A handle on one image (gapsp_create / gapsp_destroy)."""
 
     def __init__(self, img, conn: int = 8, kind: str = "grey", mask=None, B: int = 32,
-                 seed: int = 0, mem_budget: int = 0, stream=None, sweep_phases: int = 0):
+                 seed: int = 0, mem_budget: int = 0, stream=None, sweep_phases: int = 0,
+                 fill_rows: int = 0, prop_blocks: int = 0):
         lib = load()
         self._lib = lib
         self._h = ctypes.c_void_p()
@@ -167,6 +168,8 @@ class Image:
         o.seed = seed & (2 ** 64 - 1)
         o.mem_budget = mem_budget
         o.sweep_phases = sweep_phases
+        o.fill_rows = fill_rows
+        o.prop_blocks = prop_blocks
         o.stream = _torch_stream(stream)
         self.H, self.W, self.N, self.conn, self.kind, self.B = H, W, H * W, conn, kind, B
         rc = lib.gapsp_create(_ptr(img_a), H, W, _ptr(mask_a), ctypes.byref(o), ctypes.byref(self._h))

@@ -27,6 +27,8 @@ struct gapsp_handle {
     cudaStream_t st = nullptr;
     int tiles_w = 0, tiles_h = 0, words = 0;
     int sweep_phases = 0;
+    int fill_rows = 0;
+    int prop_blocks = 0;
     uint64_t launches = 0;
     // image
     uint8_t* f = nullptr;
@@ -157,6 +159,10 @@ PropArgs base_prop(const gapsp_handle* h) {
     a.status = h->status;
     a.max_sweeps = 4 * (h->N + 2);
     a.phases = h->sweep_phases ? h->sweep_phases : 2;
+    // one block per source unless its map does not fit in one block's shared
+    // memory (then the launch splits it into row strips over a cluster);
+    // splitting smaller maps costs more rounds than it saves (measured)
+    a.cluster = h->prop_blocks ? h->prop_blocks : 1;
     return a;
 }
 
@@ -293,6 +299,9 @@ gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask,
     if (o.kind != GAPSP_GREY && o.kind != GAPSP_MASK) return GAPSP_E_INVALID;
     if (o.B < 1 || o.B > 1024) return GAPSP_E_INVALID;
     if (o.sweep_phases < 0 || o.sweep_phases > 4 || o.sweep_phases == 3) return GAPSP_E_INVALID;
+    if (o.fill_rows < 0 || o.fill_rows > 32) return GAPSP_E_INVALID;
+    if (o.prop_blocks != 0 && o.prop_blocks != 1 && o.prop_blocks != 2 && o.prop_blocks != 4)
+        return GAPSP_E_INVALID;
     if (o.kind == GAPSP_GREY && !img) return GAPSP_E_INVALID;
     if (o.kind == GAPSP_MASK && !mask) return GAPSP_E_INVALID;
 
@@ -301,6 +310,8 @@ gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask,
     h->H = H; h->W = W; h->N = H * W; h->conn = o.conn; h->kind = o.kind; h->B = o.B;
     h->seed = o.seed; h->budget = o.mem_budget; h->st = (cudaStream_t)o.stream;
     h->sweep_phases = o.sweep_phases;
+    h->fill_rows = o.fill_rows;
+    h->prop_blocks = o.prop_blocks;
     h->tiles_w = (W + 7) / 8; h->tiles_h = (H + 7) / 8; h->words = h->tiles_w * h->tiles_h;
     const size_t N = h->N;
     if (h->budget && N * 32 + 4096 > h->budget) { delete h; return GAPSP_E_BUDGET; }
@@ -396,6 +407,7 @@ gapsp_status gapsp_rows(gapsp_handle* h, const int32_t* sources, int K, uint32_t
     a.njobs = K;
     a.convert = h->kind == GAPSP_MASK;
     if (!h->sweep_phases) a.phases = K > 304 ? 1 : 2;  // latency-bound when few sources
+
     const int wpb = 1;
     {
         ProfScope ps(h, K_PROP, h->st);
@@ -520,7 +532,11 @@ gapsp_status gapsp_all_pairs(gapsp_handle* h, gapsp_order order, uint32_t* D, ga
     {
         const size_t row_bytes = (size_t)h->words * 8;
         int rpb = (int)((96 * 1024) / row_bytes);
-        ta.rows_per_block = rpb < 1 ? 1 : (rpb > 32 ? 32 : rpb);
+        // 8 rows per block: enough blocks per SM to hide the latency of the
+        // tree walks (measured best on the 128x128 workload)
+        ta.rows_per_block = rpb < 1 ? 1 : (rpb > 8 ? 8 : rpb);
+        if (h->fill_rows) ta.rows_per_block = h->fill_rows;
+        if ((size_t)ta.rows_per_block * row_bytes > 200 * 1024) ta.rows_per_block = rpb < 1 ? 1 : rpb;
     }
 
     const int max_rounds = h->N + 2;

@@ -23,6 +23,7 @@ struct PropArgs {
     int max_sweeps;
     int convert;                // write UNREACH for pixels never reached
     int phases;                 // warps per sweep direction (1, 2 or 4)
+    int cluster;                // blocks (row strips) per source: 1, 2 or 4
 };
 
 // Picks the per-lane width and launches kernel (a).

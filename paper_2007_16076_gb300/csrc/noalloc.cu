@@ -107,6 +107,7 @@ extern "C" gapsp_status gapsp_rows_noalloc(const uint8_t* img, int H, int W, int
     a.njobs = K;
     a.convert = kind == GAPSP_MASK;
     a.phases = K > 304 ? 1 : 2;
+    a.cluster = 1;
     if (launch_propagate(a, conn, (int)kind, K, 1, st) != cudaSuccess) {
         cudaGetLastError();
         return GAPSP_E_CUDA;

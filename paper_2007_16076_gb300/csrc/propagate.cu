@@ -31,8 +31,12 @@
 // pass per warp) in which no warp lowered anything: the map was constant
 // while every edge direction was tested. Rounds are capped; hitting the cap
 // sets a status bit instead of looping on.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace gapsp {
 
@@ -58,13 +62,24 @@ struct GlobMap {
     __device__ __forceinline__ void lower(int r, int c, int v) const { atomicMin(base + r * pitch + c, v); }
 };
 
-// Shared state of one block besides the map.
+// Shared state of one block besides the map. A block owns the strip of rows
+// [r0, r0 + hs) of the image (the whole image unless the source is split
+// over a cluster of blocks).
 struct Shared {
-    const uint8_t* fR;  // image, row-major
-    const uint8_t* fC;  // image, column-major
-    uint8_t* chR;       // [3][H]: row line lowered during round t (slot t % 3)
+    const uint8_t* fR;  // strip of the image, row-major [hs][W]
+    const uint8_t* fC;  // strip of the image, column-major [W][hs]
+    uint8_t* chR;       // [3][hs]: row line lowered during round t (slot t % 3)
     uint8_t* chC;       // [3][W]: column line lowered during round t
-    const int* Pb;      // [H + W][32]: prefix of the line's edge weights at each lane's first pixel
+    const int* Pb;      // [hs + W][32]: prefix of the line's edge weights at each lane's first pixel
+    int r0, hs;
+    // rows next to the strip, owned by the neighbour blocks of the cluster
+    // (distributed shared memory), or NULL at the image border
+    const int* up_map;        // neighbour above: its map; its last row is row r0 - 1
+    const uint8_t* up_chR;    // its row flags
+    int up_hs;
+    const int* dn_map;        // neighbour below: its map; its first row is row r0 + hs
+    const uint8_t* dn_chR;
+    int dn_hs;
 };
 
 // One pass over all lines in one direction during round `round`; true if
@@ -76,31 +91,57 @@ struct Shared {
 template <int CONN, int KIND, int VPL, bool ROWS, class Map>
 __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int dir, int start, int lane,
                       int round, int& nproc) {
-    const int nlines = ROWS ? a.H : a.W;
-    const int len = ROWS ? a.W : a.H;
+    const int nlines = ROWS ? sh.hs : a.W;
+    const int len = ROWS ? a.W : sh.hs;
     const uint8_t* f_line = ROWS ? sh.fR : sh.fC;
     uint8_t* ch_own = (ROWS ? sh.chR : sh.chC) + (round % 3) * nlines;
     uint8_t* ch_x = (ROWS ? sh.chC : sh.chR) + (round % 3) * len;
     const uint8_t* prev_own = (ROWS ? sh.chR : sh.chC) + ((round + 2) % 3) * nlines;
     const int wrap_at = dir > 0 ? 0 : nlines - 1;  // a sweep restarts here
-    const int* Pb = sh.Pb + (ROWS ? 0 : a.H * 32);
+    const int* Pb = sh.Pb + (ROWS ? 0 : sh.hs * 32);
     // gp[k]: cost of leaving the previous line's pixel, d + f (grey) or d (mask)
     int gp[VPL];
 #pragma unroll
     for (int k = 0; k < VPL; ++k) gp[k] = PINF;
+    bool has_pred = false;      // this line has a previous line in the sweep
     bool pred_changed = false;  // the previous line changed (it must be relaxed from)
     bool changed = false;
     int l = start;
     for (int i = 0; i < nlines; ++i) {
-        if (i > 0 && l == wrap_at) {  // restart: no previous line
+        if (i == 0 || l == wrap_at) {
+            // (re)start: the previous line is the neighbour block's edge row
+            // when the sweep enters the strip from a split border, else none
+            has_pred = false;
             pred_changed = false;
 #pragma unroll
             for (int k = 0; k < VPL; ++k) gp[k] = PINF;
+            if (ROWS) {
+                const int* rmap = nullptr;
+                const uint8_t* rch = nullptr;
+                int rrow = 0, rhs = 1, grow = 0;
+                if (dir > 0 && l == 0 && sh.up_map) {
+                    rmap = sh.up_map; rch = sh.up_chR; rhs = sh.up_hs; rrow = rhs - 1; grow = sh.r0 - 1;
+                } else if (dir < 0 && l == nlines - 1 && sh.dn_map) {
+                    rmap = sh.dn_map; rch = sh.dn_chR; rhs = sh.dn_hs; rrow = 0; grow = sh.r0 + sh.hs;
+                }
+                if (rmap) {
+                    has_pred = true;
+                    pred_changed = rch[((round + 2) % 3) * rhs + rrow] != 0 ||
+                                   *((volatile const uint8_t*)(rch + (round % 3) * rhs + rrow)) != 0;
+                    const int rpitch = a.W | 1;
+#pragma unroll
+                    for (int k = 0; k < VPL; ++k) {
+                        const int pos = VPL * lane + k;
+                        const int dv = pos < len ? *((volatile const int*)(rmap + rrow * rpitch + pos)) : PINF;
+                        gp[k] = (KIND == 0 && pos < len) ? dv + (int)__ldg(a.f + grow * a.W + pos) : dv;
+                    }
+                }
+            }
         }
         // lowered in the previous round, or already in this one (seen so far);
         // before the first round the lines holding a seed count as lowered
         const bool own_changed = prev_own[l] != 0 || *((volatile const uint8_t*)(ch_own + l)) != 0;
-        const bool skip = !own_changed && !((i > 0 && l != wrap_at) ? pred_changed : false);
+        const bool skip = !own_changed && !(has_pred && pred_changed);
         int fc[VPL];
 #pragma unroll
         for (int k = 0; k < VPL; ++k) {
@@ -114,6 +155,7 @@ __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int d
                 const int dv = pos < len ? (ROWS ? map.ld(l, pos) : map.ld(pos, l)) : PINF;
                 gp[k] = KIND == 0 ? dv + fc[k] : dv;
             }
+            has_pred = true;
             pred_changed = false;
             l += dir;
             if (l < 0) l += nlines;
@@ -239,6 +281,7 @@ __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int d
             ch_own[l] = 1;
             changed = true;
         }
+        has_pred = true;
         pred_changed = own_changed || __any_sync(FULL, mine);
         l += dir;
         if (l < 0) l += nlines;
@@ -247,14 +290,14 @@ __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int d
     return changed;
 }
 
-template <int CONN, int KIND, int VPL, class Map>
+template <int CONN, int KIND, int VPL, class Map, bool CL>
 __device__ void run_block(const PropArgs& a, const Map& map, const Shared& sh, int* s_flag, int* s_rounds) {
-    const int nr = a.H, nc = a.W;
+    const int nr = sh.hs, nc = a.W;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int dirk = warp & 3, phase = warp >> 2, nph = blockDim.x >> 7;
     const bool rows = dirk < 2;
     const int dir = (dirk & 1) ? -1 : +1;
-    const int nlines = rows ? a.H : a.W;
+    const int nlines = rows ? sh.hs : a.W;
     // phases of one direction start evenly spaced over the lines
     const int off = (phase * nlines) / nph;
     const int start = dir > 0 ? off : (nlines - 1 - off);
@@ -269,8 +312,18 @@ __device__ void run_block(const PropArgs& a, const Map& map, const Shared& sh, i
         else ch = sweep<CONN, KIND, VPL, false, Map>(a, map, sh, dir, start, lane, round, nproc);
         ch = __any_sync(FULL, ch);
         if (lane == 0 && ch) s_flag[round & 1] = 1;
-        __syncthreads();
-        const bool any = s_flag[round & 1] != 0;
+        bool any;
+        if (CL) {
+            // every block of the cluster has finished the round
+            cg::cluster_group cl = cg::this_cluster();
+            cl.sync();
+            any = false;
+            for (unsigned r = 0; r < cl.num_blocks(); ++r)
+                any |= *((volatile int*)cl.map_shared_rank(s_flag + (round & 1), r)) != 0;
+        } else {
+            __syncthreads();
+            any = s_flag[round & 1] != 0;
+        }
         if (threadIdx.x == 0) s_flag[(round + 1) & 1] = 0;
         ++round;
         if (!any) break;
@@ -292,37 +345,45 @@ __device__ __forceinline__ bool is_seed(const PropArgs& a, int src, int p) {
     return a.seed_flags ? a.seed_flags[p] != 0 : p == src;
 }
 
-// Lays out the non-map shared state after `base` and initialises it.
+__host__ __device__ inline size_t shared_state_bytes(int hs, int W) {
+    return (((3 * (size_t)(hs + W) + 2 * (size_t)hs * W) + 15) & ~(size_t)15) +
+           (size_t)(hs + W) * 32 * sizeof(int);
+}
+
+// Lays out the non-map shared state of the strip [r0, r0 + hs) after `base`
+// and initialises it.
 template <int KIND, int VPL>
-__device__ Shared setup_shared(const PropArgs& a, char* base) {
-    Shared sh;
+__device__ Shared setup_shared(const PropArgs& a, char* base, int r0, int hs) {
+    Shared sh{};
+    sh.r0 = r0;
+    sh.hs = hs;
     uint8_t* bp = reinterpret_cast<uint8_t*>(base);
     sh.chR = bp;
-    sh.chC = bp + 3 * a.H;
-    uint8_t* fR = bp + 3 * (a.H + a.W);
-    uint8_t* fC = fR + a.N;
-    for (int p = threadIdx.x; p < a.N; p += blockDim.x) {
-        const uint8_t v = a.f[p];
+    sh.chC = bp + 3 * hs;
+    uint8_t* fR = bp + 3 * (hs + a.W);
+    uint8_t* fC = fR + hs * a.W;
+    for (int p = threadIdx.x; p < hs * a.W; p += blockDim.x) {
         const int r = p / a.W, c = p - r * a.W;
+        const uint8_t v = a.f[(r0 + r) * a.W + c];
         fR[p] = v;
-        fC[c * a.H + r] = v;
+        fC[c * hs + r] = v;
     }
-    for (int i = threadIdx.x; i < 3 * (a.H + a.W); i += blockDim.x) bp[i] = 0;
+    for (int i = threadIdx.x; i < 3 * (hs + a.W); i += blockDim.x) bp[i] = 0;
     sh.fR = fR;
     sh.fC = fC;
     // lane bases of the line prefixes (grey): one warp per line
-    int* Pb = reinterpret_cast<int*>(bp + ((3 * (a.H + a.W) + 2 * a.N + 15) & ~15));
+    int* Pb = reinterpret_cast<int*>(bp + ((3 * (hs + a.W) + 2 * hs * a.W + 15) & ~15));
     sh.Pb = Pb;
     if (KIND == 0) {
         const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-        for (int l = threadIdx.x >> 5; l < a.H + a.W; l += nw) {
-            const bool rows = l < a.H;
-            const int line = rows ? l : l - a.H, len = rows ? a.W : a.H;
+        for (int l = threadIdx.x >> 5; l < hs + a.W; l += nw) {
+            const bool rows = l < hs;
+            const int line = rows ? l : l - hs, len = rows ? a.W : hs;
             int t = 0;
             for (int k = 0; k < VPL; ++k) {
                 const int c = VPL * lane + k;
                 if (c + 1 < len) {
-                    const int e0 = rows ? line * a.W + c : c * a.W + line;
+                    const int e0 = rows ? (r0 + line) * a.W + c : (r0 + c) * a.W + line;
                     const int e1 = rows ? e0 + 1 : e0 + a.W;
                     t += a.f[e0] + a.f[e1] + 1;
                 }
@@ -343,62 +404,84 @@ __device__ Shared setup_shared(const PropArgs& a, char* base) {
 // reads as "previous round").
 __device__ void flag_seed_lines(const PropArgs& a, const Shared& sh, int src) {
     if (a.seed_flags) {
-        for (int p = threadIdx.x; p < a.N; p += blockDim.x)
-            if (a.seed_flags[p]) {
+        for (int p = threadIdx.x; p < sh.hs * a.W; p += blockDim.x)
+            if (a.seed_flags[sh.r0 * a.W + p]) {
                 const int r = p / a.W, c = p - r * a.W;
-                sh.chR[2 * a.H + r] = 1;
+                sh.chR[2 * sh.hs + r] = 1;
                 sh.chC[2 * a.W + c] = 1;
             }
     } else if (threadIdx.x == 0 && src >= 0) {
-        const int r = src / a.W, c = src - r * a.W;
-        sh.chR[2 * a.H + r] = 1;
-        sh.chC[2 * a.W + c] = 1;
+        const int r = src / a.W - sh.r0, c = src % a.W;
+        if (r >= 0 && r < sh.hs) {
+            sh.chR[2 * sh.hs + r] = 1;
+            sh.chC[2 * a.W + c] = 1;
+        }
     }
 }
 
-__host__ __device__ inline size_t shared_state_bytes(int H, int W) {
-    return (((3 * (size_t)(H + W) + 2 * (size_t)H * W) + 15) & ~(size_t)15) + (size_t)(H + W) * 32 * sizeof(int);
-}
-
-// Map in shared memory; one block per job.
-template <int CONN, int KIND, int VPL>
-__global__ void __launch_bounds__(32 * MAXWARPS) k_propagate_smem(PropArgs a, int pitch) {
+// Map in shared memory. One block per job, or a cluster of C blocks per job
+// (CL), each owning a strip of rows; the strips see each other's edge rows
+// through distributed shared memory.
+template <int CONN, int KIND, int VPL, bool CL>
+__global__ void __launch_bounds__(32 * MAXWARPS) k_propagate_smem(PropArgs a, int pitch, int C) {
     extern __shared__ int smap[];
     __shared__ int s_flag[2], s_rounds;
-    const int j = blockIdx.x;
+    const int j = blockIdx.x / C, rank = blockIdx.x % C;
     const int njobs = a.njobs_dev ? *a.njobs_dev : a.njobs;
-    if (j >= njobs) return;
+    if (j >= njobs) return;  // the whole cluster leaves together
+    const int hs0 = (a.H + C - 1) / C;
+    const int r0 = rank * hs0, hs = min(hs0, a.H - r0);
     const int src = a.sources ? a.sources[j] : -1;
     int* out = a.map_base + (size_t)(a.map_row ? a.map_row[j] : j) * (size_t)a.N;
-    for (int p = threadIdx.x; p < a.N; p += blockDim.x) {
+    for (int p = threadIdx.x; p < hs * a.W; p += blockDim.x) {
         const int r = p / a.W, c = p - r * a.W;
-        smap[r * pitch + c] = is_seed(a, src, p) ? 0 : PINF;
+        smap[r * pitch + c] = is_seed(a, src, r0 * a.W + p) ? 0 : PINF;
     }
-    const Shared sh = setup_shared<KIND, VPL>(a, reinterpret_cast<char*>(smap + a.H * pitch));
+    Shared sh = setup_shared<KIND, VPL>(a, reinterpret_cast<char*>(smap + hs * pitch), r0, hs);
     if (threadIdx.x == 0) { s_flag[0] = 0; s_flag[1] = 0; }
     __syncthreads();
     flag_seed_lines(a, sh, src);
-    __syncthreads();
+    if (CL) {
+        cg::cluster_group cl = cg::this_cluster();
+        if (rank > 0) {
+            sh.up_map = cl.map_shared_rank(smap, rank - 1);
+            sh.up_hs = hs0;
+            sh.up_chR = reinterpret_cast<const uint8_t*>(sh.up_map + sh.up_hs * pitch);
+        }
+        if (rank + 1 < C) {
+            sh.dn_map = cl.map_shared_rank(smap, rank + 1);
+            sh.dn_hs = min(hs0, a.H - (rank + 1) * hs0);
+            sh.dn_chR = reinterpret_cast<const uint8_t*>(sh.dn_map + sh.dn_hs * pitch);
+        }
+        cl.sync();  // every strip is initialised before any remote access
+    } else {
+        __syncthreads();
+    }
     const SmemMap map{smap, pitch};
-    run_block<CONN, KIND, VPL>(a, map, sh, s_flag, &s_rounds);
+    run_block<CONN, KIND, VPL, SmemMap, CL>(a, map, sh, s_flag, &s_rounds);
+    if (CL) cg::this_cluster().sync();  // no block leaves while others may read it
     __syncthreads();
     if (threadIdx.x == 0 && a.sweeps) atomicAdd(a.sweeps, (unsigned long long)s_rounds * (blockDim.x >> 5));
-    // finished row: coalesced 128-bit stores
-    if ((a.N & 3) == 0 && (a.W & 3) == 0) {
-        int4* o4 = reinterpret_cast<int4*>(out);
-        for (int q = threadIdx.x; q < a.N / 4; q += blockDim.x) {
+    // finished strip of the row: coalesced 128-bit stores
+    const int n = hs * a.W;
+    int* o = out + (size_t)r0 * a.W;
+    if ((a.W & 3) == 0) {
+        int4* o4 = reinterpret_cast<int4*>(o);
+        for (int q = threadIdx.x; q < n / 4; q += blockDim.x) {
             const int p = 4 * q, r = p / a.W, c = p - r * a.W;
             const int* m = smap + r * pitch + c;
             o4[q] = make_int4(finish(a, m[0]), finish(a, m[1]), finish(a, m[2]), finish(a, m[3]));
         }
     } else {
-        for (int p = threadIdx.x; p < a.N; p += blockDim.x) {
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
             const int r = p / a.W, c = p - r * a.W;
-            out[p] = finish(a, smap[r * pitch + c]);
+            o[p] = finish(a, smap[r * pitch + c]);
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0 && a.convert && src >= 0 && KIND == 1 && !a.f[src]) out[src] = 0;
+    if (threadIdx.x == 0 && a.convert && src >= 0 && KIND == 1 && !a.f[src] && src / a.W >= r0 &&
+        src / a.W < r0 + hs)
+        out[src] = 0;
 }
 
 // Map in global memory (the output row itself), for images whose map does
@@ -413,14 +496,14 @@ __global__ void __launch_bounds__(32 * MAXWARPS) k_propagate_glob(PropArgs a) {
     const int src = a.sources ? a.sources[j] : -1;
     int* map = a.map_base + (size_t)(a.map_row ? a.map_row[j] : j) * (size_t)a.N;
     for (int p = threadIdx.x; p < a.N; p += blockDim.x) map[p] = is_seed(a, src, p) ? 0 : PINF;
-    const Shared sh = setup_shared<KIND, VPL>(a, reinterpret_cast<char*>(sbuf));
+    const Shared sh = setup_shared<KIND, VPL>(a, reinterpret_cast<char*>(sbuf), 0, a.H);
     if (threadIdx.x == 0) { s_flag[0] = 0; s_flag[1] = 0; }
     __threadfence_block();
     __syncthreads();
     flag_seed_lines(a, sh, src);
     __syncthreads();
     const GlobMap gm{map, a.W};
-    run_block<CONN, KIND, VPL>(a, gm, sh, s_flag, &s_rounds);
+    run_block<CONN, KIND, VPL, GlobMap, false>(a, gm, sh, s_flag, &s_rounds);
     __syncthreads();
     if (threadIdx.x == 0 && a.sweeps) atomicAdd(a.sweeps, (unsigned long long)s_rounds * (blockDim.x >> 5));
     if (a.convert) {
@@ -438,23 +521,50 @@ constexpr int SMEM_LIMIT = 220 * 1024;
 template <int CONN, int KIND, int VPL>
 cudaError_t launch_one(const PropArgs& a, int jobs, cudaStream_t st) {
     const int pitch = a.W | 1;  // odd pitch: row and column lines spread over the banks
-    const size_t state = shared_state_bytes(a.H, a.W);
-    const size_t smem = (size_t)a.H * pitch * sizeof(int) + state;
     const int threads = 32 * 4 * (a.phases == 4 ? 4 : a.phases == 2 ? 2 : 1);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_propagate_smem<CONN, KIND, VPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             SMEM_LIMIT);
+        cudaFuncSetAttribute(k_propagate_smem<CONN, KIND, VPL, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
+        cudaFuncSetAttribute(k_propagate_smem<CONN, KIND, VPL, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
         cudaFuncSetAttribute(k_propagate_glob<CONN, KIND, VPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              SMEM_LIMIT);
         attr = true;
     }
-    if (smem <= (size_t)SMEM_LIMIT) {
-        k_propagate_smem<CONN, KIND, VPL><<<jobs, threads, smem, st>>>(a, pitch);
-    } else if (state <= (size_t)SMEM_LIMIT) {
-        k_propagate_glob<CONN, KIND, VPL><<<jobs, threads, state, st>>>(a);
+    // strips per source: the requested cluster size, halved while a strip
+    // would be shorter than 8 rows, doubled while a strip does not fit
+    int C = a.cluster > 0 ? a.cluster : 1;
+    while (C > 1 && a.H / C < 8) C >>= 1;
+    auto smem_for = [&](int c) {
+        const int hs = (a.H + c - 1) / c;
+        return (size_t)hs * pitch * sizeof(int) + shared_state_bytes(hs, a.W);
+    };
+    while (smem_for(C) > (size_t)SMEM_LIMIT && C < 8 && a.H / (2 * C) >= 1) C <<= 1;
+    if (smem_for(C) <= (size_t)SMEM_LIMIT) {
+        const size_t smem = smem_for(C);
+        if (C == 1) {
+            k_propagate_smem<CONN, KIND, VPL, false><<<jobs, threads, smem, st>>>(a, pitch, 1);
+        } else {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(jobs * C);
+            cfg.blockDim = dim3(threads);
+            cfg.dynamicSmemBytes = smem;
+            cfg.stream = st;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = C;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            cudaError_t e = cudaLaunchKernelEx(&cfg, k_propagate_smem<CONN, KIND, VPL, true>, a, pitch, C);
+            if (e != cudaSuccess) return e;
+        }
     } else {
-        return cudaErrorInvalidValue;
+        const size_t state = shared_state_bytes(a.H, a.W);
+        if (state > (size_t)SMEM_LIMIT) return cudaErrorInvalidValue;
+        k_propagate_glob<CONN, KIND, VPL><<<jobs, threads, state, st>>>(a);
     }
     return cudaGetLastError();
 }
