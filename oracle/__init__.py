@@ -24,7 +24,7 @@ _lib = None
 
 UNREACH = 0xFFFFFFFF
 UNSET = 0xFFFFFFFE
-ORDERS = {"naive": 0, "spiral": 1, "minfill": 2}
+ORDERS = {"naive": 0, "spiral": 1, "minfill": 2, "extrema": 3}
 
 
 def build(force: bool = False) -> str:
@@ -195,9 +195,10 @@ def fill(img, order="minfill", B=1, seed=0, conn=8, kind="grey", mask=None,
          want_D=False) -> FillResult:
     """Simulate the method: fill D from geodesic trees in a source order.
 
-    Sec. 3: naive (raster), spiral (Algorithm "spiral method") and minimum
-    filling rate (Algorithm "method based on the filling rate"); B sources
-    are chosen per round from the state at the round's start.
+    Sec. 3: naive (raster), spiral (Algorithm "spiral method"), geodesic
+    extrema (Algorithm "geodesic extrema method") and minimum filling rate
+    (Algorithm "method based on the filling rate"); B sources are chosen per
+    round from the state at the round's start.
     """
     img, m, H, W, k = _prep(img, mask, kind)
     N = H * W

@@ -387,7 +387,7 @@ int or_extrema(const uint8_t *f, const uint8_t *mask, int H, int W, int conn, in
 /* geodesic tree and fills every (ancestor, vertex) pair by Property 1.       */
 /* ------------------------------------------------------------------------ */
 
-enum { OR_NAIVE = 0, OR_SPIRAL = 1, OR_MINFILL = 2 };
+enum { OR_NAIVE = 0, OR_SPIRAL = 1, OR_MINFILL = 2, OR_EXTREMA = 3 };
 
 /* stats[0] propagations, [1] pre-pass propagations, [2] distance operations
  * (sum over propagations of the depth of every reached vertex), [3] new
@@ -413,6 +413,7 @@ int or_fill(const uint8_t *f, const uint8_t *mask, int H, int W, int conn, int k
     int32_t *parent = (int32_t *)malloc((size_t)N * sizeof(int32_t));
     int32_t *seq = (int32_t *)malloc((size_t)N * sizeof(int32_t));
     int32_t *rank = (int32_t *)malloc((size_t)N * sizeof(int32_t));
+    uint32_t *gcen = (uint32_t *)malloc((size_t)N * sizeof(uint32_t));
     int32_t *S = (int32_t *)malloc((size_t)(B > 0 ? B : 1) * sizeof(int32_t));
     uint8_t *taken = (uint8_t *)calloc((size_t)N, 1);
     for (int i = 0; i < 8; i++) stats[i] = 0;
@@ -452,11 +453,10 @@ int or_fill(const uint8_t *f, const uint8_t *mask, int H, int W, int conn, int k
         nseq = or_spiral_sequence(mask, kind, H, W, seed, seq);
     } else {
         uint32_t *e = (uint32_t *)malloc((size_t)N * sizeof(uint32_t));
-        uint32_t *gd = (uint32_t *)malloc((size_t)N * sizeof(uint32_t));
         int32_t *cen = (int32_t *)malloc((size_t)N * sizeof(int32_t));
-        or_extrema(f, mask, H, W, conn, kind, e, gd, cen, rank);
+        or_extrema(f, mask, H, W, conn, kind, e, gcen, cen, rank);
         stats[1] = 2;
-        free(e); free(gd); free(cen);
+        free(e); free(cen);
     }
 
     int nsel_total = 0, rounds = 0, status = 0;
@@ -468,6 +468,24 @@ int or_fill(const uint8_t *f, const uint8_t *mask, int H, int W, int conn, int k
                 int p = seq[cursor++];
                 if (cnt[p] < (uint32_t)N) S[ns++] = p;
             }
+        } else if (order == OR_EXTREMA) {
+            /* Geodesic extrema method (Sec. 3.3, Algorithm "geodesic extrema
+             * method"): the unfilled points farthest from the centroid; among
+             * points at the same distance the least filled, then the
+             * smallest index. Plain repeated minimum search. */
+            for (int k = 0; k < B; k++) {
+                int best = -1;
+                for (int p = 0; p < N; p++) {
+                    if (comp[p] < 0 || cnt[p] >= (uint32_t)N || taken[p]) continue;
+                    if (best < 0 || gcen[p] > gcen[best] ||
+                        (gcen[p] == gcen[best] && cnt[p] < cnt[best]))
+                        best = p;
+                }
+                if (best < 0) break;
+                taken[best] = 1;
+                S[ns++] = best;
+            }
+            for (int t = 0; t < ns; t++) taken[S[t]] = 0;
         } else {
             /* The B unfilled points of least filling rate; ties go to the
              * greatest geodesic extremum (smallest rank). Plain repeated
@@ -518,7 +536,7 @@ int or_fill(const uint8_t *f, const uint8_t *mask, int H, int W, int conn, int k
         stats[3] += new_this_round;
     }
     stats[4] = (uint64_t)rounds;
-    free(taken); free(S); free(rank); free(seq); free(parent); free(d);
+    free(gcen); free(taken); free(S); free(rank); free(seq); free(parent); free(d);
     free(csize); free(comp); free(cnt); free(mrk);
     return status;
 }

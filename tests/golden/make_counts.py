@@ -44,6 +44,11 @@ def main(names, orders=("minfill", "naive", "spiral")):
             }
             print(name, order, r.counts(), f"{time.time() - t:.1f}s", flush=True)
         path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"counts_{name}.json")
+        if os.path.exists(path):  # keep orders computed by earlier runs
+            old = json.load(open(path))
+            if {k: old.get(k) for k in ("H", "W", "conn", "kind", "B", "seed")} == \
+                    {k: out[k] for k in ("H", "W", "conn", "kind", "B", "seed")}:
+                out["orders"] = {**old.get("orders", {}), **out["orders"]}
         with open(path, "w") as fh:
             json.dump(out, fh, indent=1)
 

@@ -300,7 +300,7 @@ def test_one_row_minfill_single_propagation(W):
     assert r.new_pairs == W * (W - 1) // 2
 
 
-@pytest.mark.parametrize("order", ["naive", "spiral", "minfill"])
+@pytest.mark.parametrize("order", ["naive", "spiral", "extrema", "minfill"])
 @pytest.mark.parametrize("B", [1, 3, 8])
 @pytest.mark.parametrize("conn", [4, 8])
 def test_fill_invariants(order, B, conn):
@@ -319,7 +319,7 @@ def test_fill_invariants(order, B, conn):
     assert r.rounds == -(-r.propagations // B)
 
 
-@pytest.mark.parametrize("order", ["naive", "spiral", "minfill"])
+@pytest.mark.parametrize("order", ["naive", "spiral", "extrema", "minfill"])
 def test_fill_mask_invariants(order):
     """Mask variant: pairs in different components are filled at the start
     with 'unreachable'; the trees fill exactly the same-component pairs."""
