@@ -6,7 +6,7 @@ Workload: the 128x128 blob image (N = 16384, 268M-entry uint32 array),
 one complete gapsp_all_pairs fill in the minimum-filling-rate order (the
 paper's method: extrema pre-pass, then rounds of selection, propagation,
 tree and fill). `value` = N^2 entries per step / step time, summed over
-ranks. The naive and spiral orders and the naive method without the tree
+ranks. The naive, spiral and extrema orders and the naive method without the tree
 (one propagation per pixel, gapsp_rows) are timed beside it.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -72,7 +72,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "500"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (FileNotFoundError, OSError):
             self.proc = None
@@ -276,7 +276,7 @@ def run_ours(a):
 
     extras = {}
     if not a.no_extras:
-        for order in ("naive", "spiral"):
+        for order in ("naive", "spiral", "extrema"):
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -302,6 +302,32 @@ def run_ours(a):
         ms = e0.elapsed_time(e1)
         extras["naive_full_rows"] = {"ms": ms, "entries_per_s": entries / (ms / 1e3),
                                      "propagations": N, "propagations_per_s": N / (ms / 1e3)}
+        # batched form: 64 images of uneven sizes filled side by side, against
+        # the same images one at a time
+        from paper_2007_16076_gb300 import synth
+        ws = synth.batch_64(seed=0)
+        ims = [gp.Image(b.img, conn=b.conn, B=b.B, stream=stream) for b in ws]
+        outs = [torch.empty((b.N, b.N), dtype=torch.int32, device="cuda") for b in ws]
+        gp.all_pairs_batch(ims, "minfill", outs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, bst = gp.all_pairs_batch(ims, "minfill", outs)
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for imb, ob in zip(ims, outs):
+            imb.all_pairs("minfill", out=ob)
+        torch.cuda.synchronize()
+        ts = time.perf_counter() - t0
+        ent = float(sum(b.N * b.N for b in ws))
+        extras["batch64_minfill"] = {
+            "images": len(ws), "entries": ent, "array_bytes": 4 * ent,
+            "ms": tb * 1e3, "entries_per_s": ent / tb, "one_at_a_time_ms": ts * 1e3,
+            "one_at_a_time_entries_per_s": ent / ts,
+            "propagations": int(sum(x["propagations"] for x in bst))}
+        for imb in ims:
+            imb.close()
+        del outs
 
     # end to end through the C ABI with host buffers: create from a host image,
     # fill into pinned host memory, destroy

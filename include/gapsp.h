@@ -15,9 +15,12 @@
  *     points plus Property 1 (Sec. 2): along the geodesic tree of a
  *     propagation from s, d(a,b) = d(s,b) - d(s,a) for every ancestor a of b;
  *   - sources are chosen in naive (raster) order, spiral order (Sec. 3.1,
- *     Algorithm "spiral method") or by minimum filling rate with ties to the
+ *     Algorithm "spiral method"), by decreasing distance from the geodesic
+ *     centroid with ties to the least filled point (Sec. 3.3, Algorithm
+ *     "geodesic extrema method") or by minimum filling rate with ties to the
  *     greatest geodesic extremum (Sec. 3.4, Algorithm "method based on the
- *     filling rate", with the extrema pre-pass of Sec. 3.3).
+ *     filling rate"); the last two take the extrema pre-pass of Sec. 3.3 (two
+ *     more propagations).
  *
  * An obstacle-mask variant is included: w = 2 between free pixels, obstacle
  * pixels have no edges, and pairs that no path joins hold GAPSP_UNREACH.
@@ -67,7 +70,8 @@ typedef enum {
 typedef enum {
     GAPSP_NAIVE = 0,   /* raster order, filled points skipped (Sec. 1 with the tree) */
     GAPSP_SPIRAL = 1,  /* Sec. 3.1, Algorithm "spiral method" */
-    GAPSP_MINFILL = 2  /* Sec. 3.4, Algorithm "method based on the filling rate" */
+    GAPSP_MINFILL = 2, /* Sec. 3.4, Algorithm "method based on the filling rate" */
+    GAPSP_EXTREMA = 3  /* Sec. 3.3, Algorithm "geodesic extrema method" */
 } gapsp_order;
 
 typedef enum {
@@ -139,6 +143,21 @@ gapsp_status gapsp_create(const uint8_t *img, int H, int W, const uint8_t *mask,
  */
 gapsp_status gapsp_all_pairs(gapsp_handle *h, gapsp_order order, uint32_t *D,
                              gapsp_stats *st);
+
+/*
+ * Batched form: fills the arrays of n images at once, one handle and one
+ * caller-owned array D[i] per image (device or host pointers, as for
+ * gapsp_all_pairs), all in the same order. The round loops of the images run
+ * side by side on one worker stream per image, so many small images keep
+ * the GPU busy together; every result and count equals that of
+ * gapsp_all_pairs on the image alone. The work is ordered after each
+ * handle's stream and each handle's stream is ordered after it.
+ *   st : NULL or n entries.
+ * Errors: GAPSP_E_INVALID (n < 0, NULL pointers, a handle given twice), and
+ * those of gapsp_all_pairs; on error the arrays are unspecified.
+ */
+gapsp_status gapsp_all_pairs_batch(gapsp_handle *const *h, int n, gapsp_order order,
+                                   uint32_t *const *D, gapsp_stats *st);
 
 /*
  * Single-source propagations (Sec. 1: "geodesic propagation"): out[k*N + q]

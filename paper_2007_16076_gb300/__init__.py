@@ -18,7 +18,7 @@ import numpy as np
 from . import _build
 
 UNREACH = 0xFFFFFFFF
-ORDERS = {"naive": 0, "spiral": 1, "minfill": 2}
+ORDERS = {"naive": 0, "spiral": 1, "minfill": 2, "extrema": 3}
 KINDS = {"grey": 0, "mask": 1}
 KERNELS = ("select", "propagate", "tree", "unused3", "fill", "init", "prepass", "unused7", "recount")
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "memory budget exceeded",
@@ -86,6 +86,8 @@ def load(build_if_missing: bool = True):
     lib.gapsp_profile_read.restype = ctypes.c_int
     lib.gapsp_profile_trace.argtypes = [P, P, P, P, P, ctypes.c_uint64, P]
     lib.gapsp_profile_trace.restype = ctypes.c_int
+    lib.gapsp_all_pairs_batch.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P]
+    lib.gapsp_all_pairs_batch.restype = ctypes.c_int
     lib.gapsp_rows_noalloc.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        P, ctypes.c_int, P, P]
     lib.gapsp_rows_noalloc.restype = ctypes.c_int
@@ -119,6 +121,30 @@ def _torch_stream(stream):
     if stream is None:
         return None
     return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+def all_pairs_batch(images, order: str = "minfill", outs=None):
+    """gapsp_all_pairs_batch: fills the arrays of several images at once.
+
+    `images` is a list of :class:`Image` handles; `outs` (optional) one
+    N_i x N_i array per image (CUDA tensors by default). Returns (outs, stats
+    list); every result equals that of ``Image.all_pairs`` alone.
+    """
+    lib = load()
+    n = len(images)
+    if outs is None:
+        import torch
+        outs = [torch.empty((im.N, im.N), dtype=torch.int32, device="cuda") for im in images]
+    hs = (ctypes.c_void_p * max(n, 1))(*[im._h for im in images])
+    ds = (ctypes.c_void_p * max(n, 1))(*[_ptr(o) for o in outs])
+    sts = (Stats * max(n, 1))()
+    rc = lib.gapsp_all_pairs_batch(hs, n, ORDERS[order], ds, sts)
+    if rc != 0:
+        raise GapspError(rc, "gapsp_all_pairs_batch")
+    stats = [{"propagations": sts[i].propagations, "prepass_propagations": sts[i].prepass_propagations,
+              "distance_ops": sts[i].distance_ops, "new_pairs": sts[i].new_pairs,
+              "rounds": sts[i].rounds, "ms_total": sts[i].ms_total} for i in range(n)]
+    return outs, stats
 
 
 NOALLOC_MAX_SOURCES = 4096

@@ -55,6 +55,7 @@ struct gapsp_handle {
     int* done = nullptr;
     int32_t* seq = nullptr;
     int32_t* rank = nullptr;
+    int32_t* grank = nullptr;
     unsigned long long* stats = nullptr;
     unsigned long long* round_new = nullptr;
     unsigned long long* last_new = nullptr;
@@ -168,7 +169,10 @@ PropArgs base_prop(const gapsp_handle* h) {
 
 size_t fill_state_bytes(const gapsp_handle* h) {
     const size_t N = h->N, B = h->B;
-    return N * h->words * 8 + B * N * (4 + 16 + 16) + N * (4 + 4 + 4 + 4 + 8 + 8 + 1 + 4) + 4096;
+    // marks; parent, seg, jmp, acc per source; cnt, cnt_base, dirty, seq,
+    // rank, grank, round_new, sel_log, emap, gmap, best, cen per point
+    return N * h->words * 8 + B * N * (4 + 16 + 8 + 8) +
+           N * (4 + 4 + 1 + 4 + 4 + 4 + 8 + 4 + 4 + 4 + 8 + 1) + 4096;
 }
 
 gapsp_status ensure_fill_state(gapsp_handle* h) {
@@ -188,6 +192,7 @@ gapsp_status ensure_fill_state(gapsp_handle* h) {
     CK(dalloc(&h->done, 1));
     CK(dalloc(&h->seq, N));
     CK(dalloc(&h->rank, N));
+    CK(dalloc(&h->grank, N));
     CK(dalloc(&h->stats, S_SLOTS));
     CK(dalloc(&h->round_new, N + 1));
     CK(dalloc(&h->last_new, 1));
@@ -205,7 +210,7 @@ void free_all(gapsp_handle* h) {
     dfree(h->f); dfree(h->Prow); dfree(h->Pcol); dfree(h->bound); dfree(h->comp);
     dfree(h->comp_size); dfree(h->status); dfree(h->changed);
     dfree(h->cnt); dfree(h->cnt_base); dfree(h->dirty); dfree(h->marks); dfree(h->parent); dfree(h->seg); dfree(h->jmp); dfree(h->acc);
-    dfree(h->sel); dfree(h->nsel); dfree(h->cursor); dfree(h->done); dfree(h->seq); dfree(h->rank);
+    dfree(h->sel); dfree(h->nsel); dfree(h->cursor); dfree(h->done); dfree(h->seq); dfree(h->rank); dfree(h->grank);
     dfree(h->stats); dfree(h->round_new); dfree(h->last_new); dfree(h->sel_log);
     dfree(h->emap); dfree(h->gmap); dfree(h->best); dfree(h->cen);
     dfree(h->Dtmp); dfree(h->src_dev); dfree(h->out_tmp);
@@ -421,45 +426,67 @@ gapsp_status gapsp_rows(gapsp_handle* h, const int32_t* sources, int K, uint32_t
     return status_from_word(sw);
 }
 
-gapsp_status gapsp_all_pairs(gapsp_handle* h, gapsp_order order, uint32_t* D, gapsp_stats* st) {
-    if (!h || !D) return GAPSP_E_INVALID;
-    if (order != GAPSP_NAIVE && order != GAPSP_SPIRAL && order != GAPSP_MINFILL) return GAPSP_E_INVALID;
+}  // extern "C"
+
+namespace {
+
+// One fill in progress: the state of gapsp_all_pairs between its steps, so
+// that several fills (one per image) can advance side by side.
+struct FillRun {
+    gapsp_handle* h = nullptr;
+    gapsp_order order = GAPSP_MINFILL;
+    uint32_t* D = nullptr;   // caller's array
+    uint32_t* Dd = nullptr;  // device array the kernels fill
+    bool d_dev = true;
+    cudaStream_t s = nullptr;
+    int nseq = 0;
+    uint64_t prepass = 0;
+    SelectArgs sa{};
+    PropArgs pa{};
+    TreeArgs ta{};
+    int rounds = 0;
+    bool finished = false;
+};
+
+gapsp_status fill_begin(FillRun& r) {
+    gapsp_handle* h = r.h;
     const size_t N = h->N;
-    const bool d_dev = is_device_ptr(D);
+    r.d_dev = is_device_ptr(r.D);
     const size_t dbytes = N * N * sizeof(uint32_t);
-    const size_t need = fill_state_bytes(h) + (d_dev ? 0 : dbytes);
+    const size_t need = fill_state_bytes(h) + (r.d_dev ? 0 : dbytes);
     if (h->budget && need > h->budget) return GAPSP_E_BUDGET;
     gapsp_status gs = ensure_fill_state(h);
     if (gs != GAPSP_OK) return gs;
-    uint32_t* Dd = D;
-    if (!d_dev) {
+    r.Dd = r.D;
+    if (!r.d_dev) {
         if (h->Dtmp_bytes < dbytes) {
             dfree(h->Dtmp);
             h->Dtmp_bytes = 0;
             CK(dalloc(&h->Dtmp, N * N));
             h->Dtmp_bytes = dbytes;
         }
-        Dd = h->Dtmp;
+        r.Dd = h->Dtmp;
     }
-    cudaStream_t s = h->st;
+    cudaStream_t s = r.s;
+    uint32_t* Dd = r.Dd;
 
     // host-built sequences (naive / spiral)
-    int nseq = 0;
-    if (order != GAPSP_MINFILL) {
+    const bool ranked = r.order == GAPSP_MINFILL || r.order == GAPSP_EXTREMA;
+    if (!ranked) {
         std::vector<uint8_t> freef;
         if (h->kind == GAPSP_MASK) {
             freef.resize(N);
             CK(cudaMemcpy(freef.data(), h->f, N, cudaMemcpyDeviceToHost));
         }
         std::vector<int32_t> seq;
-        if (order == GAPSP_NAIVE) {
+        if (r.order == GAPSP_NAIVE) {
             for (int p = 0; p < h->N; ++p)
                 if (freef.empty() || freef[p]) seq.push_back(p);
         } else {
             seq = spiral_sequence(h->H, h->W, h->seed, freef);
         }
-        nseq = (int)seq.size();
-        if (nseq) CK(cudaMemcpyAsync(h->seq, seq.data(), nseq * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        r.nseq = (int)seq.size();
+        if (r.nseq) CK(cudaMemcpyAsync(h->seq, seq.data(), r.nseq * sizeof(int32_t), cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));  // the host vector goes out of scope
     }
 
@@ -480,8 +507,8 @@ gapsp_status gapsp_all_pairs(gapsp_handle* h, gapsp_order order, uint32_t* D, ga
     CK(cudaMemsetAsync(h->dirty, 0, N, s));
     h->launches += 1;
 
-    uint64_t prepass = 0;
-    if (order == GAPSP_MINFILL) {
+    r.prepass = 0;
+    if (ranked) {
         // geodesic extrema (Sec. 3.3): distance from the boundary vertices,
         // centroid(s), distance from the centroid(s), rank in Ext
         PropArgs a = base_prop(h);
@@ -494,7 +521,7 @@ gapsp_status gapsp_all_pairs(gapsp_handle* h, gapsp_order order, uint32_t* D, ga
             CK(launch_propagate(a, h->conn, h->kind, 1, 1, s));
         }
         ExtremaArgs ea{h->N, h->kind == GAPSP_MASK ? h->f : nullptr, h->comp, h->emap, h->best, h->cen,
-                       h->gmap, h->rank};
+                       h->gmap, h->rank, h->grank};
         {
             ProfScope ps(h, K_PRE, s);
             CK(launch_centroids(ea, s));
@@ -510,19 +537,21 @@ gapsp_status gapsp_all_pairs(gapsp_handle* h, gapsp_order order, uint32_t* D, ga
             CK(launch_rank(ea, s));
         }
         h->launches += 6;
-        prepass = 2;
+        r.prepass = 2;
     }
 
-    SelectArgs sa{h->N, h->B, (int)order, h->cnt, h->rank, h->seq, nseq, h->cursor, h->sel, h->nsel,
-                  h->stats, h->round_new, h->last_new, h->sel_log, h->done};
-    PropArgs pa = base_prop(h);
+    r.sa = SelectArgs{h->N, h->B, (int)r.order, h->cnt, h->rank, h->grank, h->seq, r.nseq, h->cursor, h->sel, h->nsel,
+                      h->stats, h->round_new, h->last_new, h->sel_log, h->done};
+    PropArgs& pa = r.pa;
+    pa = base_prop(h);
     pa.map_base = (int*)Dd;
     pa.map_row = h->sel;
     pa.sources = h->sel;
     pa.njobs_dev = h->nsel;
     pa.convert = h->kind == GAPSP_MASK;
     pa.sweeps = h->stats + S_SWEEPS;
-    TreeArgs ta{};
+    TreeArgs& ta = r.ta;
+    ta = TreeArgs{};
     ta.H = h->H; ta.W = h->W; ta.N = h->N; ta.conn = h->conn; ta.kind = h->kind;
     ta.tiles_w = h->tiles_w; ta.words = h->words;
     ta.f = h->f; ta.D = Dd; ta.sel = h->sel; ta.nsel = h->nsel;
@@ -538,44 +567,55 @@ gapsp_status gapsp_all_pairs(gapsp_handle* h, gapsp_order order, uint32_t* D, ga
         if (h->fill_rows) ta.rows_per_block = h->fill_rows;
         if ((size_t)ta.rows_per_block * row_bytes > 200 * 1024) ta.rows_per_block = rpb < 1 ? 1 : rpb;
     }
+    r.rounds = 0;
+    r.finished = false;
+    return GAPSP_OK;
+}
 
-    const int max_rounds = h->N + 2;
-    const int chunk = 16;
-    int rounds = 0;
-    bool finished = false;
-    while (!finished) {
-        for (int i = 0; i < chunk; ++i) {
-            {
-                ProfScope ps(h, K_SELECT, s);
-                CK(launch_select(sa, s));
-            }
-            {
-                ProfScope ps(h, K_PROP, s);
-                CK(launch_propagate(pa, h->conn, h->kind, h->B, 1, s));
-            }
-            {
-                ProfScope ps(h, K_TREE, s);
-                CK(launch_tree(ta, h->B, s));
-            }
-            {
-                ProfScope ps(h, K_FILL, s);
-                CK(launch_fill(ta, h->B, s));
-            }
-            {
-                ProfScope ps(h, K_RECOUNT, s);
-                CK(launch_recount(ta, s));
-            }
-            h->launches += 5;
+// Enqueues `chunk` rounds and an asynchronous copy of the "done" flag.
+gapsp_status fill_enqueue(FillRun& r, int chunk) {
+    gapsp_handle* h = r.h;
+    cudaStream_t s = r.s;
+    for (int i = 0; i < chunk; ++i) {
+        {
+            ProfScope ps(h, K_SELECT, s);
+            CK(launch_select(r.sa, s));
         }
-        rounds += chunk;
-        CK(cudaMemcpyAsync(h->h_done, h->done, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        finished = *h->h_done != 0;
-        if (!finished && rounds > max_rounds) {
-            CK(cudaStreamSynchronize(s));
-            return GAPSP_E_TIMEOUT;
+        {
+            ProfScope ps(h, K_PROP, s);
+            CK(launch_propagate(r.pa, h->conn, h->kind, h->B, 1, s));
         }
+        {
+            ProfScope ps(h, K_TREE, s);
+            CK(launch_tree(r.ta, h->B, s));
+        }
+        {
+            ProfScope ps(h, K_FILL, s);
+            CK(launch_fill(r.ta, h->B, s));
+        }
+        {
+            ProfScope ps(h, K_RECOUNT, s);
+            CK(launch_recount(r.ta, s));
+        }
+        h->launches += 5;
     }
+    r.rounds += chunk;
+    CK(cudaMemcpyAsync(h->h_done, h->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+    return GAPSP_OK;
+}
+
+// Waits for the enqueued rounds and reads the "done" flag.
+gapsp_status fill_poll(FillRun& r) {
+    CK(cudaStreamSynchronize(r.s));
+    r.finished = *r.h->h_done != 0;
+    if (!r.finished && r.rounds > r.h->N + 2) return GAPSP_E_TIMEOUT;
+    return GAPSP_OK;
+}
+
+gapsp_status fill_finish(FillRun& r, gapsp_stats* st) {
+    gapsp_handle* h = r.h;
+    cudaStream_t s = r.s;
+    const size_t N = h->N;
     CK(cudaEventRecord(h->ev1, s));
     unsigned long long hs[S_SLOTS];
     int sw = 0;
@@ -584,7 +624,7 @@ gapsp_status gapsp_all_pairs(gapsp_handle* h, gapsp_order order, uint32_t* D, ga
     CK(cudaStreamSynchronize(s));
     if (st) {
         st->propagations = hs[S_PROPAGATIONS];
-        st->prepass_propagations = prepass;
+        st->prepass_propagations = r.prepass;
         st->distance_ops = hs[S_OPS];
         st->new_pairs = hs[S_NEW];
         st->rounds = hs[S_ROUNDS];
@@ -613,8 +653,89 @@ gapsp_status gapsp_all_pairs(gapsp_handle* h, gapsp_order order, uint32_t* D, ga
             st->prefilled_pairs = (uint64_t)N * (N - 1) / 2 - same;
         }
     }
-    if (!d_dev) CK(cudaMemcpy(D, Dd, dbytes, cudaMemcpyDeviceToHost));
+    if (!r.d_dev) CK(cudaMemcpyAsync(r.D, r.Dd, N * N * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
     return status_from_word(sw);
+}
+
+bool valid_order(gapsp_order o) {
+    return o == GAPSP_NAIVE || o == GAPSP_SPIRAL || o == GAPSP_MINFILL || o == GAPSP_EXTREMA;
+}
+
+}  // namespace
+
+extern "C" {
+
+gapsp_status gapsp_all_pairs(gapsp_handle* h, gapsp_order order, uint32_t* D, gapsp_stats* st) {
+    if (!h || !D) return GAPSP_E_INVALID;
+    if (!valid_order(order)) return GAPSP_E_INVALID;
+    FillRun r;
+    r.h = h;
+    r.order = order;
+    r.D = D;
+    r.s = h->st;
+    gapsp_status gs = fill_begin(r);
+    if (gs != GAPSP_OK) return gs;
+    while (!r.finished) {
+        if ((gs = fill_enqueue(r, 16)) != GAPSP_OK) return gs;
+        if ((gs = fill_poll(r)) != GAPSP_OK) return gs;
+    }
+    return fill_finish(r, st);
+}
+
+gapsp_status gapsp_all_pairs_batch(gapsp_handle* const* hs, int n, gapsp_order order, uint32_t* const* Ds,
+                                   gapsp_stats* st) {
+    if (n < 0 || (n > 0 && (!hs || !Ds))) return GAPSP_E_INVALID;
+    if (!valid_order(order)) return GAPSP_E_INVALID;
+    for (int i = 0; i < n; ++i) {
+        if (!hs[i] || !Ds[i]) return GAPSP_E_INVALID;
+        for (int k = 0; k < i; ++k)
+            if (hs[k] == hs[i]) return GAPSP_E_INVALID;  // one fill per handle
+    }
+    if (n == 0) return GAPSP_OK;
+    // one worker stream per image, ordered after the handle's own stream
+    std::vector<cudaStream_t> ws(n, nullptr);
+    std::vector<FillRun> runs(n);
+    gapsp_status result = GAPSP_OK;
+    for (int i = 0; i < n && result == GAPSP_OK; ++i) {
+        cudaEvent_t e = nullptr;
+        if (cudaStreamCreateWithFlags(&ws[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventRecord(e, hs[i]->st) != cudaSuccess || cudaStreamWaitEvent(ws[i], e, 0) != cudaSuccess) {
+            cudaGetLastError();
+            result = GAPSP_E_CUDA;
+        }
+        if (e) cudaEventDestroy(e);
+        runs[i].h = hs[i];
+        runs[i].order = order;
+        runs[i].D = Ds[i];
+        runs[i].s = ws[i];
+    }
+    for (int i = 0; i < n && result == GAPSP_OK; ++i) result = fill_begin(runs[i]);
+    bool all = false;
+    while (result == GAPSP_OK && !all) {
+        for (int i = 0; i < n && result == GAPSP_OK; ++i)
+            if (!runs[i].finished) result = fill_enqueue(runs[i], 16);
+        all = true;
+        for (int i = 0; i < n && result == GAPSP_OK; ++i)
+            if (!runs[i].finished) {
+                result = fill_poll(runs[i]);
+                all = all && runs[i].finished;
+            }
+    }
+    for (int i = 0; i < n && result == GAPSP_OK; ++i) result = fill_finish(runs[i], st ? st + i : nullptr);
+    for (int i = 0; i < n; ++i) {
+        if (!ws[i]) continue;
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
+            cudaEventRecord(e, ws[i]);
+            cudaStreamWaitEvent(hs[i]->st, e, 0);
+            cudaEventDestroy(e);
+        }
+        cudaStreamDestroy(ws[i]);
+    }
+    cudaGetLastError();
+    return result;
 }
 
 gapsp_status gapsp_profile_enable(gapsp_handle* h, int enable) {

@@ -64,9 +64,10 @@ cudaError_t launch_fill(const TreeArgs& a, int B, cudaStream_t st);
 cudaError_t launch_recount(const TreeArgs& a, cudaStream_t st);
 
 struct SelectArgs {
-    int N, B, order;            // 0 naive / 1 spiral (sequence), 2 minfill
+    int N, B, order;            // 0 naive / 1 spiral (sequence), 2 minfill, 3 extrema
     const uint32_t* cnt;
-    const int32_t* rank;        // minfill
+    const int32_t* rank;        // minfill: position in Ext
+    const int32_t* grank;       // extrema: free points strictly farther from the centroid
     const int32_t* seq;         // naive / spiral sequence
     int nseq;
     int* cursor;                // sequence cursor
@@ -99,6 +100,7 @@ struct ExtremaArgs {
     uint8_t* cen_flags;         // [N] centroid seeds
     const uint32_t* g;          // distance from the centroids
     int32_t* rank;              // [N]
+    int32_t* grank;             // [N]
 };
 cudaError_t launch_centroids(const ExtremaArgs& a, cudaStream_t st);
 cudaError_t launch_rank(const ExtremaArgs& a, cudaStream_t st);

@@ -243,10 +243,15 @@ __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int d
             for (int off = 1; off < 32; off <<= 1) {
                 const int tx2 = __shfl_up_sync(FULL, tx, off);
                 const int ty2 = __shfl_down_sync(FULL, ty, off);
-                const bool hx2 = __shfl_up_sync(FULL, (int)hx, off);
-                const bool hy2 = __shfl_down_sync(FULL, (int)hy, off);
-                if (lane >= off && !hx) { tx = min(tx, tx2); hx = hx2; }
-                if (lane + off < 32 && !hy) { ty = min(ty, ty2); hy = hy2; }
+                if (KIND == 1) {  // segmented scans: stop at a lane holding an obstacle
+                    const bool hx2 = __shfl_up_sync(FULL, (int)hx, off);
+                    const bool hy2 = __shfl_down_sync(FULL, (int)hy, off);
+                    if (lane >= off && !hx) { tx = min(tx, tx2); hx = hx2; }
+                    if (lane + off < 32 && !hy) { ty = min(ty, ty2); hy = hy2; }
+                } else {
+                    if (lane >= off) tx = min(tx, tx2);
+                    if (lane + off < 32) ty = min(ty, ty2);
+                }
             }
             int ex = __shfl_up_sync(FULL, tx, 1);
             int ey = __shfl_down_sync(FULL, ty, 1);

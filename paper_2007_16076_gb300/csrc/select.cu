@@ -7,7 +7,10 @@
 //  - minimum filling rate (Algorithm "method based on the filling rate"):
 //    the B unfilled points with the smallest fill count cnt, ties going to
 //    the greatest geodesic extremum, i.e. the smallest position in the
-//    extrema list Ext (Sec. 3.3). With B = 1 this is the paper's loop.
+//    extrema list Ext (Sec. 3.3). With B = 1 this is the paper's loop;
+//  - geodesic extrema (Algorithm "geodesic extrema method"): the B unfilled
+//    points farthest from the geodesic centroid, ties going to the smallest
+//    fill count, then to the smallest index.
 // "Filled" is tau(x) = 1, i.e. cnt(x) = N (Sec. 2, eq. "filling rate pt").
 #include "common.cuh"
 #include "internal.h"
@@ -58,14 +61,20 @@ __global__ void k_select_seq(SelectArgs a) {
     }
 }
 
-// Minimum filling rate: radix selection of the B smallest keys
-// (cnt << 17 | rank) among unfilled points, one block of 1024 threads.
+// Radix selection of the B smallest keys among unfilled points, one block of
+// 1024 threads. Keys are distinct and below 2^50 (N <= 2^16, cnt <= 2^16):
+//   minimum filling rate:  cnt << 17 | rank
+//   geodesic extrema:      grank << 34 | cnt << 17 | p
+// where grank counts the free points strictly farther from the centroid, so
+// that a smaller grank is a farther point and equal distances share it.
 constexpr int SEL_THREADS = 1024;
 
 __device__ __forceinline__ unsigned long long mf_key(const SelectArgs& a, int p) {
     const uint32_t c = a.cnt[p];
     const int32_t r = a.rank[p];
     if (c >= (uint32_t)a.N || r < 0) return ~0ull;
+    if (a.order == 3)
+        return ((unsigned long long)a.grank[p] << 34) | ((unsigned long long)c << 17) | (unsigned long long)p;
     return ((unsigned long long)c << 17) | (unsigned long long)r;
 }
 
@@ -98,8 +107,8 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
     unsigned long long thr = ~0ull - 1;  // select keys <= thr
     if (want > 0 && want < unfilled) {
         // the want-th smallest key, 8 bits at a time from the top bit a key
-        // can have (rank in the low 17 bits, count above)
-        int top = 17;
+        // can have (17 bits per field below the top one)
+        int top = a.order == 3 ? 34 : 17;
         for (int n = a.N - 1; n > 0; n >>= 1) ++top;
         if (tid == 0) s_need = want;
         unsigned long long prefix = 0;
@@ -216,14 +225,15 @@ __global__ void k_centroid_mark(ExtremaArgs a) {
 }
 
 // Position in the extrema list Ext: free pixels by decreasing distance from
-// the centroid, ties by increasing index. Counted directly.
+// the centroid, ties by increasing index; and the number of free pixels
+// strictly farther from the centroid. Counted directly.
 __global__ void k_rank(ExtremaArgs a) {
     __shared__ uint32_t sg[1024];
     __shared__ uint8_t sf[1024];
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const bool have = p < a.N && (!a.freef || a.freef[p]);
     const uint32_t gp = have ? a.g[p] : 0;
-    int r = 0;
+    int r = 0, gr = 0;
     for (int base = 0; base < a.N; base += 1024) {
         __syncthreads();
         for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
@@ -237,10 +247,14 @@ __global__ void k_rank(ExtremaArgs a) {
             for (int i = 0; i < lim; ++i) {
                 const int q = base + i;
                 r += sf[i] && (sg[i] > gp || (sg[i] == gp && q < p));
+                gr += sf[i] && sg[i] > gp;
             }
         }
     }
-    if (p < a.N) a.rank[p] = have ? r : -1;
+    if (p < a.N) {
+        a.rank[p] = have ? r : -1;
+        a.grank[p] = have ? gr : -1;
+    }
 }
 
 // Connected components of free pixels by minimum-label propagation with
@@ -287,7 +301,7 @@ __global__ void k_components(CompArgs a) {
 }  // namespace
 
 cudaError_t launch_select(const SelectArgs& a, cudaStream_t st) {
-    if (a.order == 2) {
+    if (a.order == 2 || a.order == 3) {
         if (a.N <= 16384) {
             static bool attr = false;
             if (!attr) {

@@ -74,22 +74,33 @@ __global__ void __launch_bounds__(1024) k_tree(TreeArgs a) {
     int32_t* par = a.parent + (size_t)j * N;
     ulonglong2* seg = a.seg + (size_t)j * N;
     const TileGeom tg{a.W, a.tiles_w, a.words};
-    uint16_t* spar = sdep + 4 * N;  // parent + 1 (SMALL)
-    for (int b = threadIdx.x; b < N; b += blockDim.x) {
-        const int pb = canonical_parent(a, drow, s, b);
-        par[b] = pb;
-        if (SMALL) spar[b] = (uint16_t)(pb + 1);
+    // SMALL: the distance row is staged in shared memory (it shares the space
+    // of the jumping arrays, used only later); spar = parent + 1, 0 for the
+    // root, 0xFFFF for unreached vertices
+    uint16_t* spar = sdep + 4 * N;
+    if (SMALL) {
+        uint32_t* srow = reinterpret_cast<uint32_t*>(sdep);
+        for (int v = threadIdx.x; v < N; v += blockDim.x) srow[v] = __ldcg(drow + v);
+        __syncthreads();
+        for (int b = threadIdx.x; b < N; b += blockDim.x) {
+            const int pb = canonical_parent(a, srow, s, b);
+            par[b] = pb;
+            spar[b] = srow[b] == UNREACH ? (uint16_t)0xFFFF : (uint16_t)(pb + 1);
+        }
+    } else {
+        for (int b = threadIdx.x; b < N; b += blockDim.x) par[b] = canonical_parent(a, drow, s, b);
     }
     __syncthreads();
     for (int v = threadIdx.x; v < N; v += blockDim.x) {
         const int t = tg.tile_of(v);
         unsigned long long m = 1ull << tg.bit_of(v);
-        int x = SMALL ? (int)spar[v] - 1 : __ldcg(par + v);
+        const int sv = SMALL ? (int)spar[v] : 0;
+        int x = SMALL ? (sv == 0xFFFF ? -1 : sv - 1) : __ldcg(par + v);
         for (int guard = 0; x >= 0 && guard < 64 && tg.tile_of(x) == t; ++guard) {
             m |= 1ull << tg.bit_of(x);
             x = SMALL ? (int)spar[x] - 1 : __ldcg(par + x);
         }
-        const bool reached = drow[v] != UNREACH;
+        const bool reached = SMALL ? sv != 0xFFFF : drow[v] != UNREACH;
         seg[v] = make_ulonglong2(m, (unsigned long long)(x + 1));
         if (SMALL) {
             sdep[v] = reached ? (uint16_t)__popcll(m) : 0;                 // acc, buffer 0
@@ -144,7 +155,8 @@ __global__ void __launch_bounds__(1024) k_tree(TreeArgs a) {
     }
     unsigned long long ops = 0;
     for (int b = threadIdx.x; b < N; b += blockDim.x) {
-        const int pb = SMALL ? (int)spar[b] - 1 : __ldcg(par + b);
+        const int sb = SMALL ? (int)spar[b] : 0;
+        const int pb = SMALL ? (sb == 0xFFFF ? -1 : sb - 1) : __ldcg(par + b);
         if (pb >= 0)
             ops += SMALL ? (unsigned long long)sdep[cur * N + pb]
                          : (unsigned long long)__ldcg(a.acc + (size_t)(cur * B + j) * N + pb);

@@ -187,3 +187,19 @@ def scaled_blobs(H: int, W: int, conn: int, seed: int, B: int = 32) -> Workload:
     sig = max(1.5, 8.0 * (H + W) / 256.0)
     return Workload(f"blobs-{H}x{W}-{conn}conn", blobs(H, W, nb, sig, 55.0, seed),
                     conn, B=B, meta={"seed": seed})
+
+
+def batch_64(seed: int = 0, n: int = 64) -> list[Workload]:
+    """Many images of uneven sizes: heights and widths log-uniform in
+    [24, 96] px, drawn independently; 4- or 8-connected with equal
+    probability; the blob generator at the 128x128 density; B = 32."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        H = int(round(math.exp(rng.uniform(math.log(24), math.log(96)))))
+        W = int(round(math.exp(rng.uniform(math.log(24), math.log(96)))))
+        conn = 4 if rng.random() < 0.5 else 8
+        w = scaled_blobs(H, W, conn, seed=seed * 1000 + k, B=32)
+        w.name = f"batch{k}-{H}x{W}-{conn}conn"
+        out.append(w)
+    return out

@@ -137,14 +137,14 @@ def _check_fill(gp, img, order, B, conn, kind="grey", mask=None, seed=0):
     return st
 
 
-@pytest.mark.parametrize("order", ["naive", "spiral", "minfill"])
+@pytest.mark.parametrize("order", ["naive", "spiral", "extrema", "minfill"])
 def test_all_pairs_plain_32(gp, order):
     """32x32 blobs, 4-connected, B = 1: the paper's sequential loop."""
     w = synth.plain_32(0)
     _check_fill(gp, w.img, order, 1, 4)
 
 
-@pytest.mark.parametrize("order", ["naive", "spiral", "minfill"])
+@pytest.mark.parametrize("order", ["naive", "spiral", "extrema", "minfill"])
 @pytest.mark.parametrize("B", [2, 5, 32])
 @pytest.mark.parametrize("shape,conn", [((17, 23), 8), ((24, 9), 4), ((1, 40), 8)])
 def test_all_pairs_batched(gp, order, B, shape, conn):
@@ -152,7 +152,7 @@ def test_all_pairs_batched(gp, order, B, shape, conn):
     _check_fill(gp, img, order, B, conn, seed=B)
 
 
-@pytest.mark.parametrize("order", ["naive", "spiral", "minfill"])
+@pytest.mark.parametrize("order", ["naive", "spiral", "extrema", "minfill"])
 @pytest.mark.parametrize("conn", [4, 8])
 def test_all_pairs_mask(gp, order, conn):
     m = synth.disk_mask(26, 31, 0.4, 2, 4, seed=conn)
@@ -164,7 +164,7 @@ def test_all_pairs_mask(gp, order, conn):
 def test_all_pairs_degenerate(gp):
     for img in (np.array([[7]], np.uint8), np.array([[1, 2]], np.uint8),
                 np.full((3, 1), 4, np.uint8)):
-        for order in ("naive", "spiral", "minfill"):
+        for order in ("naive", "spiral", "extrema", "minfill"):
             _check_fill(gp, img, order, 1, 8)
 
 
@@ -182,7 +182,7 @@ def test_all_pairs_repeat_and_orders_share_handle(gp):
     img = synth.blobs(19, 22, 3, 2.5, 55.0, seed=6)
     ref = oracle.apsp(img, conn=8)
     with gp.Image(img, conn=8, B=3) as im:
-        for order in ("minfill", "naive", "spiral", "minfill"):
+        for order in ("minfill", "naive", "extrema", "spiral", "minfill"):
             D, _ = im.all_pairs(order)
             assert np.array_equal(_u32(D), ref)
 
@@ -199,7 +199,7 @@ def test_budget_rejected_before_allocation(gp):
 # Full-size workload: 128x128, 8-connected, B = 32
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("order", ["minfill", "naive", "spiral"])
+@pytest.mark.parametrize("order", ["minfill", "naive", "spiral", "extrema"])
 def test_full_size_blobs128(gp, order):
     """The benchmark's workload in the benchmark's launch configuration:
     counts, per-round new pairs and the selected sources against the
@@ -209,7 +209,10 @@ def test_full_size_blobs128(gp, order):
     path = os.path.join(GOLDEN, "counts_blobs128.json")
     if not os.path.exists(path):
         pytest.skip("counts fixture not generated")
-    gold = json.load(open(path))["orders"][order]
+    gold_all = json.load(open(path))["orders"]
+    if order not in gold_all:
+        pytest.skip(f"{order} counts not generated")
+    gold = gold_all[order]
     w = synth.batched_128(0)
     with gp.Image(w.img, conn=w.conn, B=w.B, seed=0) as im:
         D, st = im.all_pairs(order, want_log=True)
@@ -228,3 +231,69 @@ def test_full_size_blobs128(gp, order):
     assert bool((D == D.T).all())
     assert bool((torch.diagonal(D) == 0).all())
     assert int((D.view(torch.int32) < 0).sum()) == 0  # no unreachable pair on a grey image
+
+
+# --------------------------------------------------------------------------
+# Full-size 256x256 workloads (17.2 GB array on the device)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,factory", [("steps256", synth.steps_256), ("mask256", synth.mask_256)])
+def test_full_size_256(gp, name, factory):
+    """256x256, 8-connected, B = 32, minimum filling rate: the counts against
+    the oracle's stored simulation, sampled rows and columns of D against
+    Dijkstra, and symmetry of the sampled entries."""
+    import torch
+    path = os.path.join(GOLDEN, f"counts_{name}.json")
+    if not os.path.exists(path):
+        pytest.skip("counts fixture not generated")
+    gold_all = json.load(open(path))["orders"]
+    if "minfill" not in gold_all:
+        pytest.skip("minfill counts not generated")
+    gold = gold_all["minfill"]
+    w = factory(0)
+    N = w.N
+    img = w.img if w.kind == "grey" else None
+    D = torch.empty((N, N), dtype=torch.int32, device="cuda")
+    with gp.Image(img, conn=w.conn, kind=w.kind, mask=w.mask, B=w.B, seed=0) as im:
+        _, st = im.all_pairs("minfill", out=D, want_log=True)
+    for k in ("propagations", "prepass_propagations", "distance_ops", "new_pairs", "rounds"):
+        assert st[k] == gold[k], k
+    assert [int(x) for x in st["round_new"]] == gold["round_new"]
+    assert hashlib.sha256(st["sources"].astype("<i4").tobytes()).hexdigest() == gold["sources_sha256"]
+    rng = np.random.default_rng(2)
+    rows = np.unique(np.concatenate([[0, N - 1], rng.integers(0, N, size=24)])).astype(np.int32)
+    ref = oracle.rows(w.img, rows, conn=w.conn, kind=w.kind, mask=w.mask)
+    idx = torch.from_numpy(rows).long().cuda()
+    assert np.array_equal(_u32(D[idx]), ref)
+    assert np.array_equal(_u32(D[:, idx]).T, ref)
+    del D
+    torch.cuda.empty_cache()
+
+
+# --------------------------------------------------------------------------
+# Batched form: many images of uneven sizes side by side
+# --------------------------------------------------------------------------
+
+def test_all_pairs_batch_equals_alone(gp):
+    """Each image of a batch gets the array and counts it gets alone
+    (images of uneven sizes, 4- and 8-connected, one mask)."""
+    rng = np.random.default_rng(4)
+    specs = []
+    for k in range(6):
+        H, W = int(rng.integers(5, 30)), int(rng.integers(5, 30))
+        specs.append((synth.blobs(H, W, 3, 2.5, 55.0, seed=k), None, 4 if k % 2 else 8))
+    specs.append((None, synth.disk_mask(21, 26, 0.4, 2, 3, seed=9), 8))
+    ims = [gp.Image(img, conn=c, kind="grey" if m is None else "mask", mask=m, B=4)
+           for img, m, c in specs]
+    try:
+        outs, stats = gp.all_pairs_batch(ims, "minfill")
+        for (img, m, c), D, st in zip(specs, outs, stats):
+            base = img if m is None else np.zeros_like(m)
+            kind = "grey" if m is None else "mask"
+            assert np.array_equal(_u32(D), oracle.apsp(base, conn=c, kind=kind, mask=m))
+            ref = oracle.fill(base, "minfill", B=4, conn=c, kind=kind, mask=m)
+            for key in ("propagations", "distance_ops", "new_pairs", "rounds"):
+                assert st[key] == getattr(ref, key), key
+    finally:
+        for im in ims:
+            im.close()
