@@ -106,6 +106,12 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+# DRAM bytes (read + write) of one k_propagate_smem launch of this workload,
+# from the ncu capture summarised in profiles/k_propagate_smem_blobs128.md.
+# None whenever the kernel has changed since that capture.
+PROP_DRAM_BYTES = 53760
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -266,7 +272,7 @@ def run_ours(a):
         relax = 2.0 * w.conn * N * (props + st["prepass_propagations"])
         achieved = relax / (prop_ms_k / 1e3) / 1e12 if prop_ms_k else 0.0
         roof = {"kernel": "k_propagate", "bound": "alu", "achieved": achieved, "peak": peak_relax,
-                "unit": "T relax/s", "frac": achieved / peak_relax, "traffic": None,
+                "unit": "T relax/s", "frac": achieved / peak_relax, "traffic": PROP_DRAM_BYTES,
                 "peak_source": "derived: 152 SMs x 128 int32 lanes x max SM clock, 2 ops each",
                 "algorithmic_relaxations_per_launch": relax / max(prop_n, 1),
                 "avg_launch_ms": prop_ms_k / max(prop_n, 1)}
