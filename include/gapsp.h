@@ -91,6 +91,14 @@ typedef struct {
     void *stream;      /* cudaStream_t the calls run on (NULL = default stream) */
     int prop_blocks;   /* blocks (row strips, one thread-block cluster) per propagation:
                           0 = auto, 1, 2 or 4 */
+    int lookahead;     /* gapsp_all_pairs: candidates per round whose rows are
+                          computed ahead, on a second stream, while the round's
+                          trees fill D: 0 = auto (one per multiprocessor the round's
+                          B sources leave free), -1 = none, else 1..1024-B. The
+                          candidates are the next points in the order's ranking
+                          at the round's start; a later round whose source was
+                          computed ahead skips that propagation. D and every count
+                          are the same with or without it. */
 } gapsp_opts;
 
 typedef struct {
@@ -110,6 +118,9 @@ typedef struct {
     uint64_t sweeps;               /* directional sweeps run by all propagations */
     uint64_t lines;                /* image lines those sweeps processed (the rest were
                                       skipped as unchanged) */
+    uint64_t lookahead_propagations; /* rows computed ahead of their round (opts.lookahead);
+                                        not part of `propagations` */
+    uint64_t lookahead_hits;       /* propagations whose row had been computed ahead */
 } gapsp_stats;
 
 /* Fills *opts with the defaults (conn 8, grey, B 32, seed 0, no budget). */
@@ -187,8 +198,9 @@ uint64_t gapsp_kernel_launches(const gapsp_handle *h);
  * number of launches since the last read (then resets). Enabling adds two
  * event records per launch; leave it off for throughput timing.
  * Kernel ids: 0 selection (c), 1 propagation (a), 2 tree: parents,
- * segments and depths (a'), 3 unused, 4 tree fill (b), 5 init, 6 extrema
- * pre-pass helpers, 7 unused, 8 fill-count update.
+ * segments and depths (a'), 3 lookahead propagations (on the second stream,
+ * overlapping the others), 4 tree fill (b), 5 init, 6 extrema pre-pass
+ * helpers, 7 unused, 8 fill-count update.
  * ms and launches: caller-owned arrays of GAPSP_NUM_KERNELS entries.
  */
 #define GAPSP_NUM_KERNELS 9

@@ -20,7 +20,7 @@ from . import _build
 UNREACH = 0xFFFFFFFF
 ORDERS = {"naive": 0, "spiral": 1, "minfill": 2, "extrema": 3}
 KINDS = {"grey": 0, "mask": 1}
-KERNELS = ("select", "propagate", "tree", "unused3", "fill", "init", "prepass", "unused7", "recount")
+KERNELS = ("select", "propagate", "tree", "lookahead", "fill", "init", "prepass", "unused7", "recount")
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "memory budget exceeded",
           4: "CUDA runtime error", 5: "propagation did not converge", 6: "round limit exceeded",
           7: "cancelled"}
@@ -38,7 +38,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("conn", ctypes.c_int), ("kind", ctypes.c_int), ("B", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("mem_budget", ctypes.c_size_t),
                 ("sweep_phases", ctypes.c_int), ("fill_rows", ctypes.c_int), ("checked", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("prop_blocks", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("prop_blocks", ctypes.c_int),
+                ("lookahead", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -48,7 +49,8 @@ class Stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double),
                 ("round_new", ctypes.POINTER(ctypes.c_uint64)), ("round_new_cap", ctypes.c_uint64),
                 ("sources", ctypes.POINTER(ctypes.c_int32)), ("sources_cap", ctypes.c_uint64),
-                ("sweeps", ctypes.c_uint64), ("lines", ctypes.c_uint64)]
+                ("sweeps", ctypes.c_uint64), ("lines", ctypes.c_uint64),
+                ("lookahead_propagations", ctypes.c_uint64), ("lookahead_hits", ctypes.c_uint64)]
 
 
 def library_path() -> str:
@@ -173,7 +175,7 @@ class Image:
 
     def __init__(self, img, conn: int = 8, kind: str = "grey", mask=None, B: int = 32,
                  seed: int = 0, mem_budget: int = 0, stream=None, sweep_phases: int = 0,
-                 fill_rows: int = 0, prop_blocks: int = 0):
+                 fill_rows: int = 0, prop_blocks: int = 0, lookahead: int = 0):
         lib = load()
         self._lib = lib
         self._h = ctypes.c_void_p()
@@ -196,6 +198,7 @@ class Image:
         o.sweep_phases = sweep_phases
         o.fill_rows = fill_rows
         o.prop_blocks = prop_blocks
+        o.lookahead = lookahead
         o.stream = _torch_stream(stream)
         self.H, self.W, self.N, self.conn, self.kind, self.B = H, W, H * W, conn, kind, B
         rc = lib.gapsp_create(_ptr(img_a), H, W, _ptr(mask_a), ctypes.byref(o), ctypes.byref(self._h))
@@ -274,7 +277,9 @@ class Image:
         stats = {"propagations": st.propagations, "prepass_propagations": st.prepass_propagations,
                  "distance_ops": st.distance_ops, "new_pairs": st.new_pairs, "rounds": st.rounds,
                  "prefilled_pairs": st.prefilled_pairs, "ms_total": st.ms_total,
-                 "sweeps": st.sweeps, "lines": st.lines}
+                 "sweeps": st.sweeps, "lines": st.lines,
+                 "lookahead_propagations": st.lookahead_propagations,
+                 "lookahead_hits": st.lookahead_hits}
         if want_log:
             stats["round_new"] = rn[:st.rounds].copy()
             stats["sources"] = sl[:st.propagations].copy()

@@ -21,31 +21,18 @@ constexpr int ST_TIMEOUT = 4;
 enum StatSlot {
     S_PROPAGATIONS = 0,
     S_OPS = 1,
-    S_NEW = 2,
+    S_NEW = 2,     // twice the new pairs: each filled pair adds one mark to each of its rows
     S_ROUNDS = 3,
     S_SWEEPS = 4,  // total sweeps run by the propagation warps
     S_LINES = 5,   // lines processed (not skipped) by the propagation warps
+    S_AHEAD = 6,   // lookahead propagations run (rows computed ahead of their round)
+    S_HITS = 7,    // selected sources whose row had been computed ahead
     S_SLOTS = 8
 };
 
 // Marks: one 64-bit word per (row, 8x8 pixel tile). Bit (r%8)*8 + (c%8) of
 // word (r/8)*tiles_w + c/8 of row b says whether the pair {b, (r,c)} is
 // filled.
-struct TileGeom {
-    int W, tiles_w, words;  // words per row = tiles_h * tiles_w
-    __host__ __device__ int tile_of(int p) const {
-        int r = p / W, c = p - r * W;
-        return (r >> 3) * tiles_w + (c >> 3);
-    }
-    __host__ __device__ int bit_of(int p) const {
-        int r = p / W, c = p - r * W;
-        return ((r & 7) << 3) | (c & 7);
-    }
-    __host__ __device__ int pixel_of(int tile, int bit) const {
-        int tr = tile / tiles_w, tc = tile - tr * tiles_w;
-        return ((tr << 3) + (bit >> 3)) * W + (tc << 3) + (bit & 7);
-    }
-};
 
 __device__ __forceinline__ int ld_cg(const int* p) {
     int v;

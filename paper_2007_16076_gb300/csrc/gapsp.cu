@@ -8,6 +8,7 @@
 // the device-side selection count and does nothing once the loop is over,
 // so rounds are enqueued in chunks and the host only checks the device
 // "done" flag between chunks.
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -29,11 +30,13 @@ struct gapsp_handle {
     int sweep_phases = 0;
     int fill_rows = 0;
     int prop_blocks = 0;
+    int lookahead = 0;  // option: 0 auto, -1 off, else candidates per round
+    int sms = 0;        // multiprocessors of the device
     uint64_t launches = 0;
     // image
     uint8_t* f = nullptr;
-    int* Prow = nullptr;
-    int* Pcol = nullptr;
+    uint32_t* pgeo = nullptr;
+    int32_t* tbase = nullptr;
     uint8_t* bound = nullptr;
     int32_t* comp = nullptr;
     int32_t* comp_size = nullptr;
@@ -56,6 +59,9 @@ struct gapsp_handle {
     int32_t* seq = nullptr;
     int32_t* rank = nullptr;
     int32_t* grank = nullptr;
+    uint8_t* row_done = nullptr;  // [N]: row already written by a propagation
+    int32_t* cand = nullptr;      // [2][1024]: lookahead candidates, by round parity
+    int* ncand = nullptr;         // [2]
     unsigned long long* stats = nullptr;
     unsigned long long* round_new = nullptr;
     unsigned long long* last_new = nullptr;
@@ -155,8 +161,6 @@ PropArgs base_prop(const gapsp_handle* h) {
     a.conn = h->conn;
     a.kind_mask = h->kind == GAPSP_MASK;
     a.f = h->f;
-    a.Prow = h->Prow;
-    a.Pcol = h->Pcol;
     a.status = h->status;
     a.max_sweeps = 4 * (h->N + 2);
     a.phases = h->sweep_phases ? h->sweep_phases : 2;
@@ -170,9 +174,10 @@ PropArgs base_prop(const gapsp_handle* h) {
 size_t fill_state_bytes(const gapsp_handle* h) {
     const size_t N = h->N, B = h->B;
     // marks; parent, seg, jmp, acc per source; cnt, cnt_base, dirty, seq,
-    // rank, grank, round_new, sel_log, emap, gmap, best, cen per point
+    // rank, grank, round_new, sel_log, emap, gmap, best, cen, row_done per
+    // point; the lookahead candidate buffers
     return N * h->words * 8 + B * N * (4 + 16 + 8 + 8) +
-           N * (4 + 4 + 1 + 4 + 4 + 4 + 8 + 4 + 4 + 4 + 8 + 1) + 4096;
+           N * (4 + 4 + 1 + 4 + 4 + 4 + 8 + 4 + 4 + 4 + 8 + 1 + 1) + 2 * 1024 * 4 + 4096;
 }
 
 gapsp_status ensure_fill_state(gapsp_handle* h) {
@@ -193,6 +198,9 @@ gapsp_status ensure_fill_state(gapsp_handle* h) {
     CK(dalloc(&h->seq, N));
     CK(dalloc(&h->rank, N));
     CK(dalloc(&h->grank, N));
+    CK(dalloc(&h->row_done, N));
+    CK(dalloc(&h->cand, 2 * 1024));
+    CK(dalloc(&h->ncand, 2));
     CK(dalloc(&h->stats, S_SLOTS));
     CK(dalloc(&h->round_new, N + 1));
     CK(dalloc(&h->last_new, 1));
@@ -207,10 +215,11 @@ gapsp_status ensure_fill_state(gapsp_handle* h) {
 }
 
 void free_all(gapsp_handle* h) {
-    dfree(h->f); dfree(h->Prow); dfree(h->Pcol); dfree(h->bound); dfree(h->comp);
+    dfree(h->f); dfree(h->pgeo); dfree(h->tbase); dfree(h->bound); dfree(h->comp);
     dfree(h->comp_size); dfree(h->status); dfree(h->changed);
     dfree(h->cnt); dfree(h->cnt_base); dfree(h->dirty); dfree(h->marks); dfree(h->parent); dfree(h->seg); dfree(h->jmp); dfree(h->acc);
     dfree(h->sel); dfree(h->nsel); dfree(h->cursor); dfree(h->done); dfree(h->seq); dfree(h->rank); dfree(h->grank);
+    dfree(h->row_done); dfree(h->cand); dfree(h->ncand);
     dfree(h->stats); dfree(h->round_new); dfree(h->last_new); dfree(h->sel_log);
     dfree(h->emap); dfree(h->gmap); dfree(h->best); dfree(h->cen);
     dfree(h->Dtmp); dfree(h->src_dev); dfree(h->out_tmp);
@@ -225,7 +234,7 @@ void free_all(gapsp_handle* h) {
     h->ev0 = h->ev1 = nullptr;
 }
 
-enum { K_SELECT = 0, K_PROP = 1, K_TREE = 2, K_FILL = 4, K_INIT = 5, K_PRE = 6, K_RECOUNT = 8 };
+enum { K_SELECT = 0, K_PROP = 1, K_TREE = 2, K_AHEAD = 3, K_FILL = 4, K_INIT = 5, K_PRE = 6, K_RECOUNT = 8 };
 
 cudaEvent_t pool_get(gapsp_handle* h) {
     if (!h->pool.empty()) {
@@ -307,6 +316,7 @@ gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask,
     if (o.fill_rows < 0 || o.fill_rows > 32) return GAPSP_E_INVALID;
     if (o.prop_blocks != 0 && o.prop_blocks != 1 && o.prop_blocks != 2 && o.prop_blocks != 4)
         return GAPSP_E_INVALID;
+    if (o.lookahead < -1 || o.lookahead > 1024) return GAPSP_E_INVALID;
     if (o.kind == GAPSP_GREY && !img) return GAPSP_E_INVALID;
     if (o.kind == GAPSP_MASK && !mask) return GAPSP_E_INVALID;
 
@@ -317,6 +327,15 @@ gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask,
     h->sweep_phases = o.sweep_phases;
     h->fill_rows = o.fill_rows;
     h->prop_blocks = o.prop_blocks;
+    h->lookahead = o.lookahead;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            h->sms = 0;
+        }
+    }
     h->tiles_w = (W + 7) / 8; h->tiles_h = (H + 7) / 8; h->words = h->tiles_w * h->tiles_h;
     const size_t N = h->N;
     if (h->budget && N * 32 + 4096 > h->budget) { delete h; return GAPSP_E_BUDGET; }
@@ -329,8 +348,8 @@ gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask,
     };
     cudaError_t e;
     if ((e = dalloc(&h->f, N)) != cudaSuccess) return fail(e);
-    if ((e = dalloc(&h->Prow, N)) != cudaSuccess) return fail(e);
-    if ((e = dalloc(&h->Pcol, N)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&h->pgeo, N)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&h->tbase, (size_t)h->words)) != cudaSuccess) return fail(e);
     if ((e = dalloc(&h->bound, N)) != cudaSuccess) return fail(e);
     if ((e = dalloc(&h->status, 1)) != cudaSuccess) return fail(e);
     if ((e = dalloc(&h->changed, 1)) != cudaSuccess) return fail(e);
@@ -348,9 +367,9 @@ gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask,
         if ((e = cudaMemcpyAsync(h->f, m.data(), N, cudaMemcpyHostToDevice, h->st)) != cudaSuccess) return fail(e);
         if ((e = cudaStreamSynchronize(h->st)) != cudaSuccess) return fail(e);
     }
-    ImagePrep ip{h->f, H, W, o.conn, (int)o.kind, h->Prow, h->Pcol, h->bound};
+    ImagePrep ip{h->f, H, W, o.conn, (int)o.kind, h->bound, h->pgeo, h->tbase, h->tiles_w, h->words};
     if ((e = launch_image_prep(ip, h->st)) != cudaSuccess) return fail(e);
-    h->launches += o.kind == GAPSP_GREY ? 2 : 1;
+    h->launches += 2;
     if (o.kind == GAPSP_MASK) {
         if ((e = dalloc(&h->comp, N)) != cudaSuccess) return fail(e);
         if ((e = dalloc(&h->comp_size, N)) != cudaSuccess) return fail(e);
@@ -446,7 +465,31 @@ struct FillRun {
     TreeArgs ta{};
     int rounds = 0;
     bool finished = false;
+    // lookahead: the next K candidates of each round are propagated on a
+    // second stream while the round's tree and fill run
+    int K = 0;
+    PropArgs pa_ahead{};
+    cudaStream_t side = nullptr;
+    cudaEvent_t e_sel = nullptr, e_ahead = nullptr;
+    ~FillRun() {
+        if (e_sel) cudaEventDestroy(e_sel);
+        if (e_ahead) cudaEventDestroy(e_ahead);
+        if (side) cudaStreamDestroy(side);
+    }
 };
+
+// Candidates propagated ahead per round: one block (cluster) for each
+// multiprocessor the round's own sources leave free, unless set by option.
+int lookahead_count(const gapsp_handle* h, const PropArgs& pa) {
+    if (h->lookahead < 0) return 0;
+    int K = h->lookahead;
+    if (K == 0) {
+        const int per = prop_blocks_per_job(pa);
+        K = h->sms / per - h->B;
+    }
+    K = std::min(K, 1024 - h->B);
+    return K > 0 ? K : 0;
+}
 
 gapsp_status fill_begin(FillRun& r) {
     gapsp_handle* h = r.h;
@@ -540,6 +583,7 @@ gapsp_status fill_begin(FillRun& r) {
         r.prepass = 2;
     }
 
+    CK(cudaMemsetAsync(h->row_done, 0, N, s));
     r.sa = SelectArgs{h->N, h->B, (int)r.order, h->cnt, h->rank, h->grank, h->seq, r.nseq, h->cursor, h->sel, h->nsel,
                       h->stats, h->round_new, h->last_new, h->sel_log, h->done};
     PropArgs& pa = r.pa;
@@ -550,16 +594,30 @@ gapsp_status fill_begin(FillRun& r) {
     pa.njobs_dev = h->nsel;
     pa.convert = h->kind == GAPSP_MASK;
     pa.sweeps = h->stats + S_SWEEPS;
+    pa.row_done = h->row_done;
+    r.K = lookahead_count(h, pa);
+    if (r.K > 0) {
+        r.sa.K = r.K;
+        r.sa.cand = h->cand;
+        r.sa.ncand = h->ncand;
+        r.pa_ahead = pa;
+        r.pa_ahead.ran = h->stats + S_AHEAD;
+        pa.hits = h->stats + S_HITS;
+        CK(cudaStreamCreateWithFlags(&r.side, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&r.e_sel, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&r.e_ahead, cudaEventDisableTiming));
+    }
     TreeArgs& ta = r.ta;
     ta = TreeArgs{};
     ta.H = h->H; ta.W = h->W; ta.N = h->N; ta.conn = h->conn; ta.kind = h->kind;
     ta.tiles_w = h->tiles_w; ta.words = h->words;
     ta.f = h->f; ta.D = Dd; ta.sel = h->sel; ta.nsel = h->nsel;
+    ta.pgeo = h->pgeo; ta.tbase = h->tbase;
     ta.parent = h->parent; ta.seg = h->seg; ta.jmp = h->jmp; ta.acc = h->acc;
     ta.marks = h->marks; ta.cnt = h->cnt; ta.Dw = Dd; ta.stats = h->stats;
     ta.cnt_base = h->cnt_base; ta.dirty = h->dirty;
     {
-        const size_t row_bytes = (size_t)h->words * 8;
+        const size_t row_bytes = (size_t)h->words * 9;  // marks + changed flags
         int rpb = (int)((96 * 1024) / row_bytes);
         // 8 rows per block: enough blocks per SM to hide the latency of the
         // tree walks (measured best on the 128x128 workload)
@@ -577,9 +635,32 @@ gapsp_status fill_enqueue(FillRun& r, int chunk) {
     gapsp_handle* h = r.h;
     cudaStream_t s = r.s;
     for (int i = 0; i < chunk; ++i) {
+        // the candidate buffers alternate by round: a round's lookahead
+        // launch reads one while the next selection writes the other
+        const int par = (r.rounds + i) & 1;
+        if (r.K > 0) {
+            r.sa.cand = h->cand + par * 1024;
+            r.sa.ncand = h->ncand + par;
+        }
         {
             ProfScope ps(h, K_SELECT, s);
             CK(launch_select(r.sa, s));
+        }
+        if (r.K > 0) {
+            // this round's sources may have been computed by the previous
+            // round's lookahead: wait for it, then start this round's
+            CK(cudaStreamWaitEvent(s, r.e_ahead, 0));
+            CK(cudaEventRecord(r.e_sel, s));
+            CK(cudaStreamWaitEvent(r.side, r.e_sel, 0));
+            r.pa_ahead.sources = h->cand + par * 1024;
+            r.pa_ahead.map_row = h->cand + par * 1024;
+            r.pa_ahead.njobs_dev = h->ncand + par;
+            {
+                ProfScope ps(h, K_AHEAD, r.side);
+                CK(launch_propagate(r.pa_ahead, h->conn, h->kind, r.K, 1, r.side));
+            }
+            CK(cudaEventRecord(r.e_ahead, r.side));
+            h->launches += 1;
         }
         {
             ProfScope ps(h, K_PROP, s);
@@ -616,6 +697,7 @@ gapsp_status fill_finish(FillRun& r, gapsp_stats* st) {
     gapsp_handle* h = r.h;
     cudaStream_t s = r.s;
     const size_t N = h->N;
+    if (r.K > 0) CK(cudaStreamWaitEvent(s, r.e_ahead, 0));
     CK(cudaEventRecord(h->ev1, s));
     unsigned long long hs[S_SLOTS];
     int sw = 0;
@@ -626,11 +708,13 @@ gapsp_status fill_finish(FillRun& r, gapsp_stats* st) {
         st->propagations = hs[S_PROPAGATIONS];
         st->prepass_propagations = r.prepass;
         st->distance_ops = hs[S_OPS];
-        st->new_pairs = hs[S_NEW];
+        st->new_pairs = hs[S_NEW] >> 1;
         st->rounds = hs[S_ROUNDS];
         st->prefilled_pairs = 0;
         st->sweeps = hs[S_SWEEPS];
         st->lines = hs[S_LINES];
+        st->lookahead_propagations = hs[S_AHEAD];
+        st->lookahead_hits = hs[S_HITS];
         float ms = 0.f;
         cudaEventElapsedTime(&ms, h->ev0, h->ev1);
         st->ms_total = ms;

@@ -16,14 +16,16 @@ struct PropArgs {
     int njobs;
     int H, W, N, conn, kind_mask;
     const uint8_t* f;           // grey levels (grey) or free flags (mask)
-    const int* Prow;            // [H][W]: sum of horizontal edge weights left of (r,c)
-    const int* Pcol;            // [W][H]: sum of vertical edge weights above (r,c)
     int* status;                // device status word (ST_* bits)
     unsigned long long* sweeps; // optional: total sweeps run
     int max_sweeps;
     int convert;                // write UNREACH for pixels never reached
     int phases;                 // warps per sweep direction (1, 2 or 4)
     int cluster;                // blocks (row strips) per source: 1, 2 or 4
+    uint8_t* row_done;          // [N] or NULL: skip sources whose row is already in the
+                                // output; set the flag once a row is written
+    unsigned long long* ran;    // or NULL: counts the jobs that were not skipped
+    unsigned long long* hits;   // or NULL: counts the jobs skipped by row_done
 };
 
 // Picks the per-lane width and launches kernel (a).
@@ -31,13 +33,16 @@ cudaError_t launch_propagate(const PropArgs& a, int conn, int kind, int grid, in
                              cudaStream_t st);
 // Values held per lane for lines of length up to `side`.
 int prop_vpl(int side);
+// Blocks (one cluster) a single-source propagation of this image uses.
+int prop_blocks_per_job(const PropArgs& a);
 
 struct ImagePrep {
     const uint8_t* f;
     int H, W, conn, kind;
-    int* Prow;
-    int* Pcol;
     uint8_t* bound;  // boundary flags: free pixels with fewer free neighbours than conn
+    uint32_t* pgeo;  // [N]: tile << 8 | bit of each pixel (see TileGeom)
+    int32_t* tbase;  // [tiles]: pixel index of each tile's top-left pixel
+    int tiles_w, tiles;
 };
 cudaError_t launch_image_prep(const ImagePrep& p, cudaStream_t st);
 
@@ -47,8 +52,11 @@ struct TreeArgs {
     const uint32_t* D;          // the array; row sel[j] holds d(sel[j], .)
     const int32_t* sel;         // selected sources
     const int* nsel;            // device count
-    int32_t* parent;            // [B][N]
-    ulonglong2* seg;            // [B][N]: x = mask of the tile segment, y = exit vertex (+1)
+    const uint32_t* pgeo;       // [N]: tile << 8 | bit of each pixel
+    const int32_t* tbase;       // [words]: top-left pixel of each tile
+    int32_t* parent;            // [B][N] (N > 16384 only)
+    ulonglong2* seg;            // [B][N]: x = mask of the tile segment; y = exit vertex + 1
+                                // (0 past the root) | tile of the exit << 32
     int32_t* jmp;               // [2][B][N] scratch for the depth pointer jumping
     int32_t* acc;               // [2][B][N] scratch for the depth pointer jumping
     unsigned long long* marks;  // [N][words]
@@ -78,6 +86,9 @@ struct SelectArgs {
     unsigned long long* last_new;       // S_NEW value at the previous round
     int32_t* sel_log;           // sources in selection order (capacity N)
     int* done;                  // set to 1 once every point is filled
+    int32_t* cand;              // lookahead candidates (capacity K), or NULL
+    int* ncand;                 // device count of candidates, or NULL
+    int K;                      // wanted candidates (B + K <= 1024)
 };
 cudaError_t launch_select(const SelectArgs& a, cudaStream_t st);
 

@@ -437,6 +437,13 @@ __global__ void __launch_bounds__(32 * MAXWARPS) k_propagate_smem(PropArgs a, in
     const int hs0 = (a.H + C - 1) / C;
     const int r0 = rank * hs0, hs = min(hs0, a.H - r0);
     const int src = a.sources ? a.sources[j] : -1;
+    // a row computed ahead of its round is not computed again (no launch that
+    // may run concurrently with this one writes this source's flag, so the
+    // blocks of a cluster all see the same value and leave together)
+    if (a.row_done && src >= 0 && a.row_done[src]) {
+        if (a.hits && threadIdx.x == 0 && rank == 0) atomicAdd(a.hits, 1ull);
+        return;
+    }
     int* out = a.map_base + (size_t)(a.map_row ? a.map_row[j] : j) * (size_t)a.N;
     for (int p = threadIdx.x; p < hs * a.W; p += blockDim.x) {
         const int r = p / a.W, c = p - r * a.W;
@@ -487,6 +494,10 @@ __global__ void __launch_bounds__(32 * MAXWARPS) k_propagate_smem(PropArgs a, in
     if (threadIdx.x == 0 && a.convert && src >= 0 && KIND == 1 && !a.f[src] && src / a.W >= r0 &&
         src / a.W < r0 + hs)
         out[src] = 0;
+    if (threadIdx.x == 0 && rank == 0 && a.row_done && src >= 0) {
+        a.row_done[src] = 1;  // read by later launches only
+        if (a.ran) atomicAdd(a.ran, 1ull);
+    }
 }
 
 // Map in global memory (the output row itself), for images whose map does
@@ -499,6 +510,10 @@ __global__ void __launch_bounds__(32 * MAXWARPS) k_propagate_glob(PropArgs a) {
     const int njobs = a.njobs_dev ? *a.njobs_dev : a.njobs;
     if (j >= njobs) return;
     const int src = a.sources ? a.sources[j] : -1;
+    if (a.row_done && src >= 0 && a.row_done[src]) {
+        if (a.hits && threadIdx.x == 0) atomicAdd(a.hits, 1ull);
+        return;
+    }
     int* map = a.map_base + (size_t)(a.map_row ? a.map_row[j] : j) * (size_t)a.N;
     for (int p = threadIdx.x; p < a.N; p += blockDim.x) map[p] = is_seed(a, src, p) ? 0 : PINF;
     const Shared sh = setup_shared<KIND, VPL>(a, reinterpret_cast<char*>(sbuf), 0, a.H);
@@ -519,9 +534,30 @@ __global__ void __launch_bounds__(32 * MAXWARPS) k_propagate_glob(PropArgs a) {
         __syncthreads();
         if (threadIdx.x == 0 && src >= 0 && KIND == 1 && !a.f[src]) map[src] = 0;
     }
+    if (threadIdx.x == 0 && a.row_done && src >= 0) {
+        a.row_done[src] = 1;  // read by later launches only
+        if (a.ran) atomicAdd(a.ran, 1ull);
+    }
 }
 
 constexpr int SMEM_LIMIT = 220 * 1024;
+
+size_t smem_for_strips(const PropArgs& a, int c) {
+    const int pitch = a.W | 1;
+    const int hs = (a.H + c - 1) / c;
+    return (size_t)hs * pitch * sizeof(int) + shared_state_bytes(hs, a.W);
+}
+
+// Row strips (blocks of one cluster) per source: the requested cluster size,
+// halved while a strip would be shorter than 8 rows, doubled while a strip
+// does not fit in shared memory; 0 when even 8 strips do not fit (the map
+// then lives in global memory, one block per source).
+int strips_per_job(const PropArgs& a) {
+    int C = a.cluster > 0 ? a.cluster : 1;
+    while (C > 1 && a.H / C < 8) C >>= 1;
+    while (smem_for_strips(a, C) > (size_t)SMEM_LIMIT && C < 8 && a.H / (2 * C) >= 1) C <<= 1;
+    return smem_for_strips(a, C) <= (size_t)SMEM_LIMIT ? C : 0;
+}
 
 template <int CONN, int KIND, int VPL>
 cudaError_t launch_one(const PropArgs& a, int jobs, cudaStream_t st) {
@@ -537,17 +573,9 @@ cudaError_t launch_one(const PropArgs& a, int jobs, cudaStream_t st) {
                              SMEM_LIMIT);
         attr = true;
     }
-    // strips per source: the requested cluster size, halved while a strip
-    // would be shorter than 8 rows, doubled while a strip does not fit
-    int C = a.cluster > 0 ? a.cluster : 1;
-    while (C > 1 && a.H / C < 8) C >>= 1;
-    auto smem_for = [&](int c) {
-        const int hs = (a.H + c - 1) / c;
-        return (size_t)hs * pitch * sizeof(int) + shared_state_bytes(hs, a.W);
-    };
-    while (smem_for(C) > (size_t)SMEM_LIMIT && C < 8 && a.H / (2 * C) >= 1) C <<= 1;
-    if (smem_for(C) <= (size_t)SMEM_LIMIT) {
-        const size_t smem = smem_for(C);
+    const int C = strips_per_job(a);
+    if (C > 0) {
+        const size_t smem = smem_for_strips(a, C);
         if (C == 1) {
             k_propagate_smem<CONN, KIND, VPL, false><<<jobs, threads, smem, st>>>(a, pitch, 1);
         } else {
@@ -587,6 +615,11 @@ cudaError_t launch_vpl(const PropArgs& a, int vpl, int jobs, cudaStream_t st) {
 
 }  // namespace
 
+int prop_blocks_per_job(const PropArgs& a) {
+    const int C = strips_per_job(a);
+    return C > 0 ? C : 1;
+}
+
 int prop_vpl(int side) {
     if (side <= 32) return 1;
     if (side <= 64) return 2;
@@ -604,26 +637,22 @@ cudaError_t launch_propagate(const PropArgs& a, int conn, int kind, int grid, in
 }
 
 // ---------------------------------------------------------------------------
-// Per-image set-up: line prefixes of the edge weights and boundary flags.
+// Per-image set-up: tile geometry of the pixels and boundary flags.
 // ---------------------------------------------------------------------------
 
 namespace {
 
-// One thread per line: Prow[r][c] = sum_{k<c} w((r,k),(r,k+1)) (grey only).
-__global__ void k_prefix(ImagePrep p) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < p.H) {
-        int r = t, acc = 0;
-        for (int c = 0; c < p.W; ++c) {
-            p.Prow[r * p.W + c] = acc;
-            if (c + 1 < p.W) acc += p.f[r * p.W + c] + p.f[r * p.W + c + 1] + 1;
-        }
-    } else if (t < p.H + p.W) {
-        int c = t - p.H, acc = 0;
-        for (int r = 0; r < p.H; ++r) {
-            p.Pcol[c * p.H + r] = acc;
-            if (r + 1 < p.H) acc += p.f[r * p.W + c] + p.f[(r + 1) * p.W + c] + 1;
-        }
+// The 8x8 tile and the bit inside it of every pixel, and the top-left pixel
+// of every tile, so that the tree and fill kernels need no division.
+__global__ void k_geometry(ImagePrep p) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < p.H * p.W) {
+        const int r = q / p.W, c = q - r * p.W;
+        p.pgeo[q] = ((uint32_t)((r >> 3) * p.tiles_w + (c >> 3)) << 8) | (uint32_t)(((r & 7) << 3) | (c & 7));
+    }
+    if (q < p.tiles) {
+        const int tr = q / p.tiles_w, tc = q - tr * p.tiles_w;
+        p.tbase[q] = (tr << 3) * p.W + (tc << 3);
     }
 }
 
@@ -658,9 +687,8 @@ __global__ void k_unreach(uint32_t* rows, size_t n) {
 }  // namespace
 
 cudaError_t launch_image_prep(const ImagePrep& p, cudaStream_t st) {
-    int lines = p.H + p.W;
-    if (p.kind == 0) k_prefix<<<(lines + 127) / 128, 128, 0, st>>>(p);
     int N = p.H * p.W;
+    k_geometry<<<(N + 255) / 256, 256, 0, st>>>(p);
     k_boundary<<<(N + 255) / 256, 256, 0, st>>>(p);
     return cudaGetLastError();
 }

@@ -22,7 +22,13 @@ namespace {
 // Sequence orders: one warp scans forward from the cursor with ballots.
 __global__ void k_select_seq(SelectArgs a) {
     const int lane = threadIdx.x;
-    if (*a.done) { if (lane == 0) *a.nsel = 0; return; }
+    if (*a.done) {
+        if (lane == 0) {
+            *a.nsel = 0;
+            if (a.ncand) *a.ncand = 0;
+        }
+        return;
+    }
     int cursor = *a.cursor, ns = 0;
     while (ns < a.B && cursor < a.nseq) {
         const int idx = cursor + lane;
@@ -42,14 +48,32 @@ __global__ void k_select_seq(SelectArgs a) {
         }
         ns += take;
     }
+    // lookahead candidates: the next K points of the sequence after the
+    // selection that are unfilled now (the cursor does not move for them)
+    int nc = 0;
+    if (a.K > 0) {
+        int c2 = cursor;
+        while (nc < a.K && c2 < a.nseq) {
+            const int idx = c2 + lane;
+            const int p = idx < a.nseq ? a.seq[idx] : -1;
+            const bool ok = p >= 0 && a.cnt[p] < (uint32_t)a.N;
+            const unsigned m = __ballot_sync(FULL, ok);
+            const int take = min(__popc(m), a.K - nc);
+            const int before = __popc(m & ((1u << lane) - 1u));
+            if (ok && before < take) a.cand[nc + before] = p;
+            nc += take;
+            c2 += 32;
+        }
+    }
     const unsigned long long props = a.stats[S_PROPAGATIONS];
     __syncwarp();
     for (int i = lane; i < ns; i += 32) a.sel_log[props + i] = a.sel[i];
     if (lane == 0) {
         *a.cursor = cursor;
         *a.nsel = ns;
+        if (a.ncand) *a.ncand = ns ? nc : 0;
         const unsigned long long rounds = a.stats[S_ROUNDS];
-        const unsigned long long cur_new = a.stats[S_NEW];
+        const unsigned long long cur_new = a.stats[S_NEW] >> 1;
         if (rounds > 0) a.round_new_log[rounds - 1] = cur_new - *a.last_new;
         *a.last_new = cur_new;
         if (ns == 0) {
@@ -89,7 +113,13 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
     __shared__ unsigned long long s_keys[1024];
     __shared__ int s_pix[1024];
     const int tid = threadIdx.x;
-    if (*a.done) { if (tid == 0) *a.nsel = 0; return; }
+    if (*a.done) {
+        if (tid == 0) {
+            *a.nsel = 0;
+            if (a.ncand) *a.ncand = 0;
+        }
+        return;
+    }
     if (tid == 0) { s_unfilled = 0; s_count = 0; s_prefix = 0; }
     __syncthreads();
     int mine = 0;
@@ -104,13 +134,15 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
     auto key = [&](int p) -> unsigned long long { return CACHED ? skeys[p] : mf_key(a, p); };
     const int unfilled = s_unfilled;
     const int want = min(unfilled, a.B);
+    // the selection, then up to K lookahead candidates in key order
+    const int wantc = min(unfilled, a.B + (a.K > 0 ? a.K : 0));
     unsigned long long thr = ~0ull - 1;  // select keys <= thr
-    if (want > 0 && want < unfilled) {
+    if (wantc > 0 && wantc < unfilled) {
         // the want-th smallest key, 8 bits at a time from the top bit a key
         // can have (17 bits per field below the top one)
         int top = a.order == 3 ? 34 : 17;
         for (int n = a.N - 1; n > 0; n >>= 1) ++top;
-        if (tid == 0) s_need = want;
+        if (tid == 0) s_need = wantc;
         unsigned long long prefix = 0;
         for (int shift = ((top - 1) / 8) * 8; shift >= 0; shift -= 8) {
             if (tid < 256) hist[tid] = 0;
@@ -163,21 +195,28 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
         }
     }
     __syncthreads();
-    const int ns = min(s_count, want);
-    // order the selection by key (rank sort; keys are distinct)
-    if (tid < ns) {
+    const int nall = min(s_count, wantc);
+    const int ns = min(nall, want);
+    // order by key (rank sort; keys are distinct): the first ns are the
+    // selection, the rest the candidates
+    if (tid < nall) {
         const unsigned long long k = s_keys[tid];
         int pos = 0;
-        for (int i = 0; i < ns; ++i) pos += s_keys[i] < k;
-        a.sel[pos] = s_pix[tid];
-        const unsigned long long props = a.stats[S_PROPAGATIONS];
-        a.sel_log[props + pos] = s_pix[tid];
+        for (int i = 0; i < nall; ++i) pos += s_keys[i] < k;
+        if (pos < ns) {
+            a.sel[pos] = s_pix[tid];
+            const unsigned long long props = a.stats[S_PROPAGATIONS];
+            a.sel_log[props + pos] = s_pix[tid];
+        } else if (a.cand) {
+            a.cand[pos - ns] = s_pix[tid];
+        }
     }
     __syncthreads();
     if (tid == 0) {
         *a.nsel = ns;
+        if (a.ncand) *a.ncand = ns ? nall - ns : 0;
         unsigned long long rounds = a.stats[S_ROUNDS];
-        unsigned long long cur_new = a.stats[S_NEW];
+        unsigned long long cur_new = a.stats[S_NEW] >> 1;
         if (rounds > 0) a.round_new_log[rounds - 1] = cur_new - *a.last_new;
         *a.last_new = cur_new;
         if (ns == 0) {

@@ -16,11 +16,11 @@
 // To avoid visiting ancestors one by one, each tree path is cut into
 // segments that stay inside one 8x8 pixel tile: for every vertex a, the
 // segment record holds the bits of a and of its ancestors up to the first
-// one outside a's tile, and that first outside ancestor. The marks use the
-// same tiling (one 64-bit word per row and tile), so one segment is tested
-// against row b's marks with a single AND. The operation count (every
-// ancestor pair, marked or not) comes from the tree depths instead, so rows
-// already filled are not walked at all.
+// one outside a's tile, and that first outside ancestor with its tile. The
+// marks use the same tiling (one 64-bit word per row and tile), so one
+// segment is tested against row b's marks with a single AND. The operation
+// count (every ancestor pair, marked or not) comes from the tree depths
+// instead, so rows already filled are not walked at all.
 #include "common.cuh"
 #include "internal.h"
 
@@ -53,10 +53,10 @@ __device__ __forceinline__ int canonical_parent(const TreeArgs& a, const uint32_
 }
 
 // The tree of one selected source, one block per source:
-//  1. parent[j][b]: the canonical parent;
+//  1. the canonical parent of every vertex;
 //  2. seg[j][v]: x = bits of v and of its ancestors up to the first one
-//     outside v's 8x8 tile, y = that first outside ancestor + 1 (0 past the
-//     root);
+//     outside v's 8x8 tile; y = that first outside ancestor + 1 (0 past the
+//     root) in the low 32 bits and its tile in the high 32 bits;
 //  3. the distance operations of the tree: the sum over reached b != s of
 //     depth(b), the number of proper ancestors of b. With acc(v) = number of
 //     vertices from v up to the root, depth(b) = acc(parent(b)); acc is
@@ -73,7 +73,6 @@ __global__ void __launch_bounds__(1024) k_tree(TreeArgs a) {
     const uint32_t* drow = a.D + (size_t)s * N;
     int32_t* par = a.parent + (size_t)j * N;
     ulonglong2* seg = a.seg + (size_t)j * N;
-    const TileGeom tg{a.W, a.tiles_w, a.words};
     // SMALL: the distance row is staged in shared memory (it shares the space
     // of the jumping arrays, used only later); spar = parent + 1, 0 for the
     // root, 0xFFFF for unreached vertices
@@ -84,7 +83,6 @@ __global__ void __launch_bounds__(1024) k_tree(TreeArgs a) {
         __syncthreads();
         for (int b = threadIdx.x; b < N; b += blockDim.x) {
             const int pb = canonical_parent(a, srow, s, b);
-            par[b] = pb;
             spar[b] = srow[b] == UNREACH ? (uint16_t)0xFFFF : (uint16_t)(pb + 1);
         }
     } else {
@@ -92,16 +90,20 @@ __global__ void __launch_bounds__(1024) k_tree(TreeArgs a) {
     }
     __syncthreads();
     for (int v = threadIdx.x; v < N; v += blockDim.x) {
-        const int t = tg.tile_of(v);
-        unsigned long long m = 1ull << tg.bit_of(v);
+        const uint32_t gv = __ldg(a.pgeo + v);
+        const uint32_t t = gv >> 8;
+        unsigned long long m = 1ull << (gv & 63);
         const int sv = SMALL ? (int)spar[v] : 0;
         int x = SMALL ? (sv == 0xFFFF ? -1 : sv - 1) : __ldcg(par + v);
-        for (int guard = 0; x >= 0 && guard < 64 && tg.tile_of(x) == t; ++guard) {
-            m |= 1ull << tg.bit_of(x);
+        uint32_t gx = x >= 0 ? __ldg(a.pgeo + x) : 0;
+        for (int guard = 0; x >= 0 && guard < 64 && (gx >> 8) == t; ++guard) {
+            m |= 1ull << (gx & 63);
             x = SMALL ? (int)spar[x] - 1 : __ldcg(par + x);
+            gx = x >= 0 ? __ldg(a.pgeo + x) : 0;
         }
         const bool reached = SMALL ? sv != 0xFFFF : drow[v] != UNREACH;
-        seg[v] = make_ulonglong2(m, (unsigned long long)(x + 1));
+        const unsigned long long y = x >= 0 ? ((unsigned long long)(gx >> 8) << 32) | (unsigned long long)(x + 1) : 0ull;
+        seg[v] = make_ulonglong2(m, y);
         if (SMALL) {
             sdep[v] = reached ? (uint16_t)__popcll(m) : 0;                 // acc, buffer 0
             sdep[2 * N + v] = reached ? (uint16_t)(x + 1) : 0;            // jmp + 1, buffer 0
@@ -167,12 +169,21 @@ __global__ void __launch_bounds__(1024) k_tree(TreeArgs a) {
 
 // One block owns up to 32 consecutive rows of the marks. Rows already
 // filled (cnt = N) hold every pair and are skipped; the others are copied
-// to shared memory, and for each selected source the block walks the tree
-// path of each of its rows, one tile segment at a time.
+// to shared memory. For each selected source the block walks the tree path
+// of each of its rows b, one tile segment at a time, from b's own segment
+// record: ORing a segment into the shared copy of row b returns the bits it
+// already had, and the others are new pairs {a, b}, so a pair that several
+// trees of the round share is taken once per row. For every new pair,
+// D[a][b] = D[b][a] = d(s,b) - d(s,a) (Property 1) and the mirror bit (row
+// a, column b) is ORed into the global marks without waiting for the old
+// value; the shared rows are ORed back at the end. A pair found from both of
+// its rows in the same round is written twice with the same value; the
+// counts come from the marks (k_recount), which hold each pair once per row.
 __global__ void k_fill(TreeArgs a) {
     extern __shared__ unsigned long long srow[];
-    __shared__ int s_rows[32];
+    __shared__ int s_rows[32], s_tile[32], s_bit[32];
     __shared__ int s_nu;
+    __shared__ unsigned s_gain;  // bit i: row s_rows[i] gained marks
     const int nsel = *a.nsel;
     if (nsel == 0) return;
     const int b0 = blockIdx.x * a.rows_per_block;
@@ -181,81 +192,133 @@ __global__ void k_fill(TreeArgs a) {
         const int lane = threadIdx.x;
         const bool open = lane < nrows && __ldcg(a.cnt + b0 + lane) < (uint32_t)a.N;
         const unsigned m = __ballot_sync(FULL, open);
-        if (open) s_rows[__popc(m & ((1u << lane) - 1u))] = b0 + lane;
-        if (lane == 0) s_nu = __popc(m);
+        if (open) {
+            const int i = __popc(m & ((1u << lane) - 1u));
+            const uint32_t g = __ldg(a.pgeo + b0 + lane);
+            s_rows[i] = b0 + lane;
+            s_tile[i] = (int)(g >> 8);
+            s_bit[i] = (int)(g & 63);
+        }
+        if (lane == 0) {
+            s_nu = __popc(m);
+            s_gain = 0;
+        }
     }
     __syncthreads();
     const int nu = s_nu;
     if (nu == 0) return;
-    const TileGeom tg{a.W, a.tiles_w, a.words};
-    for (int i = threadIdx.x; i < nu * a.words; i += blockDim.x) {
-        const int r = i / a.words, w = i - r * a.words;
-        srow[i] = ld_cg64(a.marks + (size_t)s_rows[r] * a.words + w);
+    const int words = a.words;
+    uint8_t* chg = reinterpret_cast<uint8_t*>(srow + (size_t)a.rows_per_block * words);
+    for (int i = threadIdx.x; i < nu * words; i += blockDim.x) {
+        const int r = i / words, w = i - r * words;
+        srow[i] = ld_cg64(a.marks + (size_t)s_rows[r] * words + w);
+        chg[i] = 0;
     }
     __syncthreads();
-    unsigned long long fresh = 0;
     const int items = nu * nsel;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
         const int j = it / nu, bl = it - j * nu, b = s_rows[bl];
         const int s = a.sel[j];
         const uint32_t* drow = a.D + (size_t)s * a.N;
-        const uint32_t db = drow[b];
+        const uint32_t db = __ldg(drow + b);
         if (b == s || db == UNREACH) continue;
         const ulonglong2* seg = a.seg + (size_t)j * a.N;
-        unsigned long long* myrow = srow + (size_t)bl * a.words;
-        unsigned fresh_b = 0;
-        int v = a.parent[(size_t)j * a.N + b];
-        for (int guard = 0; v >= 0 && guard <= a.N; ++guard) {
-            const ulonglong2 g = seg[v];
-            const int t = tg.tile_of(v);
-            unsigned long long nb = g.x & ~myrow[t];
-            while (nb) {
-                const int bit = __ffsll((long long)nb) - 1;
-                nb &= nb - 1;
-                const int ap = tg.pixel_of(t, bit);
-                // The pair {ap, b} is claimed on its canonical bit: row
-                // min(ap, b), column max(ap, b). The first claimant fills it.
-                const int lo = min(ap, b), hi = max(ap, b);
-                const unsigned long long cbit = 1ull << tg.bit_of(hi);
-                const unsigned long long old = atomicOr(a.marks + (size_t)lo * a.words + tg.tile_of(hi), cbit);
-                if (!(old & cbit)) {
-                    atomicOr(a.marks + (size_t)hi * a.words + tg.tile_of(lo), 1ull << tg.bit_of(lo));
-                    a.dirty[ap] = 1;
-                    ++fresh_b;
-                    const uint32_t val = db - drow[ap];
-                    // streaming stores: D is far larger than L2, keep the
-                    // trees and marks resident instead
-                    __stcs(a.Dw + (size_t)ap * a.N + b, val);
-                    __stcs(a.Dw + (size_t)b * a.N + ap, val);
+        unsigned long long* myrow = srow + (size_t)bl * words;
+        uint8_t* mychg = chg + (size_t)bl * words;
+        const int tb = s_tile[bl];
+        const unsigned long long bbit = 1ull << s_bit[bl];
+        ulonglong2 g = __ldg(seg + b);
+        unsigned long long m = g.x & ~bbit;  // b's ancestors inside b's tile
+        int t = tb;
+        bool gained = false;
+        for (int guard = 0; guard <= a.N; ++guard) {
+            const unsigned long long y = g.y;
+            const int ex = (int)(uint32_t)y - 1;
+            // fetch the next segment record before working on this one
+            ulonglong2 gn = make_ulonglong2(0ull, 0ull);
+            if (ex >= 0) gn = __ldg(seg + ex);
+            if (m) {
+                // two 32-bit ORs: a 64-bit OR on shared memory is much slower
+                unsigned* w32 = reinterpret_cast<unsigned*>(myrow + t);
+                const unsigned lo = (unsigned)m, hi = (unsigned)(m >> 32);
+                const unsigned olo = lo ? atomicOr(w32, lo) : 0xFFFFFFFFu;
+                const unsigned ohi = hi ? atomicOr(w32 + 1, hi) : 0xFFFFFFFFu;
+                unsigned long long nb = m & ~(((unsigned long long)ohi << 32) | olo);
+                if (nb) {
+                    gained = true;
+                    mychg[t] = 1;
+                    const int base = __ldg(a.tbase + t);
+                    // up to 8 new pairs at a time: the distance loads first,
+                    // so that they are in flight together, then the stores.
+                    // The rows d(s, .) read here only ever receive the same
+                    // exact values again, so read-only loads are safe.
+                    while (nb) {
+                        int ap[8];
+                        uint32_t dv[8];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            ap[k] = -1;
+                            if (nb) {
+                                const int bit = __ffsll((long long)nb) - 1;
+                                nb &= nb - 1;
+                                ap[k] = base + (bit >> 3) * a.W + (bit & 7);
+                                dv[k] = __ldg(drow + ap[k]);
+                            }
+                        }
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            if (ap[k] < 0) continue;
+                            const uint32_t val = db - dv[k];
+                            atomicOr(a.marks + (size_t)ap[k] * words + tb, bbit);
+                            a.dirty[ap[k]] = 1;
+                            // streaming stores: D is far larger than L2, keep
+                            // the trees and marks resident instead
+                            __stcs(a.Dw + (size_t)ap[k] * a.N + b, val);
+                            __stcs(a.Dw + (size_t)b * a.N + ap[k], val);
+                        }
+                    }
                 }
-                atomicOr(myrow + t, 1ull << bit);
             }
-            v = (int)g.y - 1;
+            if (ex < 0) break;
+            t = (int)(y >> 32);
+            g = gn;
+            m = g.x;
         }
-        if (fresh_b) {
-            a.dirty[b] = 1;
-            fresh += fresh_b;
-        }
+        if (gained) atomicOr(&s_gain, 1u << bl);
     }
-    for (int o = 16; o > 0; o >>= 1) fresh += __shfl_down_sync(FULL, fresh, o);
-    if ((threadIdx.x & 31) == 0 && fresh) atomicAdd(a.stats + S_NEW, fresh);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nu * words; i += blockDim.x)
+        if (chg[i]) {
+            const int r = i / words, w = i - r * words;
+            atomicOr(a.marks + (size_t)s_rows[r] * words + w, srow[i]);
+        }
+    if (threadIdx.x < nu && ((s_gain >> threadIdx.x) & 1u)) a.dirty[s_rows[threadIdx.x]] = 1;
 }
 
 // Fill counts of the rows that gained marks: cnt(x) = cnt at the start +
 // the number of marked pairs of row x (both bits of a pair are set, so row
-// x holds every filled pair {x, y}). One warp per row.
+// x holds every filled pair {x, y}). One warp per row. The increments are
+// summed into S_NEW, which thus counts every new pair twice.
 __global__ void k_recount(TreeArgs a) {
+    __shared__ unsigned long long s_sum;
+    if (threadIdx.x == 0) s_sum = 0;
+    __syncthreads();
     const int x = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (x >= a.N || !a.dirty[x]) return;
-    const unsigned long long* row = a.marks + (size_t)x * a.words;
-    unsigned c = 0;
-    for (int w = lane; w < a.words; w += 32) c += __popcll(__ldcg(row + w));
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(FULL, c, o);
-    if (lane == 0) {
-        a.cnt[x] = a.cnt_base[x] + c;
-        a.dirty[x] = 0;
+    if (x < a.N && a.dirty[x]) {
+        const unsigned long long* row = a.marks + (size_t)x * a.words;
+        unsigned c = 0;
+        for (int w = lane; w < a.words; w += 32) c += __popcll(__ldcg(row + w));
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(FULL, c, o);
+        if (lane == 0) {
+            const uint32_t nc = a.cnt_base[x] + c;
+            atomicAdd(&s_sum, (unsigned long long)(nc - a.cnt[x]));
+            a.cnt[x] = nc;
+            a.dirty[x] = 0;
+        }
     }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_sum) atomicAdd(a.stats + S_NEW, s_sum);
 }
 
 }  // namespace
@@ -281,7 +344,8 @@ cudaError_t launch_tree(const TreeArgs& a, int B, cudaStream_t st) {
 
 cudaError_t launch_fill(const TreeArgs& a, int B, cudaStream_t st) {
     (void)B;
-    const size_t smem = (size_t)a.rows_per_block * a.words * sizeof(unsigned long long);
+    // mark rows, then one "changed" byte per row word
+    const size_t smem = (size_t)a.rows_per_block * a.words * (sizeof(unsigned long long) + 1);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

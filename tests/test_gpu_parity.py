@@ -187,6 +187,35 @@ def test_all_pairs_repeat_and_orders_share_handle(gp):
             assert np.array_equal(_u32(D), ref)
 
 
+@pytest.mark.parametrize("order", ["minfill", "naive", "spiral", "extrema"])
+@pytest.mark.parametrize("lookahead", [-1, 1, 5, 0])
+def test_lookahead_changes_nothing(gp, order, lookahead):
+    """Rows computed ahead of their round (any candidate count, or none)
+    leave D, the counts, the per-round new pairs and the source order as the
+    oracle's simulation has them."""
+    img = synth.blobs(37, 29, 5, 3.0, 55.0, seed=8)
+    with gp.Image(img, conn=8, B=6, lookahead=lookahead) as im:
+        D, st = im.all_pairs(order, want_log=True)
+    ref = oracle.fill(img, order, B=6, conn=8)
+    assert np.array_equal(_u32(D), oracle.apsp(img, conn=8))
+    for k in ("propagations", "prepass_propagations", "distance_ops", "new_pairs", "rounds"):
+        assert st[k] == getattr(ref, k), k
+    assert np.array_equal(st["round_new"], ref.round_new)
+    assert np.array_equal(st["sources"], ref.sources)
+    if lookahead < 0:
+        assert st["lookahead_propagations"] == 0
+    else:
+        assert st["lookahead_propagations"] > 0
+
+
+def test_lookahead_rejects_bad_counts(gp):
+    img = synth.blobs(8, 8, 2, 2.0, 55.0, seed=1)
+    for bad in (-2, 1025):
+        with pytest.raises(gp.GapspError) as e:
+            gp.Image(img, conn=8, B=4, lookahead=bad)
+        assert e.value.code == 1
+
+
 def test_budget_rejected_before_allocation(gp):
     img = synth.blobs(64, 64, 4, 4.0, 55.0, seed=1)
     with gp.Image(img, conn=8, B=32, mem_budget=1 << 20) as im:
