@@ -470,10 +470,12 @@ struct FillRun {
     int K = 0;
     PropArgs pa_ahead{};
     cudaStream_t side = nullptr;
-    cudaEvent_t e_sel = nullptr, e_ahead = nullptr;
+    cudaEvent_t e_sel = nullptr;
+    cudaEvent_t e_ahead[2] = {nullptr, nullptr};  // lookahead launch of an even / odd round
     ~FillRun() {
         if (e_sel) cudaEventDestroy(e_sel);
-        if (e_ahead) cudaEventDestroy(e_ahead);
+        for (cudaEvent_t e : e_ahead)
+            if (e) cudaEventDestroy(e);
         if (side) cudaStreamDestroy(side);
     }
 };
@@ -598,6 +600,8 @@ gapsp_status fill_begin(FillRun& r) {
     r.K = lookahead_count(h, pa);
     if (r.K > 0) {
         r.sa.K = r.K;
+        r.sa.KL = 1024 - h->B;
+        r.sa.row_done = h->row_done;
         r.sa.cand = h->cand;
         r.sa.ncand = h->ncand;
         r.pa_ahead = pa;
@@ -605,7 +609,8 @@ gapsp_status fill_begin(FillRun& r) {
         pa.hits = h->stats + S_HITS;
         CK(cudaStreamCreateWithFlags(&r.side, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&r.e_sel, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&r.e_ahead, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&r.e_ahead[0], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&r.e_ahead[1], cudaEventDisableTiming));
     }
     TreeArgs& ta = r.ta;
     ta = TreeArgs{};
@@ -647,9 +652,9 @@ gapsp_status fill_enqueue(FillRun& r, int chunk) {
             CK(launch_select(r.sa, s));
         }
         if (r.K > 0) {
-            // this round's sources may have been computed by the previous
-            // round's lookahead: wait for it, then start this round's
-            CK(cudaStreamWaitEvent(s, r.e_ahead, 0));
+            // this round's candidates go to the second stream, where they
+            // start as soon as the previous round's lookahead is done (the
+            // kernel skips any row that launch computed meanwhile) ...
             CK(cudaEventRecord(r.e_sel, s));
             CK(cudaStreamWaitEvent(r.side, r.e_sel, 0));
             r.pa_ahead.sources = h->cand + par * 1024;
@@ -659,8 +664,11 @@ gapsp_status fill_enqueue(FillRun& r, int chunk) {
                 ProfScope ps(h, K_AHEAD, r.side);
                 CK(launch_propagate(r.pa_ahead, h->conn, h->kind, r.K, 1, r.side));
             }
-            CK(cudaEventRecord(r.e_ahead, r.side));
+            CK(cudaEventRecord(r.e_ahead[par], r.side));
             h->launches += 1;
+            // ... and this round's own propagation waits for the previous
+            // round's lookahead, which may have computed its sources
+            CK(cudaStreamWaitEvent(s, r.e_ahead[par ^ 1], 0));
         }
         {
             ProfScope ps(h, K_PROP, s);
@@ -697,7 +705,10 @@ gapsp_status fill_finish(FillRun& r, gapsp_stats* st) {
     gapsp_handle* h = r.h;
     cudaStream_t s = r.s;
     const size_t N = h->N;
-    if (r.K > 0) CK(cudaStreamWaitEvent(s, r.e_ahead, 0));
+    if (r.K > 0) {
+        CK(cudaStreamWaitEvent(s, r.e_ahead[0], 0));
+        CK(cudaStreamWaitEvent(s, r.e_ahead[1], 0));
+    }
     CK(cudaEventRecord(h->ev1, s));
     unsigned long long hs[S_SLOTS];
     int sw = 0;

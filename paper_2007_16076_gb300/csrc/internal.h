@@ -88,7 +88,10 @@ struct SelectArgs {
     int* done;                  // set to 1 once every point is filled
     int32_t* cand;              // lookahead candidates (capacity K), or NULL
     int* ncand;                 // device count of candidates, or NULL
-    int K;                      // wanted candidates (B + K <= 1024)
+    int K;                      // candidates wanted: rows not computed yet
+    int KL;                     // ranking positions after the selection they are taken
+                                // from (B + KL <= 1024)
+    const uint8_t* row_done;    // [N]: rows already computed
 };
 cudaError_t launch_select(const SelectArgs& a, cudaStream_t st);
 

@@ -88,7 +88,25 @@ struct Shared {
 // rounds, the last result of this warp on it still satisfies every edge
 // this direction tests (the flags of a round are read only after the
 // block barrier that ends it).
-template <int CONN, int KIND, int VPL, bool ROWS, class Map>
+// VPL grey levels of one lane, from a VPL-aligned address in shared memory.
+template <int VPL>
+__device__ __forceinline__ void load_levels(const uint8_t* p, int (&fc)[VPL]) {
+    if constexpr (VPL == 4) {
+        const uchar4 u = *reinterpret_cast<const uchar4*>(p);
+        fc[0] = u.x; fc[1] = u.y; fc[2] = u.z; fc[3] = u.w;
+    } else if constexpr (VPL == 2) {
+        const uchar2 u = *reinterpret_cast<const uchar2*>(p);
+        fc[0] = u.x; fc[1] = u.y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < VPL; ++k) fc[k] = p[k];
+    }
+}
+
+// EX: every line is exactly 32 * VPL pixels long (square single-block
+// images such as 128 x 128 with VPL = 4), so no lane holds a pixel past the
+// end of a line and the bounds tests drop out.
+template <int CONN, int KIND, int VPL, bool ROWS, bool EX, class Map>
 __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int dir, int start, int lane,
                       int round, int& nproc) {
     const int nlines = ROWS ? sh.hs : a.W;
@@ -146,13 +164,14 @@ __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int d
 #pragma unroll
         for (int k = 0; k < VPL; ++k) {
             const int pos = VPL * lane + k;
-            fc[k] = pos < len ? f_line[l * len + pos] : 0;
+            if (!EX) fc[k] = pos < len ? f_line[l * len + pos] : 0;
         }
+        if (EX) load_levels<VPL>(f_line + l * len + VPL * lane, fc);
         if (skip) {
 #pragma unroll
             for (int k = 0; k < VPL; ++k) {
                 const int pos = VPL * lane + k;
-                const int dv = pos < len ? (ROWS ? map.ld(l, pos) : map.ld(pos, l)) : PINF;
+                const int dv = (EX || pos < len) ? (ROWS ? map.ld(l, pos) : map.ld(pos, l)) : PINF;
                 gp[k] = KIND == 0 ? dv + fc[k] : dv;
             }
             has_pred = true;
@@ -167,7 +186,7 @@ __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int d
 #pragma unroll
         for (int k = 0; k < VPL; ++k) {
             const int pos = VPL * lane + k;
-            const bool valid = pos < len;
+            const bool valid = EX || pos < len;
             o[k] = valid ? (ROWS ? map.ld(l, pos) : map.ld(pos, l)) : PINF;
             freep[k] = valid && (KIND == 0 || fc[k] != 0);
         }
@@ -295,7 +314,7 @@ __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int d
     return changed;
 }
 
-template <int CONN, int KIND, int VPL, class Map, bool CL>
+template <int CONN, int KIND, int VPL, class Map, bool CL, bool EX>
 __device__ void run_block(const PropArgs& a, const Map& map, const Shared& sh, int* s_flag, int* s_rounds) {
     const int nr = sh.hs, nc = a.W;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -313,8 +332,8 @@ __device__ void run_block(const PropArgs& a, const Map& map, const Shared& sh, i
         for (int i = threadIdx.x; i < nr; i += blockDim.x) sh.chR[nx * nr + i] = 0;
         for (int i = threadIdx.x; i < nc; i += blockDim.x) sh.chC[nx * nc + i] = 0;
         bool ch;
-        if (rows) ch = sweep<CONN, KIND, VPL, true, Map>(a, map, sh, dir, start, lane, round, nproc);
-        else ch = sweep<CONN, KIND, VPL, false, Map>(a, map, sh, dir, start, lane, round, nproc);
+        if (rows) ch = sweep<CONN, KIND, VPL, true, EX, Map>(a, map, sh, dir, start, lane, round, nproc);
+        else ch = sweep<CONN, KIND, VPL, false, EX, Map>(a, map, sh, dir, start, lane, round, nproc);
         ch = __any_sync(FULL, ch);
         if (lane == 0 && ch) s_flag[round & 1] = 1;
         bool any;
@@ -427,7 +446,7 @@ __device__ void flag_seed_lines(const PropArgs& a, const Shared& sh, int src) {
 // Map in shared memory. One block per job, or a cluster of C blocks per job
 // (CL), each owning a strip of rows; the strips see each other's edge rows
 // through distributed shared memory.
-template <int CONN, int KIND, int VPL, bool CL>
+template <int CONN, int KIND, int VPL, bool CL, bool EX>
 __global__ void __launch_bounds__(32 * MAXWARPS) k_propagate_smem(PropArgs a, int pitch, int C) {
     extern __shared__ int smap[];
     __shared__ int s_flag[2], s_rounds;
@@ -470,7 +489,7 @@ __global__ void __launch_bounds__(32 * MAXWARPS) k_propagate_smem(PropArgs a, in
         __syncthreads();
     }
     const SmemMap map{smap, pitch};
-    run_block<CONN, KIND, VPL, SmemMap, CL>(a, map, sh, s_flag, &s_rounds);
+    run_block<CONN, KIND, VPL, SmemMap, CL, EX>(a, map, sh, s_flag, &s_rounds);
     if (CL) cg::this_cluster().sync();  // no block leaves while others may read it
     __syncthreads();
     if (threadIdx.x == 0 && a.sweeps) atomicAdd(a.sweeps, (unsigned long long)s_rounds * (blockDim.x >> 5));
@@ -523,7 +542,7 @@ __global__ void __launch_bounds__(32 * MAXWARPS) k_propagate_glob(PropArgs a) {
     flag_seed_lines(a, sh, src);
     __syncthreads();
     const GlobMap gm{map, a.W};
-    run_block<CONN, KIND, VPL, GlobMap, false>(a, gm, sh, s_flag, &s_rounds);
+    run_block<CONN, KIND, VPL, GlobMap, false, false>(a, gm, sh, s_flag, &s_rounds);
     __syncthreads();
     if (threadIdx.x == 0 && a.sweeps) atomicAdd(a.sweeps, (unsigned long long)s_rounds * (blockDim.x >> 5));
     if (a.convert) {
@@ -565,9 +584,11 @@ cudaError_t launch_one(const PropArgs& a, int jobs, cudaStream_t st) {
     const int threads = 32 * 4 * (a.phases == 4 ? 4 : a.phases == 2 ? 2 : 1);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_propagate_smem<CONN, KIND, VPL, false>,
+        cudaFuncSetAttribute(k_propagate_smem<CONN, KIND, VPL, false, false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
-        cudaFuncSetAttribute(k_propagate_smem<CONN, KIND, VPL, true>,
+        cudaFuncSetAttribute(k_propagate_smem<CONN, KIND, VPL, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
+        cudaFuncSetAttribute(k_propagate_smem<CONN, KIND, VPL, true, false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
         cudaFuncSetAttribute(k_propagate_glob<CONN, KIND, VPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              SMEM_LIMIT);
@@ -577,7 +598,10 @@ cudaError_t launch_one(const PropArgs& a, int jobs, cudaStream_t st) {
     if (C > 0) {
         const size_t smem = smem_for_strips(a, C);
         if (C == 1) {
-            k_propagate_smem<CONN, KIND, VPL, false><<<jobs, threads, smem, st>>>(a, pitch, 1);
+            if (a.W == 32 * VPL && a.H == 32 * VPL)
+                k_propagate_smem<CONN, KIND, VPL, false, true><<<jobs, threads, smem, st>>>(a, pitch, 1);
+            else
+                k_propagate_smem<CONN, KIND, VPL, false, false><<<jobs, threads, smem, st>>>(a, pitch, 1);
         } else {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(jobs * C);
@@ -591,7 +615,7 @@ cudaError_t launch_one(const PropArgs& a, int jobs, cudaStream_t st) {
             at[0].val.clusterDim.z = 1;
             cfg.attrs = at;
             cfg.numAttrs = 1;
-            cudaError_t e = cudaLaunchKernelEx(&cfg, k_propagate_smem<CONN, KIND, VPL, true>, a, pitch, C);
+            cudaError_t e = cudaLaunchKernelEx(&cfg, k_propagate_smem<CONN, KIND, VPL, true, false>, a, pitch, C);
             if (e != cudaSuccess) return e;
         }
     } else {

@@ -48,15 +48,17 @@ __global__ void k_select_seq(SelectArgs a) {
         }
         ns += take;
     }
-    // lookahead candidates: the next K points of the sequence after the
-    // selection that are unfilled now (the cursor does not move for them)
+    // lookahead candidates: within the next KL positions of the sequence
+    // after the selection, the first K points that are unfilled now and whose
+    // rows are not computed yet (the cursor does not move for them)
     int nc = 0;
     if (a.K > 0) {
         int c2 = cursor;
-        while (nc < a.K && c2 < a.nseq) {
+        const int lim = min(a.nseq, cursor + a.KL);
+        while (nc < a.K && c2 < lim) {
             const int idx = c2 + lane;
-            const int p = idx < a.nseq ? a.seq[idx] : -1;
-            const bool ok = p >= 0 && a.cnt[p] < (uint32_t)a.N;
+            const int p = idx < lim ? a.seq[idx] : -1;
+            const bool ok = p >= 0 && a.cnt[p] < (uint32_t)a.N && !(a.row_done && a.row_done[p]);
             const unsigned m = __ballot_sync(FULL, ok);
             const int take = min(__popc(m), a.K - nc);
             const int before = __popc(m & ((1u << lane) - 1u));
@@ -112,6 +114,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
     __shared__ int s_need, s_count, s_unfilled;
     __shared__ unsigned long long s_keys[1024];
     __shared__ int s_pix[1024];
+    __shared__ int s_wcount[32], s_ncand;
     const int tid = threadIdx.x;
     if (*a.done) {
         if (tid == 0) {
@@ -134,8 +137,9 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
     auto key = [&](int p) -> unsigned long long { return CACHED ? skeys[p] : mf_key(a, p); };
     const int unfilled = s_unfilled;
     const int want = min(unfilled, a.B);
-    // the selection, then up to K lookahead candidates in key order
-    const int wantc = min(unfilled, a.B + (a.K > 0 ? a.K : 0));
+    // the selection, then the next KL points in key order, from which the
+    // lookahead candidates are taken
+    const int wantc = min(unfilled, a.B + (a.K > 0 ? a.KL : 0));
     unsigned long long thr = ~0ull - 1;  // select keys <= thr
     if (wantc > 0 && wantc < unfilled) {
         // the want-th smallest key, 8 bits at a time from the top bit a key
@@ -184,12 +188,18 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
         }
         thr = prefix;
     }
-    // gather the selected points
+    // gather the selected points (one shared atomic per warp)
     if (want > 0) {
-        for (int p = tid; p < a.N; p += SEL_THREADS) {
-            const unsigned long long k = key(p);
-            if (k != ~0ull && k <= thr) {
-                const int slot = atomicAdd(&s_count, 1);
+        for (int p0 = 0; p0 < a.N; p0 += SEL_THREADS) {
+            const int p = p0 + tid;
+            const unsigned long long k = p < a.N ? key(p) : ~0ull;
+            const bool take = k != ~0ull && k <= thr;
+            const unsigned m = __ballot_sync(FULL, take);
+            int base = 0;
+            if ((tid & 31) == 0 && m) base = atomicAdd(&s_count, __popc(m));
+            base = __shfl_sync(FULL, base, 0);
+            if (take) {
+                const int slot = base + __popc(m & ((1u << (tid & 31)) - 1u));
                 if (slot < 1024) { s_keys[slot] = k; s_pix[slot] = p; }
             }
         }
@@ -197,24 +207,58 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
     __syncthreads();
     const int nall = min(s_count, wantc);
     const int ns = min(nall, want);
-    // order by key (rank sort; keys are distinct): the first ns are the
-    // selection, the rest the candidates
-    if (tid < nall) {
-        const unsigned long long k = s_keys[tid];
-        int pos = 0;
-        for (int i = 0; i < nall; ++i) pos += s_keys[i] < k;
-        if (pos < ns) {
-            a.sel[pos] = s_pix[tid];
-            const unsigned long long props = a.stats[S_PROPAGATIONS];
-            a.sel_log[props + pos] = s_pix[tid];
-        } else if (a.cand) {
-            a.cand[pos - ns] = s_pix[tid];
+    // bitonic sort by key (keys are distinct), padded to a power of two
+    int n2 = 1;
+    while (n2 < nall) n2 <<= 1;
+    for (int i = nall + tid; i < n2; i += SEL_THREADS) s_keys[i] = ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= n2; k <<= 1)
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int i = tid; i < n2; i += SEL_THREADS) {
+                const int ixj = i ^ jj;
+                if (ixj > i) {
+                    const unsigned long long ki = s_keys[i], kj = s_keys[ixj];
+                    if ((ki > kj) == ((i & k) == 0)) {
+                        s_keys[i] = kj;
+                        s_keys[ixj] = ki;
+                        const int t = s_pix[i];
+                        s_pix[i] = s_pix[ixj];
+                        s_pix[ixj] = t;
+                    }
+                }
+            }
+            __syncthreads();
         }
+    if (tid < ns) {
+        a.sel[tid] = s_pix[tid];
+        a.sel_log[a.stats[S_PROPAGATIONS] + tid] = s_pix[tid];
+    }
+    // candidates: in key order after the selection, the first K whose rows
+    // are not computed yet
+    if (a.cand) {
+        const int i = ns + tid;
+        const bool ok = i < nall && !(a.row_done && a.row_done[s_pix[i]]);
+        const unsigned m = __ballot_sync(FULL, ok);
+        if ((tid & 31) == 0) s_wcount[tid >> 5] = __popc(m);
+        __syncthreads();
+        if (tid < 32) {
+            const int c = s_wcount[tid];
+            int incl = c;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(FULL, incl, o);
+                if (tid >= o) incl += u;
+            }
+            s_wcount[tid] = incl - c;  // exclusive
+            if (tid == 31) s_ncand = incl;
+        }
+        __syncthreads();
+        const int pos = s_wcount[tid >> 5] + __popc(m & ((1u << (tid & 31)) - 1u));
+        if (ok && pos < a.K) a.cand[pos] = s_pix[i];
     }
     __syncthreads();
     if (tid == 0) {
         *a.nsel = ns;
-        if (a.ncand) *a.ncand = ns ? nall - ns : 0;
+        if (a.ncand) *a.ncand = ns ? min(s_ncand, a.K) : 0;
         unsigned long long rounds = a.stats[S_ROUNDS];
         unsigned long long cur_new = a.stats[S_NEW] >> 1;
         if (rounds > 0) a.round_new_log[rounds - 1] = cur_new - *a.last_new;
