@@ -163,7 +163,7 @@ PropArgs base_prop(const gapsp_handle* h) {
     a.f = h->f;
     a.status = h->status;
     a.max_sweeps = 4 * (h->N + 2);
-    a.phases = h->sweep_phases ? h->sweep_phases : 2;
+    a.phases = h->sweep_phases ? h->sweep_phases : 4;
     // one block per source unless its map does not fit in one block's shared
     // memory (then the launch splits it into row strips over a cluster);
     // splitting smaller maps costs more rounds than it saves (measured)
@@ -430,7 +430,7 @@ gapsp_status gapsp_rows(gapsp_handle* h, const int32_t* sources, int K, uint32_t
     a.sources = h->src_dev;
     a.njobs = K;
     a.convert = h->kind == GAPSP_MASK;
-    if (!h->sweep_phases) a.phases = K > 304 ? 1 : 2;  // latency-bound when few sources
+    if (!h->sweep_phases) a.phases = K > 304 ? 1 : 4;  // latency-bound when few sources
 
     const int wpb = 1;
     {

@@ -106,7 +106,7 @@ extern "C" gapsp_status gapsp_rows_noalloc(const uint8_t* img, int H, int W, int
     a.sources = dsrc;
     a.njobs = K;
     a.convert = kind == GAPSP_MASK;
-    a.phases = K > 304 ? 1 : 2;
+    a.phases = K > 304 ? 1 : 4;
     a.cluster = 1;
     if (launch_propagate(a, conn, (int)kind, K, 1, st) != cudaSuccess) {
         cudaGetLastError();

@@ -10,16 +10,17 @@
 // at the seeds and "unreached" elsewhere, next to two copies of the image
 // (row-major and column-major). Warps sweep the map concurrently, each in
 // its own direction (rows top-down, rows bottom-up, columns left-right,
-// columns right-left), one or two warps per direction starting half an
-// image apart. For each line a warp
+// columns right-left); when a direction has two or four warps, each sweeps
+// an equal contiguous share of its lines every round, starting from the
+// line before its share as it stands. For each line a warp
 //   1. relaxes every pixel from the previous line it just finished (the
 //      three neighbours behind it for 8-connectivity, one for 4), then
-//   2. closes the line in both directions: with P the prefix sum of the
-//      line's edge weights, the best value along the line is
-//      min_c' v(c') + |P(c) - P(c')|, a prefix-min of v - P and a suffix-min
-//      of v + P. Lane j holds pixels VPL*j .. VPL*j+VPL-1, so the scans run
-//      inside the lane and use warp shuffles only when a boundary test
-//      shows that a value must cross from one lane to another,
+//   2. closes the line inside each lane: lane j holds pixels VPL*j ..
+//      VPL*j+VPL-1 and, with P the prefix sum of the line's edge weights,
+//      takes min_c' v(c') + |P(c) - P(c')| over its own pixels (a prefix-min
+//      of v - P and a suffix-min of v + P). Values cross lane boundaries
+//      through the sweeps of the other axis; a full warp-wide scan on every
+//      line measured slower,
 // and lowers the map with atomic minima, flagging every line that a lowered
 // pixel belongs to (its own line and the crossing one). After the first
 // rounds most lines stop changing, and a warp skips a line when neither it
@@ -70,7 +71,6 @@ struct Shared {
     const uint8_t* fC;  // strip of the image, column-major [W][hs]
     uint8_t* chR;       // [3][hs]: row line lowered during round t (slot t % 3)
     uint8_t* chC;       // [3][W]: column line lowered during round t
-    const int* Pb;      // [hs + W][32]: prefix of the line's edge weights at each lane's first pixel
     int r0, hs;
     // rows next to the strip, owned by the neighbour blocks of the cluster
     // (distributed shared memory), or NULL at the image border
@@ -108,7 +108,7 @@ __device__ __forceinline__ void load_levels(const uint8_t* p, int (&fc)[VPL]) {
 // end of a line and the bounds tests drop out.
 template <int CONN, int KIND, int VPL, bool ROWS, bool EX, class Map>
 __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int dir, int start, int lane,
-                      int round, int& nproc) {
+                      int round, int& nproc, int seg) {
     const int nlines = ROWS ? sh.hs : a.W;
     const int len = ROWS ? a.W : sh.hs;
     const uint8_t* f_line = ROWS ? sh.fR : sh.fC;
@@ -116,7 +116,6 @@ __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int d
     uint8_t* ch_x = (ROWS ? sh.chC : sh.chR) + (round % 3) * len;
     const uint8_t* prev_own = (ROWS ? sh.chR : sh.chC) + ((round + 2) % 3) * nlines;
     const int wrap_at = dir > 0 ? 0 : nlines - 1;  // a sweep restarts here
-    const int* Pb = sh.Pb + (ROWS ? 0 : sh.hs * 32);
     // gp[k]: cost of leaving the previous line's pixel, d + f (grey) or d (mask)
     int gp[VPL];
 #pragma unroll
@@ -125,7 +124,7 @@ __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int d
     bool pred_changed = false;  // the previous line changed (it must be relaxed from)
     bool changed = false;
     int l = start;
-    for (int i = 0; i < nlines; ++i) {
+    for (int i = 0; i < seg; ++i) {
         if (i == 0 || l == wrap_at) {
             // (re)start: the previous line is the neighbour block's edge row
             // when the sweep enters the strip from a split border, else none
@@ -151,9 +150,24 @@ __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int d
                     for (int k = 0; k < VPL; ++k) {
                         const int pos = VPL * lane + k;
                         const int dv = pos < len ? *((volatile const int*)(rmap + rrow * rpitch + pos)) : PINF;
-                        gp[k] = (KIND == 0 && pos < len) ? dv + (int)__ldg(a.f + grow * a.W + pos) : dv;
+                        const int fg = pos < len ? (int)__ldg(a.f + grow * a.W + pos) : 0;
+                        gp[k] = KIND == 0 ? (pos < len ? dv + fg : dv) : (fg ? dv : PINF);
                     }
                 }
+            }
+        }
+        if (i == 0 && l != wrap_at) {
+            // the warp's share of the lines starts inside the image: relax
+            // from the line before it, as it stands now
+            const int lp = l - dir;
+            has_pred = true;
+            pred_changed = prev_own[lp] != 0 || *((volatile const uint8_t*)(ch_own + lp)) != 0;
+#pragma unroll
+            for (int k = 0; k < VPL; ++k) {
+                const int pos = VPL * lane + k;
+                const int dv = (EX || pos < len) ? (ROWS ? map.ld(lp, pos) : map.ld(pos, lp)) : PINF;
+                const int fp = (EX || pos < len) ? (int)f_line[lp * len + pos] : 0;
+                gp[k] = KIND == 0 ? dv + fp : (fp ? dv : PINF);
             }
         }
         // lowered in the previous round, or already in this one (seen so far);
@@ -172,7 +186,7 @@ __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int d
             for (int k = 0; k < VPL; ++k) {
                 const int pos = VPL * lane + k;
                 const int dv = (EX || pos < len) ? (ROWS ? map.ld(l, pos) : map.ld(pos, l)) : PINF;
-                gp[k] = KIND == 0 ? dv + fc[k] : dv;
+                gp[k] = KIND == 0 ? dv + fc[k] : (fc[k] ? dv : PINF);
             }
             has_pred = true;
             pred_changed = false;
@@ -191,9 +205,9 @@ __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int d
             freep[k] = valid && (KIND == 0 || fc[k] != 0);
         }
         if (KIND == 0) {
-            // prefix of the line's edge weights f(c) + f(c+1) + 1: the lane's
-            // base from the table, then the lane's own pixels
-            int acc = Pb[l * 32 + lane];
+            // prefix of the line's edge weights f(c) + f(c+1) + 1 from the
+            // lane's first pixel (only differences inside a lane are used)
+            int acc = 0;
 #pragma unroll
             for (int k = 0; k < VPL; ++k) {
                 p[k] = acc;
@@ -201,7 +215,7 @@ __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int d
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < VPL; ++k) p[k] = 2 * (VPL * lane + k);
+            for (int k = 0; k < VPL; ++k) p[k] = 2 * k;
         }
         // 1. relax from the previous line
         int gl0 = PINF, gr0 = PINF;
@@ -238,52 +252,6 @@ __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int d
 #pragma unroll
         for (int k = 0; k < VPL; ++k)
             d[k] = freep[k] ? min(v[k], min(sx[k] + p[k], sy[k] - p[k])) : PINF;
-        // does a value have to cross a lane boundary?
-        const int xl = freep[VPL - 1] ? d[VPL - 1] - p[VPL - 1] : BIGX;
-        const int yf = freep[0] ? d[0] + p[0] : BIGY;
-        const int xl_left = __shfl_up_sync(FULL, xl, 1);
-        const int yf_right = __shfl_down_sync(FULL, yf, 1);
-        const bool need = (lane > 0 && freep[0] && xl_left < d[0] - p[0]) ||
-                          (lane < 31 && freep[VPL - 1] && yf_right < d[VPL - 1] + p[VPL - 1]);
-        if (__any_sync(FULL, need)) {
-            // exclusive prefix-min of the lane totals of v - P (suffix-min of
-            // v + P); on a mask, runs of free pixels are separate segments
-            int tx = sx[VPL - 1], ty = sy[0];
-            bool hx = false, hy = false;
-            int first_ob = VPL, last_ob = -1;
-            if (KIND == 1) {
-#pragma unroll
-                for (int k = VPL - 1; k >= 0; --k) if (!freep[k]) first_ob = k;
-#pragma unroll
-                for (int k = 0; k < VPL; ++k) if (!freep[k]) last_ob = k;
-                hx = hy = first_ob < VPL;
-            }
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const int tx2 = __shfl_up_sync(FULL, tx, off);
-                const int ty2 = __shfl_down_sync(FULL, ty, off);
-                if (KIND == 1) {  // segmented scans: stop at a lane holding an obstacle
-                    const bool hx2 = __shfl_up_sync(FULL, (int)hx, off);
-                    const bool hy2 = __shfl_down_sync(FULL, (int)hy, off);
-                    if (lane >= off && !hx) { tx = min(tx, tx2); hx = hx2; }
-                    if (lane + off < 32 && !hy) { ty = min(ty, ty2); hy = hy2; }
-                } else {
-                    if (lane >= off) tx = min(tx, tx2);
-                    if (lane + off < 32) ty = min(ty, ty2);
-                }
-            }
-            int ex = __shfl_up_sync(FULL, tx, 1);
-            int ey = __shfl_down_sync(FULL, ty, 1);
-            if (lane == 0) ex = BIGX;
-            if (lane == 31) ey = BIGY;
-#pragma unroll
-            for (int k = 0; k < VPL; ++k) {
-                if (!freep[k]) continue;
-                const int px = (KIND == 1 && k > first_ob) ? sx[k] : min(ex, sx[k]);
-                const int py = (KIND == 1 && k < last_ob) ? sy[k] : min(ey, sy[k]);
-                d[k] = min(v[k], min(px + p[k], py - p[k]));
-            }
-        }
         // lower the map where this line improved, then bump the versions of
         // this line and of every crossing line that changed
         bool mine = false;
@@ -322,9 +290,11 @@ __device__ void run_block(const PropArgs& a, const Map& map, const Shared& sh, i
     const bool rows = dirk < 2;
     const int dir = (dirk & 1) ? -1 : +1;
     const int nlines = rows ? sh.hs : a.W;
-    // phases of one direction start evenly spaced over the lines
+    // the warps of one direction share its lines: each sweeps an equal,
+    // contiguous part of them every round
     const int off = (phase * nlines) / nph;
     const int start = dir > 0 ? off : (nlines - 1 - off);
+    const int seg = ((phase + 1) * nlines) / nph - off;
     int round = 0, nproc = 0;
     for (;;) {
         // clear the flag slot the next round will write (last used two rounds ago)
@@ -332,8 +302,8 @@ __device__ void run_block(const PropArgs& a, const Map& map, const Shared& sh, i
         for (int i = threadIdx.x; i < nr; i += blockDim.x) sh.chR[nx * nr + i] = 0;
         for (int i = threadIdx.x; i < nc; i += blockDim.x) sh.chC[nx * nc + i] = 0;
         bool ch;
-        if (rows) ch = sweep<CONN, KIND, VPL, true, EX, Map>(a, map, sh, dir, start, lane, round, nproc);
-        else ch = sweep<CONN, KIND, VPL, false, EX, Map>(a, map, sh, dir, start, lane, round, nproc);
+        if (rows) ch = sweep<CONN, KIND, VPL, true, EX, Map>(a, map, sh, dir, start, lane, round, nproc, seg);
+        else ch = sweep<CONN, KIND, VPL, false, EX, Map>(a, map, sh, dir, start, lane, round, nproc, seg);
         ch = __any_sync(FULL, ch);
         if (lane == 0 && ch) s_flag[round & 1] = 1;
         bool any;
@@ -365,13 +335,15 @@ __device__ __forceinline__ int finish(const PropArgs& a, int v) {
     return (a.convert && v >= PINF) ? (int)UNREACH : v;
 }
 
+// Seeds start at 0. On a mask, an obstacle pixel is never a seed: a source
+// on an obstacle reaches nothing (its own entry is set to 0 at the end).
 __device__ __forceinline__ bool is_seed(const PropArgs& a, int src, int p) {
-    return a.seed_flags ? a.seed_flags[p] != 0 : p == src;
+    const bool s = a.seed_flags ? a.seed_flags[p] != 0 : p == src;
+    return s && (!a.kind_mask || a.f[p] != 0);
 }
 
 __host__ __device__ inline size_t shared_state_bytes(int hs, int W) {
-    return (((3 * (size_t)(hs + W) + 2 * (size_t)hs * W) + 15) & ~(size_t)15) +
-           (size_t)(hs + W) * 32 * sizeof(int);
+    return ((3 * (size_t)(hs + W) + 2 * (size_t)hs * W) + 15) & ~(size_t)15;
 }
 
 // Lays out the non-map shared state of the strip [r0, r0 + hs) after `base`
@@ -395,31 +367,6 @@ __device__ Shared setup_shared(const PropArgs& a, char* base, int r0, int hs) {
     for (int i = threadIdx.x; i < 3 * (hs + a.W); i += blockDim.x) bp[i] = 0;
     sh.fR = fR;
     sh.fC = fC;
-    // lane bases of the line prefixes (grey): one warp per line
-    int* Pb = reinterpret_cast<int*>(bp + ((3 * (hs + a.W) + 2 * hs * a.W + 15) & ~15));
-    sh.Pb = Pb;
-    if (KIND == 0) {
-        const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-        for (int l = threadIdx.x >> 5; l < hs + a.W; l += nw) {
-            const bool rows = l < hs;
-            const int line = rows ? l : l - hs, len = rows ? a.W : hs;
-            int t = 0;
-            for (int k = 0; k < VPL; ++k) {
-                const int c = VPL * lane + k;
-                if (c + 1 < len) {
-                    const int e0 = rows ? (r0 + line) * a.W + c : (r0 + c) * a.W + line;
-                    const int e1 = rows ? e0 + 1 : e0 + a.W;
-                    t += a.f[e0] + a.f[e1] + 1;
-                }
-            }
-            int incl = t;
-            for (int off = 1; off < 32; off <<= 1) {
-                const int u = __shfl_up_sync(FULL, incl, off);
-                if (lane >= off) incl += u;
-            }
-            Pb[l * 32 + lane] = incl - t;
-        }
-    }
     return sh;
 }
 

@@ -151,11 +151,15 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
         for (int shift = ((top - 1) / 8) * 8; shift >= 0; shift -= 8) {
             if (tid < 256) hist[tid] = 0;
             __syncthreads();
-            for (int p = tid; p < a.N; p += SEL_THREADS) {
-                const unsigned long long k = key(p);
-                if (k == ~0ull) continue;
-                if ((k >> (shift + 8)) != (prefix >> (shift + 8))) continue;
-                atomicAdd(&hist[(k >> shift) & 255], 1u);
+            // keys sharing a digit within a warp add to its bin once (most
+            // keys share the top digits, which would serialise the atomics)
+            for (int p0 = 0; p0 < a.N; p0 += SEL_THREADS) {
+                const int p = p0 + tid;
+                const unsigned long long k = p < a.N ? key(p) : ~0ull;
+                const bool in = k != ~0ull && (k >> (shift + 8)) == (prefix >> (shift + 8));
+                const unsigned dig = in ? (unsigned)((k >> shift) & 255) : 256u;
+                const unsigned peers = __match_any_sync(FULL, dig);
+                if (in && (tid & 31) == __ffs(peers) - 1) atomicAdd(&hist[dig], (unsigned)__popc(peers));
             }
             __syncthreads();
             if (tid < 32) {

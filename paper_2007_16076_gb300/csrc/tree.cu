@@ -28,26 +28,43 @@ namespace gapsp {
 
 namespace {
 
-__device__ __forceinline__ int edge_w(const TreeArgs& a, int p, int q) {
-    return a.kind == 0 ? (int)a.f[p] + (int)a.f[q] + 1 : 2;
-}
-
-// Canonical parent of b in the tree of s (-1 for the root and unreached).
-__device__ __forceinline__ int canonical_parent(const TreeArgs& a, const uint32_t* drow, int s, int b) {
+// Canonical parent of b in the tree of s (-1 for the root and unreached):
+// the first neighbour q in increasing index with d(s,q) + w(q,b) = d(s,b).
+// fs: the grey levels (grey) or free flags (mask), in shared or global memory.
+__device__ __forceinline__ int canonical_parent(const TreeArgs& a, const uint32_t* drow, const uint8_t* fs, int s,
+                                                int b) {
     const uint32_t db = drow[b];
     if (b == s || db == UNREACH) return -1;
-    const int r = b / a.W, c = b - r * a.W;
-    // neighbours in increasing linear index
+    const int W = a.W;
+    const int r = b / W, c = b - r * W;
+    const uint32_t fb = a.kind == 0 ? (uint32_t)fs[b] + 1u : 2u;  // w(q,b) = f(q) + fb, or 2
+    auto tight = [&](int q) {
+        if (a.kind == 1 && !fs[q]) return false;
+        const uint32_t dq = drow[q];
+        return dq != UNREACH && dq + (a.kind == 0 ? (uint32_t)fs[q] + fb : 2u) == db;
+    };
+    if (r > 0 && r + 1 < a.H && c > 0 && c + 1 < W) {
+        // interior pixel: no bounds tests
+        if (a.conn == 8) {
+            const int off[8] = {-W - 1, -W, -W + 1, -1, 1, W - 1, W, W + 1};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (tight(b + off[i])) return b + off[i];
+        } else {
+            const int off[4] = {-W, -1, 1, W};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (tight(b + off[i])) return b + off[i];
+        }
+        return -1;
+    }
     for (int dr = -1; dr <= 1; ++dr)
         for (int dc = -1; dc <= 1; ++dc) {
             if (!dr && !dc) continue;
             if (a.conn == 4 && dr && dc) continue;
             const int rr = r + dr, cc = c + dc;
-            if (rr < 0 || rr >= a.H || cc < 0 || cc >= a.W) continue;
-            const int q = rr * a.W + cc;
-            if (a.kind == 1 && !a.f[q]) continue;
-            const uint32_t dq = drow[q];
-            if (dq != UNREACH && dq + (uint32_t)edge_w(a, q, b) == db) return q;
+            if (rr < 0 || rr >= a.H || cc < 0 || cc >= W) continue;
+            if (tight(rr * W + cc)) return rr * W + cc;
         }
     return -1;
 }
@@ -55,8 +72,10 @@ __device__ __forceinline__ int canonical_parent(const TreeArgs& a, const uint32_
 // The tree of one selected source, one block per source:
 //  1. the canonical parent of every vertex;
 //  2. seg[j][v]: x = bits of v and of its ancestors up to the first one
-//     outside v's 8x8 tile; y = that first outside ancestor + 1 (0 past the
-//     root) in the low 32 bits and its tile in the high 32 bits;
+//     outside v's 8x8 tile, the segment's exit; y = exit + 1 (bits 0-16, 0
+//     past the root), the exit's tile (bits 17-26), and the same for the exit
+//     of the exit's segment (bits 27-43 and 44-53), so that a walk can fetch
+//     two segments at once;
 //  3. the distance operations of the tree: the sum over reached b != s of
 //     depth(b), the number of proper ancestors of b. With acc(v) = number of
 //     vertices from v up to the root, depth(b) = acc(parent(b)); acc is
@@ -73,20 +92,24 @@ __global__ void __launch_bounds__(1024) k_tree(TreeArgs a) {
     const uint32_t* drow = a.D + (size_t)s * N;
     int32_t* par = a.parent + (size_t)j * N;
     ulonglong2* seg = a.seg + (size_t)j * N;
-    // SMALL: the distance row is staged in shared memory (it shares the space
-    // of the jumping arrays, used only later); spar = parent + 1, 0 for the
-    // root, 0xFFFF for unreached vertices
+    // SMALL: the distance row and the image are staged in shared memory (the
+    // row shares the space of the jumping arrays, used only later); spar =
+    // parent + 1, 0 for the root, 0xFFFF for unreached vertices
     uint16_t* spar = sdep + 4 * N;
     if (SMALL) {
         uint32_t* srow = reinterpret_cast<uint32_t*>(sdep);
-        for (int v = threadIdx.x; v < N; v += blockDim.x) srow[v] = __ldcg(drow + v);
+        uint8_t* sf = reinterpret_cast<uint8_t*>(sdep + 5 * N);
+        for (int v = threadIdx.x; v < N; v += blockDim.x) {
+            srow[v] = __ldcg(drow + v);
+            sf[v] = a.f[v];
+        }
         __syncthreads();
         for (int b = threadIdx.x; b < N; b += blockDim.x) {
-            const int pb = canonical_parent(a, srow, s, b);
+            const int pb = canonical_parent(a, srow, sf, s, b);
             spar[b] = srow[b] == UNREACH ? (uint16_t)0xFFFF : (uint16_t)(pb + 1);
         }
     } else {
-        for (int b = threadIdx.x; b < N; b += blockDim.x) par[b] = canonical_parent(a, drow, s, b);
+        for (int b = threadIdx.x; b < N; b += blockDim.x) par[b] = canonical_parent(a, drow, a.f, s, b);
     }
     __syncthreads();
     for (int v = threadIdx.x; v < N; v += blockDim.x) {
@@ -102,8 +125,7 @@ __global__ void __launch_bounds__(1024) k_tree(TreeArgs a) {
             gx = x >= 0 ? __ldg(a.pgeo + x) : 0;
         }
         const bool reached = SMALL ? sv != 0xFFFF : drow[v] != UNREACH;
-        const unsigned long long y = x >= 0 ? ((unsigned long long)(gx >> 8) << 32) | (unsigned long long)(x + 1) : 0ull;
-        seg[v] = make_ulonglong2(m, y);
+        reinterpret_cast<unsigned long long*>(seg + v)[0] = m;
         if (SMALL) {
             sdep[v] = reached ? (uint16_t)__popcll(m) : 0;                 // acc, buffer 0
             sdep[2 * N + v] = reached ? (uint16_t)(x + 1) : 0;            // jmp + 1, buffer 0
@@ -114,6 +136,17 @@ __global__ void __launch_bounds__(1024) k_tree(TreeArgs a) {
     }
     if (threadIdx.x == 0) { s_any[0] = 0; s_any[1] = 0; }
     __syncthreads();
+    // the segment exits one and two steps ahead, with their tiles (before the
+    // jumping passes overwrite the exit arrays)
+    for (int v = threadIdx.x; v < N; v += blockDim.x) {
+        const int e1 = SMALL ? (int)sdep[2 * N + v] - 1 : __ldcg(a.jmp + (size_t)j * N + v);
+        int e2 = -1;
+        if (e1 >= 0) e2 = SMALL ? (int)sdep[2 * N + e1] - 1 : __ldcg(a.jmp + (size_t)j * N + e1);
+        unsigned long long y = 0;
+        if (e1 >= 0) y = (unsigned long long)(e1 + 1) | ((unsigned long long)(__ldg(a.pgeo + e1) >> 8) << 17);
+        if (e2 >= 0) y |= ((unsigned long long)(e2 + 1) << 27) | ((unsigned long long)(__ldg(a.pgeo + e2) >> 8) << 44);
+        reinterpret_cast<unsigned long long*>(seg + v)[1] = y;
+    }
     // pointer jumping: acc(v) += acc(jmp(v)); jmp(v) = jmp(jmp(v))
     int cur = 0;
     for (int pass = 0; pass < 32; ++pass) {
@@ -227,61 +260,69 @@ __global__ void k_fill(TreeArgs a) {
         uint8_t* mychg = chg + (size_t)bl * words;
         const int tb = s_tile[bl];
         const unsigned long long bbit = 1ull << s_bit[bl];
+        bool gained = false;
+        // one tile segment: the bits of m not yet in row b are new pairs
+        auto take = [&](int t, unsigned long long m) {
+            if (!m) return;
+            // two 32-bit ORs: a 64-bit OR on shared memory is much slower
+            unsigned* w32 = reinterpret_cast<unsigned*>(myrow + t);
+            const unsigned lo = (unsigned)m, hi = (unsigned)(m >> 32);
+            const unsigned olo = lo ? atomicOr(w32, lo) : 0xFFFFFFFFu;
+            const unsigned ohi = hi ? atomicOr(w32 + 1, hi) : 0xFFFFFFFFu;
+            unsigned long long nb = m & ~(((unsigned long long)ohi << 32) | olo);
+            if (!nb) return;
+            gained = true;
+            mychg[t] = 1;
+            const int base = __ldg(a.tbase + t);
+            // up to 8 new pairs at a time: the distance loads first, so that
+            // they are in flight together, then the stores. The rows d(s, .)
+            // read here only ever receive the same exact values again, so
+            // read-only loads are safe.
+            while (nb) {
+                int ap[8];
+                uint32_t dv[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    ap[k] = -1;
+                    if (nb) {
+                        const int bit = __ffsll((long long)nb) - 1;
+                        nb &= nb - 1;
+                        ap[k] = base + (bit >> 3) * a.W + (bit & 7);
+                        dv[k] = __ldg(drow + ap[k]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    if (ap[k] < 0) continue;
+                    const uint32_t val = db - dv[k];
+                    atomicOr(a.marks + (size_t)ap[k] * words + tb, bbit);
+                    a.dirty[ap[k]] = 1;
+                    // streaming stores: D is far larger than L2, keep the
+                    // trees and marks resident instead
+                    __stcs(a.Dw + (size_t)ap[k] * a.N + b, val);
+                    __stcs(a.Dw + (size_t)b * a.N + ap[k], val);
+                }
+            }
+        };
         ulonglong2 g = __ldg(seg + b);
         unsigned long long m = g.x & ~bbit;  // b's ancestors inside b's tile
         int t = tb;
-        bool gained = false;
         for (int guard = 0; guard <= a.N; ++guard) {
+            // the next two segments are fetched together, before this one is
+            // worked on
             const unsigned long long y = g.y;
-            const int ex = (int)(uint32_t)y - 1;
-            // fetch the next segment record before working on this one
-            ulonglong2 gn = make_ulonglong2(0ull, 0ull);
-            if (ex >= 0) gn = __ldg(seg + ex);
-            if (m) {
-                // two 32-bit ORs: a 64-bit OR on shared memory is much slower
-                unsigned* w32 = reinterpret_cast<unsigned*>(myrow + t);
-                const unsigned lo = (unsigned)m, hi = (unsigned)(m >> 32);
-                const unsigned olo = lo ? atomicOr(w32, lo) : 0xFFFFFFFFu;
-                const unsigned ohi = hi ? atomicOr(w32 + 1, hi) : 0xFFFFFFFFu;
-                unsigned long long nb = m & ~(((unsigned long long)ohi << 32) | olo);
-                if (nb) {
-                    gained = true;
-                    mychg[t] = 1;
-                    const int base = __ldg(a.tbase + t);
-                    // up to 8 new pairs at a time: the distance loads first,
-                    // so that they are in flight together, then the stores.
-                    // The rows d(s, .) read here only ever receive the same
-                    // exact values again, so read-only loads are safe.
-                    while (nb) {
-                        int ap[8];
-                        uint32_t dv[8];
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            ap[k] = -1;
-                            if (nb) {
-                                const int bit = __ffsll((long long)nb) - 1;
-                                nb &= nb - 1;
-                                ap[k] = base + (bit >> 3) * a.W + (bit & 7);
-                                dv[k] = __ldg(drow + ap[k]);
-                            }
-                        }
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            if (ap[k] < 0) continue;
-                            const uint32_t val = db - dv[k];
-                            atomicOr(a.marks + (size_t)ap[k] * words + tb, bbit);
-                            a.dirty[ap[k]] = 1;
-                            // streaming stores: D is far larger than L2, keep
-                            // the trees and marks resident instead
-                            __stcs(a.Dw + (size_t)ap[k] * a.N + b, val);
-                            __stcs(a.Dw + (size_t)b * a.N + ap[k], val);
-                        }
-                    }
-                }
-            }
-            if (ex < 0) break;
-            t = (int)(y >> 32);
-            g = gn;
+            const int e1 = (int)(y & 0x1FFFFu) - 1, t1 = (int)((y >> 17) & 0x3FFu);
+            const int e2 = (int)((y >> 27) & 0x1FFFFu) - 1, t2 = (int)((y >> 44) & 0x3FFu);
+            unsigned long long m1 = 0;
+            ulonglong2 g2 = make_ulonglong2(0ull, 0ull);
+            if (e1 >= 0) m1 = __ldg(reinterpret_cast<const unsigned long long*>(seg + e1));
+            if (e2 >= 0) g2 = __ldg(seg + e2);
+            take(t, m);
+            if (e1 < 0) break;
+            take(t1, m1);
+            if (e2 < 0) break;
+            g = g2;
+            t = t2;
             m = g.x;
         }
         if (gained) atomicOr(&s_gain, 1u << bl);
@@ -332,10 +373,11 @@ cudaError_t launch_tree(const TreeArgs& a, int B, cudaStream_t st) {
     if (a.N <= 16384) {
         static bool attr = false;
         if (!attr) {
-            cudaFuncSetAttribute(k_tree<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+            cudaFuncSetAttribute(k_tree<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 11);
             attr = true;
         }
-        k_tree<true><<<B, 1024, (size_t)a.N * 5 * sizeof(uint16_t), st>>>(a);
+        // five 16-bit arrays and the image
+        k_tree<true><<<B, 1024, (size_t)a.N * 11, st>>>(a);
     } else {
         k_tree<false><<<B, 1024, 0, st>>>(a);
     }
