@@ -200,11 +200,15 @@ def run_ours(a):
     D = torch.empty((N, N), dtype=torch.int32, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
 
+    # the clock sampler starts before the warm-up: its start-up (NVML
+    # initialisation) stalls the device for a while, which must not fall
+    # into the timed steps; it keeps sampling through them
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(1.0)
     for _ in range(max(3, a.warmup)):
         _, st = im.all_pairs("minfill", out=D)
 
-    clocks = Clocks(local)
-    clocks.start()
     l0 = im.kernel_launches
     barrier()
     ev_a = torch.cuda.Event(enable_timing=True)

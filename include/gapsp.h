@@ -200,7 +200,8 @@ uint64_t gapsp_kernel_launches(const gapsp_handle *h);
  * Kernel ids: 0 selection (c), 1 propagation (a), 2 tree: parents,
  * segments and depths (a'), 3 lookahead propagations (on the second stream,
  * overlapping the others), 4 tree fill (b), 5 init, 6 extrema pre-pass
- * helpers, 7 unused, 8 fill-count update.
+ * helpers, 7 depth sums of the trees (N <= 16384, on a third stream), 8
+ * fill-count update.
  * ms and launches: caller-owned arrays of GAPSP_NUM_KERNELS entries.
  */
 #define GAPSP_NUM_KERNELS 9

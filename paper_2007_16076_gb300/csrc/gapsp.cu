@@ -62,6 +62,9 @@ struct gapsp_handle {
     uint8_t* row_done = nullptr;  // [N]: row already written by a propagation
     int32_t* cand = nullptr;      // [2][1024]: lookahead candidates, by round parity
     int* ncand = nullptr;         // [2]
+    uint16_t* dep_exit = nullptr; // [2][B][N] (N <= 16384): trees handed to k_depths, by round parity
+    uint16_t* dep_size = nullptr; // [2][B][N]
+    int* dep_count = nullptr;     // [2]
     unsigned long long* stats = nullptr;
     unsigned long long* round_new = nullptr;
     unsigned long long* last_new = nullptr;
@@ -70,7 +73,7 @@ struct gapsp_handle {
     uint32_t* gmap = nullptr;
     unsigned long long* best = nullptr;
     uint8_t* cen = nullptr;
-    int* h_done = nullptr;  // pinned
+    int* h_done = nullptr;  // pinned, [2]: "done" flag after an even / odd chunk of rounds
     // scratch for host-side arrays
     uint32_t* Dtmp = nullptr;
     size_t Dtmp_bytes = 0;
@@ -177,7 +180,8 @@ size_t fill_state_bytes(const gapsp_handle* h) {
     // rank, grank, round_new, sel_log, emap, gmap, best, cen, row_done per
     // point; the lookahead candidate buffers
     return N * h->words * 8 + B * N * (4 + 16 + 8 + 8) +
-           N * (4 + 4 + 1 + 4 + 4 + 4 + 8 + 4 + 4 + 4 + 8 + 1 + 1) + 2 * 1024 * 4 + 4096;
+           N * (4 + 4 + 1 + 4 + 4 + 4 + 8 + 4 + 4 + 4 + 8 + 1 + 1) + 2 * 1024 * 4 + 4096 +
+           (N <= 16384 ? 8 * B * N : 0);  // trees handed to k_depths
 }
 
 gapsp_status ensure_fill_state(gapsp_handle* h) {
@@ -201,6 +205,11 @@ gapsp_status ensure_fill_state(gapsp_handle* h) {
     CK(dalloc(&h->row_done, N));
     CK(dalloc(&h->cand, 2 * 1024));
     CK(dalloc(&h->ncand, 2));
+    if (N <= 16384) {
+        CK(dalloc(&h->dep_exit, 2 * B * N));
+        CK(dalloc(&h->dep_size, 2 * B * N));
+        CK(dalloc(&h->dep_count, 2));
+    }
     CK(dalloc(&h->stats, S_SLOTS));
     CK(dalloc(&h->round_new, N + 1));
     CK(dalloc(&h->last_new, 1));
@@ -209,7 +218,7 @@ gapsp_status ensure_fill_state(gapsp_handle* h) {
     CK(dalloc(&h->gmap, N));
     CK(dalloc(&h->best, N));
     CK(dalloc(&h->cen, N));
-    CK(cudaMallocHost((void**)&h->h_done, sizeof(int)));
+    CK(cudaMallocHost((void**)&h->h_done, 2 * sizeof(int)));
     h->fill_ready = true;
     return GAPSP_OK;
 }
@@ -220,6 +229,7 @@ void free_all(gapsp_handle* h) {
     dfree(h->cnt); dfree(h->cnt_base); dfree(h->dirty); dfree(h->marks); dfree(h->parent); dfree(h->seg); dfree(h->jmp); dfree(h->acc);
     dfree(h->sel); dfree(h->nsel); dfree(h->cursor); dfree(h->done); dfree(h->seq); dfree(h->rank); dfree(h->grank);
     dfree(h->row_done); dfree(h->cand); dfree(h->ncand);
+    dfree(h->dep_exit); dfree(h->dep_size); dfree(h->dep_count);
     dfree(h->stats); dfree(h->round_new); dfree(h->last_new); dfree(h->sel_log);
     dfree(h->emap); dfree(h->gmap); dfree(h->best); dfree(h->cen);
     dfree(h->Dtmp); dfree(h->src_dev); dfree(h->out_tmp);
@@ -234,7 +244,8 @@ void free_all(gapsp_handle* h) {
     h->ev0 = h->ev1 = nullptr;
 }
 
-enum { K_SELECT = 0, K_PROP = 1, K_TREE = 2, K_AHEAD = 3, K_FILL = 4, K_INIT = 5, K_PRE = 6, K_RECOUNT = 8 };
+enum { K_SELECT = 0, K_PROP = 1, K_TREE = 2, K_AHEAD = 3, K_FILL = 4, K_INIT = 5, K_PRE = 6, K_DEPTH = 7,
+       K_RECOUNT = 8 };
 
 cudaEvent_t pool_get(gapsp_handle* h) {
     if (!h->pool.empty()) {
@@ -472,11 +483,30 @@ struct FillRun {
     cudaStream_t side = nullptr;
     cudaEvent_t e_sel = nullptr;
     cudaEvent_t e_ahead[2] = {nullptr, nullptr};  // lookahead launch of an even / odd round
+    // chunks of rounds: the host keeps one chunk queued beyond the one whose
+    // "done" flag it waits for, so that the device never waits for the host
+    cudaEvent_t chunk_ev[2] = {nullptr, nullptr};
+    int chunks = 0, polled = 0;
+    // depth sums (N <= 16384) on a third, low-priority stream: a round's
+    // trees are handed over in a buffer of the round's parity, which the
+    // tree launch two rounds later waits for
+    cudaStream_t stat = nullptr;
+    cudaEvent_t e_tree[2] = {nullptr, nullptr}, e_depth[2] = {nullptr, nullptr};
+    FillRun() = default;
+    FillRun(const FillRun&) = delete;
+    FillRun& operator=(const FillRun&) = delete;
     ~FillRun() {
         if (e_sel) cudaEventDestroy(e_sel);
         for (cudaEvent_t e : e_ahead)
             if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : chunk_ev)
+            if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : e_tree)
+            if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : e_depth)
+            if (e) cudaEventDestroy(e);
         if (side) cudaStreamDestroy(side);
+        if (stat) cudaStreamDestroy(stat);
     }
 };
 
@@ -632,8 +662,24 @@ gapsp_status fill_begin(FillRun& r) {
     }
     r.rounds = 0;
     r.finished = false;
+    r.chunks = r.polled = 0;
+    CK(cudaEventCreateWithFlags(&r.chunk_ev[0], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&r.chunk_ev[1], cudaEventDisableTiming));
+    if (h->dep_exit) {
+        int least = 0, greatest = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        CK(cudaStreamCreateWithPriority(&r.stat, cudaStreamNonBlocking, least));
+        for (int i = 0; i < 2; ++i) {
+            CK(cudaEventCreateWithFlags(&r.e_tree[i], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&r.e_depth[i], cudaEventDisableTiming));
+        }
+    }
     return GAPSP_OK;
 }
+
+// Rounds per chunk: small enough that the rounds queued after the fill is
+// done cost little, large enough that the host stays ahead of the device.
+constexpr int kChunk = 8;
 
 // Enqueues `chunk` rounds and an asynchronous copy of the "done" flag.
 gapsp_status fill_enqueue(FillRun& r, int chunk) {
@@ -674,9 +720,27 @@ gapsp_status fill_enqueue(FillRun& r, int chunk) {
             ProfScope ps(h, K_PROP, s);
             CK(launch_propagate(r.pa, h->conn, h->kind, h->B, 1, s));
         }
+        if (r.stat) {
+            // hand the trees to k_depths through the buffer of this parity,
+            // once the launch that read it two rounds ago is done
+            r.ta.dep_exit = h->dep_exit + (size_t)par * h->B * h->N;
+            r.ta.dep_size = h->dep_size + (size_t)par * h->B * h->N;
+            r.ta.dep_count = h->dep_count + par;
+            CK(cudaStreamWaitEvent(s, r.e_depth[par], 0));
+        }
         {
             ProfScope ps(h, K_TREE, s);
             CK(launch_tree(r.ta, h->B, s));
+        }
+        if (r.stat) {
+            CK(cudaEventRecord(r.e_tree[par], s));
+            CK(cudaStreamWaitEvent(r.stat, r.e_tree[par], 0));
+            {
+                ProfScope ps(h, K_DEPTH, r.stat);
+                CK(launch_depths(r.ta, h->B, r.stat));
+            }
+            CK(cudaEventRecord(r.e_depth[par], r.stat));
+            h->launches += 1;
         }
         {
             ProfScope ps(h, K_FILL, s);
@@ -689,15 +753,21 @@ gapsp_status fill_enqueue(FillRun& r, int chunk) {
         h->launches += 5;
     }
     r.rounds += chunk;
-    CK(cudaMemcpyAsync(h->h_done, h->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+    const int par = r.chunks & 1;
+    CK(cudaMemcpyAsync(h->h_done + par, h->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(r.chunk_ev[par], s));
+    ++r.chunks;
     return GAPSP_OK;
 }
 
-// Waits for the enqueued rounds and reads the "done" flag.
+// Waits for the oldest chunk not yet waited for and reads its "done" flag.
+// Rounds enqueued after the fill is done return at once.
 gapsp_status fill_poll(FillRun& r) {
-    CK(cudaStreamSynchronize(r.s));
-    r.finished = *r.h->h_done != 0;
-    if (!r.finished && r.rounds > r.h->N + 2) return GAPSP_E_TIMEOUT;
+    const int par = r.polled & 1;
+    CK(cudaEventSynchronize(r.chunk_ev[par]));
+    ++r.polled;
+    r.finished = r.h->h_done[par] != 0;
+    if (!r.finished && r.rounds > r.h->N + 2 + 64) return GAPSP_E_TIMEOUT;
     return GAPSP_OK;
 }
 
@@ -708,6 +778,10 @@ gapsp_status fill_finish(FillRun& r, gapsp_stats* st) {
     if (r.K > 0) {
         CK(cudaStreamWaitEvent(s, r.e_ahead[0], 0));
         CK(cudaStreamWaitEvent(s, r.e_ahead[1], 0));
+    }
+    if (r.stat) {
+        CK(cudaStreamWaitEvent(s, r.e_depth[0], 0));
+        CK(cudaStreamWaitEvent(s, r.e_depth[1], 0));
     }
     CK(cudaEventRecord(h->ev1, s));
     unsigned long long hs[S_SLOTS];
@@ -771,8 +845,9 @@ gapsp_status gapsp_all_pairs(gapsp_handle* h, gapsp_order order, uint32_t* D, ga
     r.s = h->st;
     gapsp_status gs = fill_begin(r);
     if (gs != GAPSP_OK) return gs;
+    if ((gs = fill_enqueue(r, kChunk)) != GAPSP_OK) return gs;
     while (!r.finished) {
-        if ((gs = fill_enqueue(r, 16)) != GAPSP_OK) return gs;
+        if ((gs = fill_enqueue(r, kChunk)) != GAPSP_OK) return gs;
         if ((gs = fill_poll(r)) != GAPSP_OK) return gs;
     }
     return fill_finish(r, st);
@@ -807,10 +882,11 @@ gapsp_status gapsp_all_pairs_batch(gapsp_handle* const* hs, int n, gapsp_order o
         runs[i].s = ws[i];
     }
     for (int i = 0; i < n && result == GAPSP_OK; ++i) result = fill_begin(runs[i]);
+    for (int i = 0; i < n && result == GAPSP_OK; ++i) result = fill_enqueue(runs[i], kChunk);
     bool all = false;
     while (result == GAPSP_OK && !all) {
         for (int i = 0; i < n && result == GAPSP_OK; ++i)
-            if (!runs[i].finished) result = fill_enqueue(runs[i], 16);
+            if (!runs[i].finished) result = fill_enqueue(runs[i], kChunk);
         all = true;
         for (int i = 0; i < n && result == GAPSP_OK; ++i)
             if (!runs[i].finished) {

@@ -66,8 +66,15 @@ struct TreeArgs {
     uint32_t* Dw;               // writable array for new pairs
     unsigned long long* stats;  // StatSlot counters
     int rows_per_block;
+    // N <= 16384: the depth sums are left to k_depths; the tree hands it the
+    // segment exits (+1) and segment sizes of each tree, and the tree count
+    uint16_t* dep_exit;         // [B][N] or NULL (then the tree sums depths itself)
+    uint16_t* dep_size;         // [B][N]
+    int* dep_count;
 };
 cudaError_t launch_tree(const TreeArgs& a, int B, cudaStream_t st);
+// Distance operations of the trees handed over by a tree launch (N <= 16384).
+cudaError_t launch_depths(const TreeArgs& a, int B, cudaStream_t st);
 cudaError_t launch_fill(const TreeArgs& a, int B, cudaStream_t st);
 cudaError_t launch_recount(const TreeArgs& a, cudaStream_t st);
 

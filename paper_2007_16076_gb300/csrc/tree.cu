@@ -87,6 +87,8 @@ __global__ void __launch_bounds__(1024) k_tree(TreeArgs a) {
     extern __shared__ uint16_t sdep[];
     __shared__ int s_any[2];
     const int j = blockIdx.x, B = gridDim.x;
+    // the number of trees handed to k_depths (also when there are none)
+    if (SMALL && a.dep_exit && j == 0 && threadIdx.x == 0) *a.dep_count = *a.nsel;
     if (j >= *a.nsel) return;
     const int N = a.N, s = a.sel[j];
     const uint32_t* drow = a.D + (size_t)s * N;
@@ -147,6 +149,16 @@ __global__ void __launch_bounds__(1024) k_tree(TreeArgs a) {
         if (e2 >= 0) y |= ((unsigned long long)(e2 + 1) << 27) | ((unsigned long long)(__ldg(a.pgeo + e2) >> 8) << 44);
         reinterpret_cast<unsigned long long*>(seg + v)[1] = y;
     }
+    if (SMALL && a.dep_exit) {
+        // the depth sums run later, off the round's critical path
+        uint16_t* ex = a.dep_exit + (size_t)j * N;
+        uint16_t* sz = a.dep_size + (size_t)j * N;
+        for (int v = threadIdx.x; v < N; v += blockDim.x) {
+            ex[v] = sdep[2 * N + v];
+            sz[v] = sdep[v];
+        }
+        return;
+    }
     // pointer jumping: acc(v) += acc(jmp(v)); jmp(v) = jmp(jmp(v))
     int cur = 0;
     for (int pass = 0; pass < 32; ++pass) {
@@ -195,6 +207,55 @@ __global__ void __launch_bounds__(1024) k_tree(TreeArgs a) {
         if (pb >= 0)
             ops += SMALL ? (unsigned long long)sdep[cur * N + pb]
                          : (unsigned long long)__ldcg(a.acc + (size_t)(cur * B + j) * N + pb);
+    }
+    for (int o = 16; o > 0; o >>= 1) ops += __shfl_down_sync(FULL, ops, o);
+    if ((threadIdx.x & 31) == 0 && ops) atomicAdd(a.stats + S_OPS, ops);
+}
+
+// Distance operations of one tree from its segment exits and sizes (N <=
+// 16384): acc(v) = number of vertices from v up to the root, summed along
+// the chain of segment exits by pointer jumping; depth(b) = acc(b) - 1.
+__global__ void __launch_bounds__(1024) k_depths(TreeArgs a) {
+    extern __shared__ uint16_t sd[];  // acc [2][N], exit + 1 [2][N]
+    __shared__ int s_any[2];
+    const int j = blockIdx.x;
+    if (j >= *a.dep_count) return;
+    const int N = a.N;
+    const uint16_t* ex = a.dep_exit + (size_t)j * N;
+    const uint16_t* sz = a.dep_size + (size_t)j * N;
+    for (int v = threadIdx.x; v < N; v += blockDim.x) {
+        sd[v] = sz[v];
+        sd[2 * N + v] = ex[v];
+    }
+    if (threadIdx.x == 0) { s_any[0] = 0; s_any[1] = 0; }
+    __syncthreads();
+    int cur = 0;
+    for (int pass = 0; pass < 32; ++pass) {
+        const int nx = cur ^ 1;
+        int any = 0;
+        for (int v = threadIdx.x; v < N; v += blockDim.x) {
+            const int j1 = (int)sd[2 * N + cur * N + v] - 1;
+            int c = sd[cur * N + v], j2 = -1;
+            if (j1 >= 0) {
+                j2 = (int)sd[2 * N + cur * N + j1] - 1;
+                c += sd[cur * N + j1];
+            }
+            any |= j2 >= 0;
+            sd[nx * N + v] = (uint16_t)c;
+            sd[2 * N + nx * N + v] = (uint16_t)(j2 + 1);
+        }
+        if (any) s_any[pass & 1] = 1;
+        __syncthreads();
+        const bool more = s_any[pass & 1] != 0;
+        if (threadIdx.x == 0) s_any[(pass + 1) & 1] = 0;
+        cur = nx;
+        if (!more) break;
+        __syncthreads();
+    }
+    unsigned long long ops = 0;
+    for (int v = threadIdx.x; v < N; v += blockDim.x) {
+        const int c = sd[cur * N + v];
+        if (c > 1) ops += (unsigned long long)(c - 1);  // unreached vertices hold 0, the root 1
     }
     for (int o = 16; o > 0; o >>= 1) ops += __shfl_down_sync(FULL, ops, o);
     if ((threadIdx.x & 31) == 0 && ops) atomicAdd(a.stats + S_OPS, ops);
@@ -381,6 +442,16 @@ cudaError_t launch_tree(const TreeArgs& a, int B, cudaStream_t st) {
     } else {
         k_tree<false><<<B, 1024, 0, st>>>(a);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_depths(const TreeArgs& a, int B, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_depths, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 8);
+        attr = true;
+    }
+    k_depths<<<B, 1024, (size_t)a.N * 8, st>>>(a);
     return cudaGetLastError();
 }
 
