@@ -646,6 +646,7 @@ gapsp_status fill_begin(FillRun& r) {
     ta = TreeArgs{};
     ta.H = h->H; ta.W = h->W; ta.N = h->N; ta.conn = h->conn; ta.kind = h->kind;
     ta.tiles_w = h->tiles_w; ta.words = h->words;
+    ta.wdiv = h->W == 1 ? 0u : (unsigned)((0x100000000ull + (unsigned)h->W - 1) / (unsigned)h->W);
     ta.f = h->f; ta.D = Dd; ta.sel = h->sel; ta.nsel = h->nsel;
     ta.pgeo = h->pgeo; ta.tbase = h->tbase;
     ta.parent = h->parent; ta.seg = h->seg; ta.jmp = h->jmp; ta.acc = h->acc;

@@ -48,6 +48,7 @@ cudaError_t launch_image_prep(const ImagePrep& p, cudaStream_t st);
 
 struct TreeArgs {
     int H, W, N, conn, kind, tiles_w, words;
+    unsigned wdiv;              // ceil(2^32 / W) (0 when W = 1): row of p = umulhi(p, wdiv)
     const uint8_t* f;
     const uint32_t* D;          // the array; row sel[j] holds d(sel[j], .)
     const int32_t* sel;         // selected sources

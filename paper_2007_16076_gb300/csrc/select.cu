@@ -104,18 +104,83 @@ __device__ __forceinline__ unsigned long long mf_key(const SelectArgs& a, int p)
     return ((unsigned long long)c << 17) | (unsigned long long)r;
 }
 
+// Radix selection, 11 bits a pass from the top bit a key can have: the
+// need-th smallest (1-based) of the valid keys keyf(0 .. n-1) (~0 = not a
+// key). Every thread of the block calls it with the same arguments.
+constexpr int RB = 11, NBIN = 1 << RB;
+
+struct SelScratch {
+    unsigned hist[NBIN];
+    unsigned wsum[32];
+    unsigned long long prefix;
+    int need;
+};
+
+template <class KeyF>
+__device__ unsigned long long radix_select(KeyF keyf, int n, int need, int top, SelScratch& sc) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned long long prefix = 0;
+    if (tid == 0) { sc.need = need; sc.prefix = 0; }
+    for (int shift = ((top - 1) / RB) * RB; shift >= 0; shift -= RB) {
+        for (int i = tid; i < NBIN; i += SEL_THREADS) sc.hist[i] = 0;
+        __syncthreads();
+        // keys sharing a digit within a warp add to its bin once (most keys
+        // share the top digits, which would serialise the atomics)
+        for (int p0 = 0; p0 < n; p0 += SEL_THREADS) {
+            const int p = p0 + tid;
+            const unsigned long long k = p < n ? keyf(p) : ~0ull;
+            const bool in = k != ~0ull && (k >> (shift + RB)) == (prefix >> (shift + RB));
+            const unsigned dig = in ? (unsigned)((k >> shift) & (NBIN - 1)) : (unsigned)NBIN;
+            const unsigned peers = __match_any_sync(FULL, dig);
+            if (in && lane == __ffs(peers) - 1) atomicAdd(&sc.hist[dig], (unsigned)__popc(peers));
+        }
+        __syncthreads();
+        // block-wide scan of the bins, two per thread, to find the digit
+        // that holds the need-th key
+        const unsigned h0 = sc.hist[2 * tid], h1 = sc.hist[2 * tid + 1];
+        unsigned v = h0 + h1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(FULL, v, o);
+            if (lane >= o) v += t;
+        }
+        if (lane == 31) sc.wsum[warp] = v;
+        const int nd = sc.need;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned w = sc.wsum[lane];
+            unsigned x = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned t = __shfl_up_sync(FULL, x, o);
+                if (lane >= o) x += t;
+            }
+            sc.wsum[lane] = x - w;  // exclusive
+        }
+        __syncthreads();
+        const unsigned incl = v + sc.wsum[warp], excl = incl - h0 - h1;
+        if (excl < (unsigned)nd && (unsigned)nd <= incl) {
+            const bool first = excl + h0 >= (unsigned)nd;
+            sc.need = nd - (int)(first ? excl : excl + h0);
+            sc.prefix = prefix | ((unsigned long long)(2 * tid + (first ? 0 : 1)) << shift);
+        }
+        __syncthreads();
+        prefix = sc.prefix;
+    }
+    return prefix;
+}
+
 // Keys of the unfilled points are cached in shared memory when N <= 16384
 // (CACHED), and read from the counts otherwise.
 template <bool CACHED>
 __global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
     extern __shared__ unsigned long long skeys[];
-    __shared__ unsigned hist[256];
-    __shared__ unsigned long long s_prefix;
-    __shared__ int s_need, s_count, s_unfilled;
-    __shared__ unsigned long long s_keys[1024];
-    __shared__ int s_pix[1024];
-    __shared__ int s_wcount[32], s_ncand;
-    const int tid = threadIdx.x;
+    __shared__ SelScratch sc;
+    __shared__ int s_count, s_unfilled, s_nsel, s_ncand;
+    __shared__ unsigned long long s_keys[1024], s_selk[1024];
+    __shared__ int s_pix[1024], s_selp[1024];
+    __shared__ int s_wcount[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (*a.done) {
         if (tid == 0) {
             *a.nsel = 0;
@@ -123,7 +188,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
         }
         return;
     }
-    if (tid == 0) { s_unfilled = 0; s_count = 0; s_prefix = 0; }
+    if (tid == 0) { s_unfilled = 0; s_count = 0; s_nsel = 0; s_ncand = 0; }
     __syncthreads();
     int mine = 0;
     for (int p = tid; p < a.N; p += SEL_THREADS) {
@@ -132,7 +197,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
         mine += k != ~0ull;
     }
     for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(FULL, mine, o);
-    if ((tid & 31) == 0 && mine) atomicAdd(&s_unfilled, mine);
+    if (lane == 0 && mine) atomicAdd(&s_unfilled, mine);
     __syncthreads();
     auto key = [&](int p) -> unsigned long long { return CACHED ? skeys[p] : mf_key(a, p); };
     const int unfilled = s_unfilled;
@@ -140,59 +205,12 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
     // the selection, then the next KL points in key order, from which the
     // lookahead candidates are taken
     const int wantc = min(unfilled, a.B + (a.K > 0 ? a.KL : 0));
-    unsigned long long thr = ~0ull - 1;  // select keys <= thr
-    if (wantc > 0 && wantc < unfilled) {
-        // the want-th smallest key, 8 bits at a time from the top bit a key
-        // can have (17 bits per field below the top one)
-        int top = a.order == 3 ? 34 : 17;
-        for (int n = a.N - 1; n > 0; n >>= 1) ++top;
-        if (tid == 0) s_need = wantc;
-        unsigned long long prefix = 0;
-        for (int shift = ((top - 1) / 8) * 8; shift >= 0; shift -= 8) {
-            if (tid < 256) hist[tid] = 0;
-            __syncthreads();
-            // keys sharing a digit within a warp add to its bin once (most
-            // keys share the top digits, which would serialise the atomics)
-            for (int p0 = 0; p0 < a.N; p0 += SEL_THREADS) {
-                const int p = p0 + tid;
-                const unsigned long long k = p < a.N ? key(p) : ~0ull;
-                const bool in = k != ~0ull && (k >> (shift + 8)) == (prefix >> (shift + 8));
-                const unsigned dig = in ? (unsigned)((k >> shift) & 255) : 256u;
-                const unsigned peers = __match_any_sync(FULL, dig);
-                if (in && (tid & 31) == __ffs(peers) - 1) atomicAdd(&hist[dig], (unsigned)__popc(peers));
-            }
-            __syncthreads();
-            if (tid < 32) {
-                // warp 0 finds the digit holding the need-th key
-                const int need = s_need;
-                unsigned loc[8], sum = 0;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) { loc[i] = hist[tid * 8 + i]; sum += loc[i]; }
-                unsigned incl = sum;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const unsigned t = __shfl_up_sync(FULL, incl, o);
-                    if (tid >= o) incl += t;
-                }
-                const unsigned excl = incl - sum;
-                if (excl < (unsigned)need && (unsigned)need <= incl) {
-                    unsigned acc = excl;
-                    for (int i = 0; i < 8; ++i) {
-                        if (acc + loc[i] >= (unsigned)need) {
-                            s_need = need - (int)acc;
-                            s_prefix = prefix | ((unsigned long long)(tid * 8 + i) << shift);
-                            break;
-                        }
-                        acc += loc[i];
-                    }
-                }
-            }
-            __syncthreads();
-            prefix = s_prefix;
-        }
-        thr = prefix;
-    }
-    // gather the selected points (one shared atomic per warp)
+    // keys have 17 bits per field below the top one
+    int top = a.order == 3 ? 34 : 17;
+    for (int n = a.N - 1; n > 0; n >>= 1) ++top;
+    unsigned long long thr = ~0ull - 1;  // gather keys <= thr
+    if (wantc > 0 && wantc < unfilled) thr = radix_select(key, a.N, wantc, top, sc);
+    // gather (one shared atomic per warp)
     if (want > 0) {
         for (int p0 = 0; p0 < a.N; p0 += SEL_THREADS) {
             const int p = p0 + tid;
@@ -200,64 +218,67 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
             const bool take = k != ~0ull && k <= thr;
             const unsigned m = __ballot_sync(FULL, take);
             int base = 0;
-            if ((tid & 31) == 0 && m) base = atomicAdd(&s_count, __popc(m));
+            if (lane == 0 && m) base = atomicAdd(&s_count, __popc(m));
             base = __shfl_sync(FULL, base, 0);
             if (take) {
-                const int slot = base + __popc(m & ((1u << (tid & 31)) - 1u));
+                const int slot = base + __popc(m & ((1u << lane) - 1u));
                 if (slot < 1024) { s_keys[slot] = k; s_pix[slot] = p; }
             }
         }
     }
     __syncthreads();
     const int nall = min(s_count, wantc);
-    const int ns = min(nall, want);
-    // bitonic sort by key (keys are distinct), padded to a power of two
-    int n2 = 1;
-    while (n2 < nall) n2 <<= 1;
-    for (int i = nall + tid; i < n2; i += SEL_THREADS) s_keys[i] = ~0ull;
-    __syncthreads();
-    for (int k = 2; k <= n2; k <<= 1)
-        for (int jj = k >> 1; jj > 0; jj >>= 1) {
-            for (int i = tid; i < n2; i += SEL_THREADS) {
-                const int ixj = i ^ jj;
-                if (ixj > i) {
-                    const unsigned long long ki = s_keys[i], kj = s_keys[ixj];
-                    if ((ki > kj) == ((i & k) == 0)) {
-                        s_keys[i] = kj;
-                        s_keys[ixj] = ki;
-                        const int t = s_pix[i];
-                        s_pix[i] = s_pix[ixj];
-                        s_pix[ixj] = t;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    if (tid < ns) {
-        a.sel[tid] = s_pix[tid];
-        a.sel_log[a.stats[S_PROPAGATIONS] + tid] = s_pix[tid];
-    }
-    // candidates: in key order after the selection, the first K whose rows
-    // are not computed yet
+    // the selection: the `want` smallest gathered keys (a second radix
+    // selection over at most 1024 keys), in key order
+    unsigned long long t1 = ~0ull - 1;
+    if (want > 0 && want < nall)
+        t1 = radix_select([&](int i) -> unsigned long long { return s_keys[i]; }, nall, want, top, sc);
+    // candidates: after the selection, points whose rows are not computed
+    // yet; when there are more than K, the K smallest keys among them
+    auto cand_key = [&](int i) -> unsigned long long {
+        return (s_keys[i] > t1 && !(a.row_done && a.row_done[s_pix[i]])) ? s_keys[i] : ~0ull;
+    };
+    unsigned long long tk = ~0ull - 1;
     if (a.cand) {
-        const int i = ns + tid;
-        const bool ok = i < nall && !(a.row_done && a.row_done[s_pix[i]]);
-        const unsigned m = __ballot_sync(FULL, ok);
-        if ((tid & 31) == 0) s_wcount[tid >> 5] = __popc(m);
+        const unsigned m = __ballot_sync(FULL, tid < nall && cand_key(tid) != ~0ull);
+        if (lane == 0 && m) atomicAdd(&s_ncand, __popc(m));
         __syncthreads();
-        if (tid < 32) {
-            const int c = s_wcount[tid];
-            int incl = c;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int u = __shfl_up_sync(FULL, incl, o);
-                if (tid >= o) incl += u;
-            }
-            s_wcount[tid] = incl - c;  // exclusive
-            if (tid == 31) s_ncand = incl;
+        const int nc = s_ncand;
+        __syncthreads();
+        if (tid == 0) s_ncand = 0;
+        if (nc > a.K) tk = radix_select(cand_key, nall, a.K, top, sc);
+        __syncthreads();
+    }
+    const bool in_sel = tid < nall && s_keys[tid] <= t1;
+    const bool in_cand = tid < nall && a.cand && cand_key(tid) <= tk;
+    {
+        const unsigned ms = __ballot_sync(FULL, in_sel), mc = __ballot_sync(FULL, in_cand);
+        int bs = 0, bc = 0;
+        if (lane == 0) {
+            if (ms) bs = atomicAdd(&s_nsel, __popc(ms));
+            if (mc) bc = atomicAdd(&s_ncand, __popc(mc));
         }
-        __syncthreads();
-        const int pos = s_wcount[tid >> 5] + __popc(m & ((1u << (tid & 31)) - 1u));
-        if (ok && pos < a.K) a.cand[pos] = s_pix[i];
+        bs = __shfl_sync(FULL, bs, 0);
+        bc = __shfl_sync(FULL, bc, 0);
+        const unsigned below = (1u << lane) - 1u;
+        if (in_sel) {
+            const int slot = bs + __popc(ms & below);
+            s_selk[slot] = s_keys[tid];
+            s_selp[slot] = s_pix[tid];
+        }
+        if (in_cand) {
+            const int slot = bc + __popc(mc & below);
+            if (slot < a.K) a.cand[slot] = s_pix[tid];
+        }
+    }
+    __syncthreads();
+    const int ns = min(s_nsel, want);
+    if (tid < ns) {
+        const unsigned long long k = s_selk[tid];
+        int pos = 0;
+        for (int i = 0; i < ns; ++i) pos += s_selk[i] < k;
+        a.sel[pos] = s_selp[tid];
+        a.sel_log[a.stats[S_PROPAGATIONS] + pos] = s_selp[tid];
     }
     __syncthreads();
     if (tid == 0) {
@@ -274,6 +295,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
             a.stats[S_PROPAGATIONS] += ns;
         }
     }
+    (void)warp;
 }
 
 // Fill counts at the start (Sec. 2: D_mrk(i,i) = 1; pairs no path joins are

@@ -28,6 +28,17 @@ namespace gapsp {
 
 namespace {
 
+// Row of pixel p without a division: exact for p < 2^16 and W <= 256.
+__device__ __forceinline__ int row_of(const TreeArgs& a, int p) {
+    return a.wdiv ? (int)__umulhi((unsigned)p, a.wdiv) : p;
+}
+
+// Tile << 8 | bit of pixel p (the layout of the marks).
+__device__ __forceinline__ uint32_t tile_bit(const TreeArgs& a, int p) {
+    const int r = row_of(a, p), c = p - r * a.W;
+    return ((uint32_t)((r >> 3) * a.tiles_w + (c >> 3)) << 8) | (uint32_t)(((r & 7) << 3) | (c & 7));
+}
+
 // Canonical parent of b in the tree of s (-1 for the root and unreached):
 // the first neighbour q in increasing index with d(s,q) + w(q,b) = d(s,b).
 // fs: the grey levels (grey) or free flags (mask), in shared or global memory.
@@ -36,7 +47,7 @@ __device__ __forceinline__ int canonical_parent(const TreeArgs& a, const uint32_
     const uint32_t db = drow[b];
     if (b == s || db == UNREACH) return -1;
     const int W = a.W;
-    const int r = b / W, c = b - r * W;
+    const int r = row_of(a, b), c = b - r * W;
     const uint32_t fb = a.kind == 0 ? (uint32_t)fs[b] + 1u : 2u;  // w(q,b) = f(q) + fb, or 2
     auto tight = [&](int q) {
         if (a.kind == 1 && !fs[q]) return false;
@@ -101,9 +112,17 @@ __global__ void __launch_bounds__(1024) k_tree(TreeArgs a) {
     if (SMALL) {
         uint32_t* srow = reinterpret_cast<uint32_t*>(sdep);
         uint8_t* sf = reinterpret_cast<uint8_t*>(sdep + 5 * N);
-        for (int v = threadIdx.x; v < N; v += blockDim.x) {
-            srow[v] = __ldcg(drow + v);
-            sf[v] = a.f[v];
+        if ((N & 15) == 0) {
+            // 16-byte loads: the row starts at s * N * 4 bytes, the image at 0
+            for (int v = 4 * threadIdx.x; v < N; v += 4 * blockDim.x)
+                *reinterpret_cast<uint4*>(srow + v) = __ldcg(reinterpret_cast<const uint4*>(drow + v));
+            for (int v = 16 * threadIdx.x; v < N; v += 16 * blockDim.x)
+                *reinterpret_cast<uint4*>(sf + v) = __ldg(reinterpret_cast<const uint4*>(a.f + v));
+        } else {
+            for (int v = threadIdx.x; v < N; v += blockDim.x) {
+                srow[v] = __ldcg(drow + v);
+                sf[v] = a.f[v];
+            }
         }
         __syncthreads();
         for (int b = threadIdx.x; b < N; b += blockDim.x) {
@@ -115,16 +134,16 @@ __global__ void __launch_bounds__(1024) k_tree(TreeArgs a) {
     }
     __syncthreads();
     for (int v = threadIdx.x; v < N; v += blockDim.x) {
-        const uint32_t gv = __ldg(a.pgeo + v);
+        const uint32_t gv = tile_bit(a, v);
         const uint32_t t = gv >> 8;
         unsigned long long m = 1ull << (gv & 63);
         const int sv = SMALL ? (int)spar[v] : 0;
         int x = SMALL ? (sv == 0xFFFF ? -1 : sv - 1) : __ldcg(par + v);
-        uint32_t gx = x >= 0 ? __ldg(a.pgeo + x) : 0;
+        uint32_t gx = x >= 0 ? tile_bit(a, x) : 0;
         for (int guard = 0; x >= 0 && guard < 64 && (gx >> 8) == t; ++guard) {
             m |= 1ull << (gx & 63);
             x = SMALL ? (int)spar[x] - 1 : __ldcg(par + x);
-            gx = x >= 0 ? __ldg(a.pgeo + x) : 0;
+            gx = x >= 0 ? tile_bit(a, x) : 0;
         }
         const bool reached = SMALL ? sv != 0xFFFF : drow[v] != UNREACH;
         reinterpret_cast<unsigned long long*>(seg + v)[0] = m;
@@ -145,8 +164,8 @@ __global__ void __launch_bounds__(1024) k_tree(TreeArgs a) {
         int e2 = -1;
         if (e1 >= 0) e2 = SMALL ? (int)sdep[2 * N + e1] - 1 : __ldcg(a.jmp + (size_t)j * N + e1);
         unsigned long long y = 0;
-        if (e1 >= 0) y = (unsigned long long)(e1 + 1) | ((unsigned long long)(__ldg(a.pgeo + e1) >> 8) << 17);
-        if (e2 >= 0) y |= ((unsigned long long)(e2 + 1) << 27) | ((unsigned long long)(__ldg(a.pgeo + e2) >> 8) << 44);
+        if (e1 >= 0) y = (unsigned long long)(e1 + 1) | ((unsigned long long)(tile_bit(a, e1) >> 8) << 17);
+        if (e2 >= 0) y |= ((unsigned long long)(e2 + 1) << 27) | ((unsigned long long)(tile_bit(a, e2) >> 8) << 44);
         reinterpret_cast<unsigned long long*>(seg + v)[1] = y;
     }
     if (SMALL && a.dep_exit) {
