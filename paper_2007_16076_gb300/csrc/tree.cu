@@ -343,13 +343,18 @@ __global__ void k_fill(TreeArgs a) {
         bool gained = false;
         // one tile segment: the bits of m not yet in row b are new pairs
         auto take = [&](int t, unsigned long long m) {
-            if (!m) return;
-            // two 32-bit ORs: a 64-bit OR on shared memory is much slower
+            // a plain read first: most segments bring nothing new, and the
+            // shared-memory atomics are the scarce resource here
             unsigned* w32 = reinterpret_cast<unsigned*>(myrow + t);
-            const unsigned lo = (unsigned)m, hi = (unsigned)(m >> 32);
+            const unsigned lo = (unsigned)m & ~((volatile unsigned*)w32)[0];
+            const unsigned hi = (unsigned)(m >> 32) & ~((volatile unsigned*)w32)[1];
+            if (!(lo | hi)) return;
+            // claim the bits that look new: two 32-bit ORs (a 64-bit OR on
+            // shared memory is much slower); another tree of the round may
+            // have set some of them meanwhile
             const unsigned olo = lo ? atomicOr(w32, lo) : 0xFFFFFFFFu;
             const unsigned ohi = hi ? atomicOr(w32 + 1, hi) : 0xFFFFFFFFu;
-            unsigned long long nb = m & ~(((unsigned long long)ohi << 32) | olo);
+            unsigned long long nb = (((unsigned long long)hi << 32) | lo) & ~(((unsigned long long)ohi << 32) | olo);
             if (!nb) return;
             gained = true;
             mychg[t] = 1;
