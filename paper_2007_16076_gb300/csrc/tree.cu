@@ -21,8 +21,12 @@
 // segment is tested against row b's marks with a single AND. The operation
 // count (every ancestor pair, marked or not) comes from the tree depths
 // instead, so rows already filled are not walked at all.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace gapsp {
 
@@ -229,6 +233,94 @@ __global__ void __launch_bounds__(1024) k_tree(TreeArgs a) {
     }
     for (int o = 16; o > 0; o >>= 1) ops += __shfl_down_sync(FULL, ops, o);
     if ((threadIdx.x & 31) == 0 && ops) atomicAdd(a.stats + S_OPS, ops);
+}
+
+// The tree of one selected source on a cluster of two blocks (N <= 16384,
+// H >= 16, depth sums left to k_depths): each block owns half of the rows,
+// cut at a multiple of 8 so that no 8x8 tile is split, with the rows next to
+// its half staged for the parent tests. The second exit of a segment chain
+// may lie in the other half; it is read from the other block's shared
+// memory. Same results as k_tree.
+struct Tree2Layout {
+    int hs, smax, pmax;  // rows of the first half; staged and owned pixels of the larger half
+    __host__ __device__ Tree2Layout(int H, int W) {
+        hs = ((H / 2 + 7) / 8) * 8;
+        const int big = hs > H - hs ? hs : H - hs;
+        smax = (big + 2) * W;
+        pmax = big * W;
+    }
+    __host__ __device__ size_t bytes() const { return (size_t)smax * 5 + (size_t)pmax * 6 + 16; }
+};
+
+__global__ void __launch_bounds__(1024) k_tree2(TreeArgs a) {
+    extern __shared__ __align__(16) unsigned char sm2[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int j = blockIdx.x >> 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.dep_count = *a.nsel;
+    if (j >= *a.nsel) return;  // both blocks of the cluster leave together
+    const int N = a.N, W = a.W, H = a.H, s = a.sel[j];
+    const Tree2Layout L(H, W);
+    const int r0 = rank ? L.hs : 0, r1 = rank ? H : L.hs;
+    const int hr0 = r0 > 0 ? r0 - 1 : 0, hr1 = r1 < H ? r1 + 1 : H;
+    const int base = hr0 * W, S = (hr1 - hr0) * W;  // staged pixels [base, base + S)
+    const int p0 = r0 * W, P = (r1 - r0) * W;        // owned pixels [p0, p0 + P)
+    uint32_t* srow = reinterpret_cast<uint32_t*>(sm2);
+    uint8_t* sf = sm2 + (size_t)L.smax * 4;
+    uint16_t* spar = reinterpret_cast<uint16_t*>(sm2 + (((size_t)L.smax * 5 + 15) & ~(size_t)15));
+    uint16_t* acc = spar + L.pmax;
+    uint16_t* jx = acc + L.pmax;
+    const uint32_t* drow = a.D + (size_t)s * N;
+    ulonglong2* seg = a.seg + (size_t)j * N;
+    for (int v = threadIdx.x; v < S; v += blockDim.x) {
+        srow[v] = __ldcg(drow + base + v);
+        sf[v] = a.f[base + v];
+    }
+    __syncthreads();
+    // parents of the owned pixels (neighbours within the staged rows)
+    const uint32_t* drow_l = srow - base;
+    const uint8_t* sf_l = sf - base;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int b = p0 + i;
+        const int pb = canonical_parent(a, drow_l, sf_l, s, b);
+        spar[i] = drow_l[b] == UNREACH ? (uint16_t)0xFFFF : (uint16_t)(pb + 1);
+    }
+    __syncthreads();
+    // segments: a tile's pixels and their in-tile ancestors are all owned
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int v = p0 + i;
+        const uint32_t gv = tile_bit(a, v);
+        const uint32_t t = gv >> 8;
+        unsigned long long m = 1ull << (gv & 63);
+        const int sv = spar[i];
+        int x = sv == 0xFFFF ? -1 : sv - 1;
+        uint32_t gx = x >= 0 ? tile_bit(a, x) : 0;
+        for (int guard = 0; x >= 0 && guard < 64 && (gx >> 8) == t; ++guard) {
+            m |= 1ull << (gx & 63);
+            x = (int)spar[x - p0] - 1;
+            gx = x >= 0 ? tile_bit(a, x) : 0;
+        }
+        const bool reached = sv != 0xFFFF;
+        reinterpret_cast<unsigned long long*>(seg + v)[0] = m;
+        acc[i] = reached ? (uint16_t)__popcll(m) : 0;
+        jx[i] = reached ? (uint16_t)(x + 1) : 0;
+    }
+    cl.sync();  // both halves' exits are complete
+    const uint16_t* jx_other = cl.map_shared_rank(jx, rank ^ 1);
+    const int p0_other = rank ? 0 : L.hs * W;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int v = p0 + i;
+        const int e1 = (int)jx[i] - 1;
+        int e2 = -1;
+        if (e1 >= 0) e2 = (e1 >= p0 && e1 < p0 + P) ? (int)jx[e1 - p0] - 1 : (int)jx_other[e1 - p0_other] - 1;
+        unsigned long long y = 0;
+        if (e1 >= 0) y = (unsigned long long)(e1 + 1) | ((unsigned long long)(tile_bit(a, e1) >> 8) << 17);
+        if (e2 >= 0) y |= ((unsigned long long)(e2 + 1) << 27) | ((unsigned long long)(tile_bit(a, e2) >> 8) << 44);
+        reinterpret_cast<unsigned long long*>(seg + v)[1] = y;
+        a.dep_exit[(size_t)j * N + v] = jx[i];
+        a.dep_size[(size_t)j * N + v] = acc[i];
+    }
+    cl.sync();  // no block leaves while the other may read its exits
 }
 
 // Distance operations of one tree from its segment exits and sizes (N <=
@@ -455,6 +547,29 @@ cudaError_t launch_recount(const TreeArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_tree(const TreeArgs& a, int B, cudaStream_t st) {
+    if (a.N <= 16384 && a.dep_exit && a.H >= 16) {
+        // two blocks (one cluster) per tree
+        const Tree2Layout L(a.H, a.W);
+        const size_t smem = L.bytes();
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_tree2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr = true;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2 * B);
+        cfg.blockDim = dim3(1024);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, k_tree2, a);
+    }
     if (a.N <= 16384) {
         static bool attr = false;
         if (!attr) {
