@@ -112,6 +112,21 @@ class Clocks:
 PROP_DRAM_BYTES = None
 
 
+def rank_max(dist, world: int, x: float, device: str) -> float:
+    """The largest value of x over the ranks (the slowest rank's time)."""
+    if world == 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(entries_per_rank: float, steps: int, world: int, slowest_ms: float) -> float:
+    """Whole-job entries/s: every rank's entries over the slowest rank's time."""
+    return entries_per_rank * steps * world / (slowest_ms / 1e3)
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -187,11 +202,7 @@ def run_ours(a):
         torch.cuda.synchronize()
 
     def allmax(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return rank_max(dist, world, x, "cuda")
 
     w = _workload(a.side, rank)
     N = w.N
@@ -238,7 +249,7 @@ def run_ours(a):
     total_ms = allmax(total_ms)
     ms_per_step = total_ms / a.steps
     entries = float(N) * N
-    value = entries * a.steps * world / (total_ms / 1e3)
+    value = job_throughput(entries, a.steps, world, total_ms)
     props = st["propagations"]
 
     # per-kernel device time (a separate, event-bracketed pass)

@@ -24,7 +24,7 @@ _lib = None
 
 UNREACH = 0xFFFFFFFF
 UNSET = 0xFFFFFFFE
-ORDERS = {"naive": 0, "spiral": 1, "minfill": 2, "extrema": 3}
+ORDERS = {"naive": 0, "spiral": 1, "minfill": 2, "extrema": 3, "repulsion": 4}
 
 
 def build(force: bool = False) -> str:

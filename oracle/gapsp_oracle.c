@@ -387,7 +387,39 @@ int or_extrema(const uint8_t *f, const uint8_t *mask, int H, int W, int conn, in
 /* geodesic tree and fills every (ancestor, vertex) pair by Property 1.       */
 /* ------------------------------------------------------------------------ */
 
-enum { OR_NAIVE = 0, OR_SPIRAL = 1, OR_MINFILL = 2, OR_EXTREMA = 3 };
+enum { OR_NAIVE = 0, OR_SPIRAL = 1, OR_MINFILL = 2, OR_EXTREMA = 3, OR_REPULSION = 4 };
+
+/* Spiral turns as rings (Sec. 3.2, Algorithm "spiral method with
+ * repulsion"): frame k = {min(r, c, H-1-r, W-1-c) = k}, its free pixels in
+ * clockwise order from (k, k). A frame with at least two rows and two
+ * columns is a closed ring; a single row or column is an open line. Fills
+ * ring (all frames in turn), fstart[k] .. fstart[k+1] and fcyc[k]; returns
+ * the number of frames. */
+int or_rings(const uint8_t *mask, int kind, int H, int W, int32_t *ring, int32_t *fstart,
+             uint8_t *fcyc) {
+    int nframes = ((H < W ? H : W) + 1) / 2, n = 0;
+    for (int k = 0; k < nframes; k++) {
+        int r0 = k, r1 = H - 1 - k, c0 = k, c1 = W - 1 - k;
+        fstart[k] = n;
+        fcyc[k] = (uint8_t)(r1 > r0 && c1 > c0);
+#define OR_PUSH(rr, cc)                                            \
+    do {                                                           \
+        int p_ = (rr) * W + (cc);                                  \
+        if (!(kind == 1 && mask && !mask[p_])) ring[n++] = p_;     \
+    } while (0)
+        for (int c = c0; c <= c1; c++) OR_PUSH(r0, c);
+        if (r1 > r0) {
+            for (int r = r0 + 1; r <= r1; r++) OR_PUSH(r, c1);
+            if (c1 > c0) {
+                for (int c = c1 - 1; c >= c0; c--) OR_PUSH(r1, c);
+                for (int r = r1 - 1; r > r0; r--) OR_PUSH(r, c0);
+            }
+        }
+#undef OR_PUSH
+    }
+    fstart[nframes] = n;
+    return nframes;
+}
 
 /* stats[0] propagations, [1] pre-pass propagations, [2] distance operations
  * (sum over propagations of the depth of every reached vertex), [3] new
@@ -416,6 +448,14 @@ int or_fill(const uint8_t *f, const uint8_t *mask, int H, int W, int conn, int k
     uint32_t *gcen = (uint32_t *)malloc((size_t)N * sizeof(uint32_t));
     int32_t *S = (int32_t *)malloc((size_t)(B > 0 ? B : 1) * sizeof(int32_t));
     uint8_t *taken = (uint8_t *)calloc((size_t)N, 1);
+    /* repulsion order: rings, the current frame and its list S of ring
+     * positions (inS), and one SplitMix64 stream for the draws */
+    int32_t *ring = (int32_t *)malloc((size_t)N * sizeof(int32_t));
+    int32_t *fstart = (int32_t *)malloc((size_t)(N + 2) * sizeof(int32_t));
+    uint8_t *fcyc = (uint8_t *)malloc((size_t)(N + 1));
+    uint8_t *inS = (uint8_t *)calloc((size_t)N, 1);
+    int nframes = 0, cur = -1;
+    uint64_t rst = seed;
     for (int i = 0; i < 8; i++) stats[i] = 0;
 
     int ncomp = or_components(&g, comp, csize);
@@ -451,6 +491,8 @@ int or_fill(const uint8_t *f, const uint8_t *mask, int H, int W, int conn, int k
             if (comp[p] >= 0) seq[nseq++] = p;
     } else if (order == OR_SPIRAL) {
         nseq = or_spiral_sequence(mask, kind, H, W, seed, seq);
+    } else if (order == OR_REPULSION) {
+        nframes = or_rings(mask, kind, H, W, ring, fstart, fcyc);
     } else {
         uint32_t *e = (uint32_t *)malloc((size_t)N * sizeof(uint32_t));
         int32_t *cen = (int32_t *)malloc((size_t)N * sizeof(int32_t));
@@ -468,6 +510,46 @@ int or_fill(const uint8_t *f, const uint8_t *mask, int H, int W, int conn, int k
                 int p = seq[cursor++];
                 if (cnt[p] < (uint32_t)N) S[ns++] = p;
             }
+        } else if (order == OR_REPULSION) {
+            /* Spiral method with repulsion (Algorithm "spiral method with
+             * repulsion", h = 3): S holds the current turn's points not yet
+             * filled; a source is drawn uniformly from S, and its two left
+             * and two right neighbours on the turn leave S with it. When S
+             * is empty the outermost turn not yet filled starts again. The B
+             * sources of a round are drawn one after the other from the
+             * round-start state. */
+            if (cur >= 0)
+                for (int i = fstart[cur]; i < fstart[cur + 1]; i++)
+                    if (inS[i - fstart[cur]] && cnt[ring[i]] >= (uint32_t)N) inS[i - fstart[cur]] = 0;
+            while (ns < B) {
+                int len = cur >= 0 ? fstart[cur + 1] - fstart[cur] : 0, size = 0;
+                for (int i = 0; i < len; i++) size += inS[i];
+                if (size == 0) {
+                    cur = -1;
+                    for (int k = 0; k < nframes && cur < 0; k++)
+                        for (int i = fstart[k]; i < fstart[k + 1]; i++)
+                            if (cnt[ring[i]] < (uint32_t)N && !taken[ring[i]]) { cur = k; break; }
+                    if (cur < 0) break;
+                    len = fstart[cur + 1] - fstart[cur];
+                    for (int i = 0; i < len; i++) {
+                        int p = ring[fstart[cur] + i];
+                        inS[i] = (uint8_t)(cnt[p] < (uint32_t)N && !taken[p]);
+                        size += inS[i];
+                    }
+                }
+                int jth = (int)(or_splitmix64(&rst) % (uint64_t)size), at = -1;
+                for (int i = 0; i < len; i++)
+                    if (inS[i] && jth-- == 0) { at = i; break; }
+                int s = ring[fstart[cur] + at];
+                S[ns++] = s;
+                taken[s] = 1;
+                for (int dlt = -2; dlt <= 2; dlt++) {
+                    int i = at + dlt;
+                    if (fcyc[cur]) i = ((i % len) + len) % len;
+                    if (i >= 0 && i < len) inS[i] = 0;
+                }
+            }
+            for (int t = 0; t < ns; t++) taken[S[t]] = 0;
         } else if (order == OR_EXTREMA) {
             /* Geodesic extrema method (Sec. 3.3, Algorithm "geodesic extrema
              * method"): the unfilled points farthest from the centroid; among
@@ -536,6 +618,7 @@ int or_fill(const uint8_t *f, const uint8_t *mask, int H, int W, int conn, int k
         stats[3] += new_this_round;
     }
     stats[4] = (uint64_t)rounds;
+    free(ring); free(fstart); free(fcyc); free(inS);
     free(gcen); free(taken); free(S); free(rank); free(seq); free(parent); free(d);
     free(csize); free(comp); free(cnt); free(mrk);
     return status;

@@ -1,0 +1,65 @@
+"""Multi-rank bench logic on CPU: two gloo ranks, no GPU.
+
+The benchmark runs one independent replica per GPU (the method does not
+shard). Its whole-job figure is the entries of every rank over the slowest
+rank's time; these tests run that aggregation on two CPU processes.
+"""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+torch = pytest.importorskip("torch")
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, results):
+    import torch.distributed as dist
+
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        local_ms = 100.0 + 50.0 * rank  # rank 1 is the slowest
+        slowest = bench.rank_max(dist, world, local_ms, "cpu")
+        value = bench.job_throughput(16384.0 * 16384.0, 5, world, slowest)
+        results[rank] = (slowest, value)
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_agree_on_slowest_time_and_job_value():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        results = mgr.dict()
+        port = _free_port()
+        procs = [ctx.Process(target=_rank_main, args=(r, 2, port, results)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(120)
+        assert all(p.exitcode == 0 for p in procs)
+        got = dict(results)
+    assert got[0] == got[1]
+    slowest, value = got[0]
+    assert slowest == 150.0
+    # 2 ranks x 5 steps x N^2 entries over 150 ms
+    assert value == pytest.approx(2 * 5 * 16384.0 ** 2 / 0.150)
+
+
+def test_single_rank_needs_no_process_group():
+    import bench
+    assert bench.rank_max(None, 1, 42.0, "cpu") == 42.0
+    assert bench.job_throughput(100.0, 2, 1, 1000.0) == pytest.approx(200.0)

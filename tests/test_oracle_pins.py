@@ -251,6 +251,75 @@ def test_spiral_draws_are_uniform():
     assert chi2 < 24.3  # chi-square, 7 dof, p = 0.001
 
 
+def _ring(H, W, k):
+    """Frame k as a turn of the spiral: its pixels clockwise from (k, k)."""
+    r0, r1, c0, c1 = k, H - 1 - k, k, W - 1 - k
+    out = [(r0, c) for c in range(c0, c1 + 1)]
+    if r1 > r0:
+        out += [(r, c1) for r in range(r0 + 1, r1 + 1)]
+        if c1 > c0:
+            out += [(r1, c) for c in range(c1 - 1, c0 - 1, -1)]
+            out += [(r, c0) for r in range(r1 - 1, r0, -1)]
+    return [r * W + c for r, c in out], (r1 > r0 and c1 > c0)
+
+
+def test_repulsion_keeps_sources_apart_on_a_turn():
+    """Algorithm "spiral method with repulsion" (h = 3): the first sources
+    come from the outermost turn, and each takes its two neighbours on each
+    side out of the draw, so sources drawn in one pass over a turn are at
+    least three ring steps apart. On a 25 x 25 image the outer turn has 96
+    points; the first 8 draws (at most 40 points removed, no turn point
+    filled yet but the sources) all belong to the first pass."""
+    img = synth.blobs(25, 25, 4, 3.0, 55.0, seed=3)
+    ring, cyclic = _ring(25, 25, 0)
+    assert cyclic and len(ring) == 96
+    pos = {p: i for i, p in enumerate(ring)}
+    for seed in range(5):
+        r = oracle.fill(img, "repulsion", B=1, conn=8, seed=seed)
+        first = [int(x) for x in r.sources[:8]]
+        assert all(p in pos for p in first)
+        for a in range(8):
+            for b in range(a):
+                dd = abs(pos[first[a]] - pos[first[b]])
+                assert min(dd, 96 - dd) >= 3
+        # without repulsion (spiral), some seed puts two early sources close
+    close = 0
+    for seed in range(20):
+        sp = [int(x) for x in oracle.fill(img, "spiral", B=1, conn=8, seed=seed).sources[:8]]
+        for a in range(8):
+            for b in range(a):
+                dd = abs(pos[sp[a]] - pos[sp[b]])
+                close += min(dd, 96 - dd) < 3
+    assert close > 0
+
+
+def test_repulsion_open_line_and_batches():
+    """A single row is an open turn (no wrap-around): on 1 x 11 the first
+    pass takes sources at least three apart along the row; with B sources
+    per round each round draws them one after the other from the state at
+    the round's start, and the result is a valid fill."""
+    img = synth.uniform_random(1, 11, 1, 255, seed=2)
+    for seed in range(10):
+        r = oracle.fill(img, "repulsion", B=3, conn=8, seed=seed)
+        first = sorted(int(x) for x in r.sources[:3])
+        assert first[1] - first[0] >= 3 and first[2] - first[1] >= 3
+        assert r.new_pairs == 11 * 10 // 2
+
+
+def test_repulsion_first_draw_is_uniform():
+    """The first source is drawn uniformly from the outermost turn (here the
+    20 points of a 6 x 6 frame)."""
+    img = np.full((6, 6), 7, dtype=np.uint8)
+    ring, _ = _ring(6, 6, 0)
+    counts = {p: 0 for p in ring}
+    n = 2000
+    for seed in range(n):
+        counts[int(oracle.fill(img, "repulsion", B=1, conn=4, seed=seed).sources[0])] += 1
+    exp = n / 20
+    chi2 = sum((c - exp) ** 2 / exp for c in counts.values())
+    assert chi2 < 43.8  # chi-square, 19 dof, p = 0.001
+
+
 def test_extrema_constant_square():
     """Sec. 3.3 on a constant image: the centroid is the pixel farthest from
     the edges (the centre), and Ext starts at the corners."""
@@ -300,7 +369,7 @@ def test_one_row_minfill_single_propagation(W):
     assert r.new_pairs == W * (W - 1) // 2
 
 
-@pytest.mark.parametrize("order", ["naive", "spiral", "extrema", "minfill"])
+@pytest.mark.parametrize("order", ["naive", "spiral", "repulsion", "extrema", "minfill"])
 @pytest.mark.parametrize("B", [1, 3, 8])
 @pytest.mark.parametrize("conn", [4, 8])
 def test_fill_invariants(order, B, conn):
@@ -319,7 +388,7 @@ def test_fill_invariants(order, B, conn):
     assert r.rounds == -(-r.propagations // B)
 
 
-@pytest.mark.parametrize("order", ["naive", "spiral", "extrema", "minfill"])
+@pytest.mark.parametrize("order", ["naive", "spiral", "repulsion", "extrema", "minfill"])
 def test_fill_mask_invariants(order):
     """Mask variant: pairs in different components are filled at the start
     with 'unreachable'; the trees fill exactly the same-component pairs."""
