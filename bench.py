@@ -6,7 +6,7 @@ Workload: the 128x128 blob image (N = 16384, 268M-entry uint32 array),
 one complete gapsp_all_pairs fill in the minimum-filling-rate order (the
 paper's method: extrema pre-pass, then rounds of selection, propagation,
 tree and fill). `value` = N^2 entries per step / step time, summed over
-ranks. The naive, spiral and extrema orders and the naive method without the tree
+ranks. The naive, spiral, spiral-with-repulsion and extrema orders and the naive method without the tree
 (one propagation per pixel, gapsp_rows) are timed beside it.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -40,6 +40,8 @@ def _args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--side", type=int, default=128, help="image side (128 = the workload)")
     ap.add_argument("--no-extras", action="store_true", help="skip the side measurements")
+    ap.add_argument("--serve-seconds", type=float, default=4.0,
+                    help="length of the simulated serving run among the side measurements")
     ap.add_argument("--timed-only", action="store_true",
                     help="warm-up and timed steps only (for profiler runs); prints no JSON")
     return ap.parse_args()
@@ -125,6 +127,74 @@ def rank_max(dist, world: int, x: float, device: str) -> float:
 def job_throughput(entries_per_rank: float, steps: int, world: int, slowest_ms: float) -> float:
     """Whole-job entries/s: every rank's entries over the slowest rank's time."""
     return entries_per_rank * steps * world / (slowest_ms / 1e3)
+
+
+def _serve(gp, torch, stream, seconds: float, rate: float = 50.0, seed: int = 0) -> dict:
+    """Serving: Poisson arrivals at `rate` requests/s for `seconds`. 70 % are
+    rows requests (K ~ U{1..512} sources on a square image whose side is
+    log-uniform in [64, 256]), 30 % all-pairs requests (minimum filling rate,
+    side log-uniform in [16, 160]); 8-connected blob images. Requests are
+    served one at a time in arrival order, each through its own handle
+    (gapsp_create, the call, gapsp_destroy); the result stays on the device.
+    Latency runs from arrival to the result being complete."""
+    import math
+
+    import numpy as np
+
+    from paper_2007_16076_gb300 import synth
+    rng = np.random.default_rng(seed)
+
+    def side(lo, hi):
+        return int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+
+    # a pool of images per kind (generating one per request would dominate)
+    pool_rows = [synth.scaled_blobs(s, s, 8, seed=100 + i).img for i, s in
+                 enumerate(side(64, 256) for _ in range(12))]
+    pool_all = [synth.scaled_blobs(s, s, 8, seed=200 + i).img for i, s in
+                enumerate(side(16, 160) for _ in range(12))]
+    reqs, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > seconds:
+            break
+        if rng.random() < 0.7:
+            img = pool_rows[int(rng.integers(len(pool_rows)))]
+            k = int(rng.integers(1, 513))
+            src = rng.integers(0, img.size, size=k).astype(np.int32)
+            reqs.append((t, "rows", img, src))
+        else:
+            reqs.append((t, "all_pairs", pool_all[int(rng.integers(len(pool_all)))], None))
+
+    def serve_one(kind, img, src):
+        with gp.Image(img, conn=8, B=32, stream=stream) as im:
+            if kind == "rows":
+                im.rows(torch.from_numpy(src).cuda())
+            else:
+                im.all_pairs("minfill")
+            torch.cuda.synchronize()
+
+    serve_one("rows", pool_rows[0], np.arange(4, dtype=np.int32))  # warm-up
+    serve_one("all_pairs", pool_all[0], None)
+    lat = {"rows": [], "all_pairs": []}
+    t0 = time.perf_counter()
+    for t_arr, kind, img, src in reqs:
+        now = time.perf_counter() - t0
+        if now < t_arr:
+            time.sleep(t_arr - now)
+        serve_one(kind, img, src)
+        lat[kind].append(time.perf_counter() - t0 - t_arr)
+    span = time.perf_counter() - t0
+    both = sorted(lat["rows"] + lat["all_pairs"])
+
+    def pct(v, q):
+        return round(1e3 * float(np.percentile(v, q)), 3) if v else None
+
+    return {"requests": len(reqs), "offered_per_s": rate, "seconds": seconds,
+            "served_per_s": len(reqs) / span,
+            "p50_ms": pct(both, 50), "p99_ms": pct(both, 99), "max_ms": round(1e3 * max(both), 3),
+            "rows_p50_ms": pct(lat["rows"], 50), "rows_p99_ms": pct(lat["rows"], 99),
+            "all_pairs_p50_ms": pct(lat["all_pairs"], 50), "all_pairs_p99_ms": pct(lat["all_pairs"], 99),
+            "note": "one handle per request (create, call, destroy), result left on the device"}
 
 
 def _peaks():
@@ -218,6 +288,7 @@ def run_ours(a):
     clocks.start()
     time.sleep(1.0)
     for _ in range(max(3, a.warmup)):
+        flush.fill_(1)  # the first use of the flush kernel loads its module: not in the timed steps
         _, st = im.all_pairs("minfill", out=D)
 
     l0 = im.kernel_launches
@@ -305,7 +376,7 @@ def run_ours(a):
 
     extras = {}
     if not a.no_extras:
-        for order in ("naive", "spiral", "extrema"):
+        for order in ("naive", "spiral", "repulsion", "extrema"):
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -357,6 +428,7 @@ def run_ours(a):
         for imb in ims:
             imb.close()
         del outs
+        extras["serve"] = _serve(gp, torch, stream, seconds=a.serve_seconds)
 
     # end to end through the C ABI with host buffers: create from a host image,
     # fill into pinned host memory, destroy

@@ -15,7 +15,9 @@
  *     points plus Property 1 (Sec. 2): along the geodesic tree of a
  *     propagation from s, d(a,b) = d(s,b) - d(s,a) for every ancestor a of b;
  *   - sources are chosen in naive (raster) order, spiral order (Sec. 3.1,
- *     Algorithm "spiral method"), by decreasing distance from the geodesic
+ *     Algorithm "spiral method"), spiral order with repulsion (Sec. 3.2: a
+ *     source drawn on the current turn takes its two neighbours on each side
+ *     of the turn out of the draw), by decreasing distance from the geodesic
  *     centroid with ties to the least filled point (Sec. 3.3, Algorithm
  *     "geodesic extrema method") or by minimum filling rate with ties to the
  *     greatest geodesic extremum (Sec. 3.4, Algorithm "method based on the
@@ -71,7 +73,8 @@ typedef enum {
     GAPSP_NAIVE = 0,   /* raster order, filled points skipped (Sec. 1 with the tree) */
     GAPSP_SPIRAL = 1,  /* Sec. 3.1, Algorithm "spiral method" */
     GAPSP_MINFILL = 2, /* Sec. 3.4, Algorithm "method based on the filling rate" */
-    GAPSP_EXTREMA = 3  /* Sec. 3.3, Algorithm "geodesic extrema method" */
+    GAPSP_EXTREMA = 3, /* Sec. 3.3, Algorithm "geodesic extrema method" */
+    GAPSP_REPULSION = 4 /* Sec. 3.2, Algorithm "spiral method with repulsion", h = 3 */
 } gapsp_order;
 
 typedef enum {
@@ -83,7 +86,7 @@ typedef struct {
     int conn;          /* 4 or 8 (0 = 8) */
     gapsp_kind kind;   /* GAPSP_GREY or GAPSP_MASK */
     int B;             /* sources per round, 1..1024 (0 = 32) */
-    uint64_t seed;     /* seed of the spiral order's draws */
+    uint64_t seed;     /* seed of the spiral orders' draws */
     size_t mem_budget; /* bytes of device memory a call may use (0 = no limit) */
     int sweep_phases;  /* warps per sweep direction in a propagation: 0 = auto, 1, 2 or 4 */
     int fill_rows;     /* rows of marks per tree-fill block: 0 = auto, else 1..32 */

@@ -18,7 +18,7 @@ import numpy as np
 from . import _build
 
 UNREACH = 0xFFFFFFFF
-ORDERS = {"naive": 0, "spiral": 1, "minfill": 2, "extrema": 3}
+ORDERS = {"naive": 0, "spiral": 1, "minfill": 2, "extrema": 3, "repulsion": 4}
 KINDS = {"grey": 0, "mask": 1}
 KERNELS = ("select", "propagate", "tree", "lookahead", "fill", "init", "prepass", "depths", "recount")
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "memory budget exceeded",

@@ -60,6 +60,12 @@ struct gapsp_handle {
     int32_t* rank = nullptr;
     int32_t* grank = nullptr;
     uint8_t* row_done = nullptr;  // [N]: row already written by a propagation
+    int32_t* rp_ring = nullptr;   // spiral with repulsion: turns, S, draw state
+    int32_t* rp_fstart = nullptr;
+    uint8_t* rp_fcyc = nullptr;
+    unsigned* rp_inS = nullptr;
+    RepState* rp_state = nullptr;
+    uint8_t* rp_taken = nullptr;
     int32_t* cand = nullptr;      // [2][1024]: lookahead candidates, by round parity
     int* ncand = nullptr;         // [2]
     uint16_t* dep_exit = nullptr; // [2][B][N] (N <= 16384): trees handed to k_depths, by round parity
@@ -134,6 +140,35 @@ uint64_t splitmix_next(uint64_t& s) {
 // (Fisher-Yates driven by one SplitMix64 stream per frame). Taking the next
 // unfilled point of this sequence draws uniformly among the frame's
 // unfilled points, as Algorithm "spiral method" does.
+// Turns of the spiral as rings (Sec. 3.2): frame k's free pixels clockwise
+// from (k, k); a frame with two rows and two columns or more is closed.
+int spiral_rings(int H, int W, const std::vector<uint8_t>& freef, std::vector<int32_t>& ring,
+                 std::vector<int32_t>& fstart, std::vector<uint8_t>& fcyc) {
+    const int nf = (std::min(H, W) + 1) / 2;
+    ring.clear();
+    fstart.assign(nf + 1, 0);
+    fcyc.assign(nf, 0);
+    auto push = [&](int r, int c) {
+        const int p = r * W + c;
+        if (freef.empty() || freef[p]) ring.push_back(p);
+    };
+    for (int k = 0; k < nf; ++k) {
+        const int r0 = k, r1 = H - 1 - k, c0 = k, c1 = W - 1 - k;
+        fstart[k] = (int)ring.size();
+        fcyc[k] = (uint8_t)(r1 > r0 && c1 > c0);
+        for (int c = c0; c <= c1; ++c) push(r0, c);
+        if (r1 > r0) {
+            for (int r = r0 + 1; r <= r1; ++r) push(r, c1);
+            if (c1 > c0) {
+                for (int c = c1 - 1; c >= c0; --c) push(r1, c);
+                for (int r = r1 - 1; r > r0; --r) push(r, c0);
+            }
+        }
+    }
+    fstart[nf] = (int)ring.size();
+    return nf;
+}
+
 std::vector<int32_t> spiral_sequence(int H, int W, uint64_t seed, const std::vector<uint8_t>& freef) {
     std::vector<std::vector<int32_t>> frames((std::min(H, W) + 1) / 2);
     for (int p = 0; p < H * W; ++p) {
@@ -180,7 +215,7 @@ size_t fill_state_bytes(const gapsp_handle* h) {
     // rank, grank, round_new, sel_log, emap, gmap, best, cen, row_done per
     // point; the lookahead candidate buffers
     return N * h->words * 8 + B * N * (4 + 16 + 8 + 8) +
-           N * (4 + 4 + 1 + 4 + 4 + 4 + 8 + 4 + 4 + 4 + 8 + 1 + 1) + 2 * 1024 * 4 + 4096 +
+           N * (4 + 4 + 1 + 4 + 4 + 4 + 8 + 4 + 4 + 4 + 8 + 1 + 1 + 4 + 4 + 1 + 1) + 2 * 1024 * 4 + 4096 +
            (N <= 16384 ? 8 * B * N : 0);  // trees handed to k_depths
 }
 
@@ -203,6 +238,12 @@ gapsp_status ensure_fill_state(gapsp_handle* h) {
     CK(dalloc(&h->rank, N));
     CK(dalloc(&h->grank, N));
     CK(dalloc(&h->row_done, N));
+    CK(dalloc(&h->rp_ring, N));
+    CK(dalloc(&h->rp_fstart, N + 2));
+    CK(dalloc(&h->rp_fcyc, N + 1));
+    CK(dalloc(&h->rp_inS, 32));
+    CK(dalloc(&h->rp_state, 1));
+    CK(dalloc(&h->rp_taken, N));
     CK(dalloc(&h->cand, 2 * 1024));
     CK(dalloc(&h->ncand, 2));
     if (N <= 16384) {
@@ -229,6 +270,8 @@ void free_all(gapsp_handle* h) {
     dfree(h->cnt); dfree(h->cnt_base); dfree(h->dirty); dfree(h->marks); dfree(h->parent); dfree(h->seg); dfree(h->jmp); dfree(h->acc);
     dfree(h->sel); dfree(h->nsel); dfree(h->cursor); dfree(h->done); dfree(h->seq); dfree(h->rank); dfree(h->grank);
     dfree(h->row_done); dfree(h->cand); dfree(h->ncand);
+    dfree(h->rp_ring); dfree(h->rp_fstart); dfree(h->rp_fcyc); dfree(h->rp_inS); dfree(h->rp_state);
+    dfree(h->rp_taken);
     dfree(h->dep_exit); dfree(h->dep_size); dfree(h->dep_count);
     dfree(h->stats); dfree(h->round_new); dfree(h->last_new); dfree(h->sel_log);
     dfree(h->emap); dfree(h->gmap); dfree(h->best); dfree(h->cen);
@@ -472,6 +515,7 @@ struct FillRun {
     int nseq = 0;
     uint64_t prepass = 0;
     SelectArgs sa{};
+    RepArgs ra{};
     PropArgs pa{};
     TreeArgs ta{};
     int rounds = 0;
@@ -545,9 +589,28 @@ gapsp_status fill_begin(FillRun& r) {
     cudaStream_t s = r.s;
     uint32_t* Dd = r.Dd;
 
-    // host-built sequences (naive / spiral)
+    // host-built sequences (naive / spiral) and turns (spiral with repulsion)
     const bool ranked = r.order == GAPSP_MINFILL || r.order == GAPSP_EXTREMA;
-    if (!ranked) {
+    if (r.order == GAPSP_REPULSION) {
+        std::vector<uint8_t> freef;
+        if (h->kind == GAPSP_MASK) {
+            freef.resize(N);
+            CK(cudaMemcpy(freef.data(), h->f, N, cudaMemcpyDeviceToHost));
+        }
+        std::vector<int32_t> ring, fstart;
+        std::vector<uint8_t> fcyc;
+        const int nf = spiral_rings(h->H, h->W, freef, ring, fstart, fcyc);
+        if (!ring.empty())
+            CK(cudaMemcpyAsync(h->rp_ring, ring.data(), ring.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(h->rp_fstart, fstart.data(), fstart.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        if (nf) CK(cudaMemcpyAsync(h->rp_fcyc, fcyc.data(), fcyc.size(), cudaMemcpyHostToDevice, s));
+        const RepState rs{h->seed, -1, nf};
+        CK(cudaMemcpyAsync(h->rp_state, &rs, sizeof(rs), cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(h->rp_inS, 0, 32 * sizeof(unsigned), s));
+        CK(cudaMemsetAsync(h->rp_taken, 0, N, s));
+        CK(cudaStreamSynchronize(s));  // the host vectors go out of scope
+        r.ra = RepArgs{h->rp_ring, h->rp_fstart, h->rp_fcyc, h->rp_inS, h->rp_state, h->rp_taken};
+    } else if (!ranked) {
         std::vector<uint8_t> freef;
         if (h->kind == GAPSP_MASK) {
             freef.resize(N);
@@ -627,7 +690,8 @@ gapsp_status fill_begin(FillRun& r) {
     pa.convert = h->kind == GAPSP_MASK;
     pa.sweeps = h->stats + S_SWEEPS;
     pa.row_done = h->row_done;
-    r.K = lookahead_count(h, pa);
+    // the repulsion order's draws cannot be foreseen: no lookahead
+    r.K = r.order == GAPSP_REPULSION ? 0 : lookahead_count(h, pa);
     if (r.K > 0) {
         r.sa.K = r.K;
         r.sa.KL = 1024 - h->B;
@@ -696,7 +760,8 @@ gapsp_status fill_enqueue(FillRun& r, int chunk) {
         }
         {
             ProfScope ps(h, K_SELECT, s);
-            CK(launch_select(r.sa, s));
+            if (r.order == GAPSP_REPULSION) CK(launch_select_repulsion(r.sa, r.ra, s));
+            else CK(launch_select(r.sa, s));
         }
         if (r.K > 0) {
             // this round's candidates go to the second stream, where they
@@ -829,7 +894,8 @@ gapsp_status fill_finish(FillRun& r, gapsp_stats* st) {
 }
 
 bool valid_order(gapsp_order o) {
-    return o == GAPSP_NAIVE || o == GAPSP_SPIRAL || o == GAPSP_MINFILL || o == GAPSP_EXTREMA;
+    return o == GAPSP_NAIVE || o == GAPSP_SPIRAL || o == GAPSP_MINFILL || o == GAPSP_EXTREMA ||
+           o == GAPSP_REPULSION;
 }
 
 }  // namespace

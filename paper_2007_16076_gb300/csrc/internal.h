@@ -103,6 +103,23 @@ struct SelectArgs {
 };
 cudaError_t launch_select(const SelectArgs& a, cudaStream_t st);
 
+// Spiral with repulsion: the turns (rings of free pixels, clockwise), the
+// current turn's list S as a bit per ring position, and the draw state.
+struct RepState {
+    unsigned long long rng;     // SplitMix64 state
+    int cur;                    // current turn, -1 = none
+    int nframes;
+};
+struct RepArgs {
+    const int32_t* ring;        // [N] pixels of all turns, turn after turn
+    const int32_t* fstart;      // [nframes + 1]
+    const uint8_t* fcyc;        // [nframes]: closed ring (else an open line)
+    unsigned* inS;              // [32]: bit i of word i/32 = ring position i of the current turn in S
+    RepState* state;
+    uint8_t* taken;             // [N]: drawn in the current round
+};
+cudaError_t launch_select_repulsion(const SelectArgs& a, const RepArgs& r, cudaStream_t st);
+
 struct InitArgs {
     int N;
     uint32_t* D;

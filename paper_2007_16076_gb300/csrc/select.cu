@@ -298,6 +298,114 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
     (void)warp;
 }
 
+// Spiral method with repulsion (Algorithm "spiral method with repulsion",
+// h = 3), one warp. S is the current turn's list of points not yet filled,
+// one bit per ring position (a turn has at most 1020 points: 32 words, one
+// per lane). A source is drawn uniformly from S with SplitMix64 (Steele, Lea
+// & Flood, OOPSLA 2014); it and its two neighbours on each side of the turn
+// (wrapping around on a closed ring) leave S. Filled points leave S at the
+// start of each round; an empty S restarts at the outermost turn that has a
+// point not yet filled (and not drawn in this round).
+__device__ __forceinline__ unsigned long long splitmix_next(unsigned long long& st) {
+    unsigned long long z = (st += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_select_rep(SelectArgs a, RepArgs r) {
+    const int lane = threadIdx.x;
+    if (*a.done) { if (lane == 0) *a.nsel = 0; return; }
+    RepState st = *r.state;
+    unsigned word = r.inS[lane];
+    auto warp_sum = [](int v) {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+        return v;
+    };
+    // points filled by the previous round leave S
+    if (st.cur >= 0) {
+        const int base = r.fstart[st.cur], len = r.fstart[st.cur + 1] - base;
+        for (int b = 0; b < 32; ++b) {
+            const int i = lane * 32 + b;
+            if (i < len && ((word >> b) & 1u) && a.cnt[r.ring[base + i]] >= (uint32_t)a.N) word &= ~(1u << b);
+        }
+    }
+    int ns = 0;
+    while (ns < a.B) {
+        int size = warp_sum(__popc(word));
+        if (size == 0) {
+            st.cur = -1;
+            for (int k = 0; k < st.nframes && st.cur < 0; ++k) {
+                const int base = r.fstart[k], len = r.fstart[k + 1] - base;
+                bool any = false;
+                for (int i = lane; i < len; i += 32) {
+                    const int p = r.ring[base + i];
+                    any |= a.cnt[p] < (uint32_t)a.N && !r.taken[p];
+                }
+                if (__any_sync(FULL, any)) st.cur = k;
+            }
+            if (st.cur < 0) break;
+            const int base = r.fstart[st.cur], len = r.fstart[st.cur + 1] - base;
+            word = 0;
+            for (int b = 0; b < 32; ++b) {
+                const int i = lane * 32 + b;
+                if (i < len) {
+                    const int p = r.ring[base + i];
+                    if (a.cnt[p] < (uint32_t)a.N && !r.taken[p]) word |= 1u << b;
+                }
+            }
+            size = warp_sum(__popc(word));
+        }
+        const int base = r.fstart[st.cur], len = r.fstart[st.cur + 1] - base;
+        const int jth = (int)(splitmix_next(st.rng) % (unsigned long long)size);  // same on every lane
+        // the lane holding the jth point of S, by an exclusive scan of counts
+        const int pc = __popc(word);
+        int incl = pc;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int excl = incl - pc;
+        const bool mine = excl <= jth && jth < incl;
+        int at = mine ? lane * 32 + (int)__fns(word, 0, jth - excl + 1) : 0;
+        const unsigned who = __ballot_sync(FULL, mine);
+        at = __shfl_sync(FULL, at, __ffs(who) - 1);
+        const int s = r.ring[base + at];
+        if (lane == 0) {
+            a.sel[ns] = s;
+            r.taken[s] = 1;
+        }
+        ++ns;
+        for (int d = -2; d <= 2; ++d) {
+            int i = at + d;
+            if (r.fcyc[st.cur]) i = ((i % len) + len) % len;
+            if (i >= 0 && i < len && (i >> 5) == lane) word &= ~(1u << (i & 31));
+        }
+        __syncwarp();
+    }
+    r.inS[lane] = word;
+    const unsigned long long props = a.stats[S_PROPAGATIONS];
+    __syncwarp();
+    for (int i = lane; i < ns; i += 32) {
+        a.sel_log[props + i] = a.sel[i];
+        r.taken[a.sel[i]] = 0;
+    }
+    if (lane == 0) {
+        *r.state = st;
+        *a.nsel = ns;
+        const unsigned long long rounds = a.stats[S_ROUNDS];
+        const unsigned long long cur_new = a.stats[S_NEW] >> 1;
+        if (rounds > 0) a.round_new_log[rounds - 1] = cur_new - *a.last_new;
+        *a.last_new = cur_new;
+        if (ns == 0) {
+            *a.done = 1;
+        } else {
+            a.stats[S_ROUNDS] = rounds + 1;
+            a.stats[S_PROPAGATIONS] = props + ns;
+        }
+    }
+}
+
 // Fill counts at the start (Sec. 2: D_mrk(i,i) = 1; pairs no path joins are
 // known at once) and the zero diagonal of D.
 __global__ void k_init(InitArgs a) {
@@ -424,6 +532,11 @@ cudaError_t launch_select(const SelectArgs& a, cudaStream_t st) {
         }
     }
     else k_select_seq<<<1, 32, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select_repulsion(const SelectArgs& a, const RepArgs& r, cudaStream_t st) {
+    k_select_rep<<<1, 32, 0, st>>>(a, r);
     return cudaGetLastError();
 }
 

@@ -137,14 +137,14 @@ def _check_fill(gp, img, order, B, conn, kind="grey", mask=None, seed=0):
     return st
 
 
-@pytest.mark.parametrize("order", ["naive", "spiral", "extrema", "minfill"])
+@pytest.mark.parametrize("order", ["naive", "spiral", "repulsion", "extrema", "minfill"])
 def test_all_pairs_plain_32(gp, order):
     """32x32 blobs, 4-connected, B = 1: the paper's sequential loop."""
     w = synth.plain_32(0)
     _check_fill(gp, w.img, order, 1, 4)
 
 
-@pytest.mark.parametrize("order", ["naive", "spiral", "extrema", "minfill"])
+@pytest.mark.parametrize("order", ["naive", "spiral", "repulsion", "extrema", "minfill"])
 @pytest.mark.parametrize("B", [2, 5, 32])
 @pytest.mark.parametrize("shape,conn", [((17, 23), 8), ((24, 9), 4), ((1, 40), 8)])
 def test_all_pairs_batched(gp, order, B, shape, conn):
@@ -152,7 +152,7 @@ def test_all_pairs_batched(gp, order, B, shape, conn):
     _check_fill(gp, img, order, B, conn, seed=B)
 
 
-@pytest.mark.parametrize("order", ["naive", "spiral", "extrema", "minfill"])
+@pytest.mark.parametrize("order", ["naive", "spiral", "repulsion", "extrema", "minfill"])
 @pytest.mark.parametrize("conn", [4, 8])
 def test_all_pairs_mask(gp, order, conn):
     m = synth.disk_mask(26, 31, 0.4, 2, 4, seed=conn)
@@ -164,7 +164,7 @@ def test_all_pairs_mask(gp, order, conn):
 def test_all_pairs_degenerate(gp):
     for img in (np.array([[7]], np.uint8), np.array([[1, 2]], np.uint8),
                 np.full((3, 1), 4, np.uint8)):
-        for order in ("naive", "spiral", "extrema", "minfill"):
+        for order in ("naive", "spiral", "repulsion", "extrema", "minfill"):
             _check_fill(gp, img, order, 1, 8)
 
 
@@ -187,7 +187,7 @@ def test_all_pairs_repeat_and_orders_share_handle(gp):
             assert np.array_equal(_u32(D), ref)
 
 
-@pytest.mark.parametrize("order", ["minfill", "naive", "spiral", "extrema"])
+@pytest.mark.parametrize("order", ["minfill", "naive", "spiral", "extrema", "repulsion"])
 @pytest.mark.parametrize("lookahead", [-1, 1, 5, 0])
 def test_lookahead_changes_nothing(gp, order, lookahead):
     """Rows computed ahead of their round (any candidate count, or none)
@@ -202,7 +202,7 @@ def test_lookahead_changes_nothing(gp, order, lookahead):
         assert st[k] == getattr(ref, k), k
     assert np.array_equal(st["round_new"], ref.round_new)
     assert np.array_equal(st["sources"], ref.sources)
-    if lookahead < 0:
+    if lookahead < 0 or order == "repulsion":  # random draws: nothing to foresee
         assert st["lookahead_propagations"] == 0
     else:
         assert st["lookahead_propagations"] > 0
@@ -228,7 +228,7 @@ def test_budget_rejected_before_allocation(gp):
 # Full-size workload: 128x128, 8-connected, B = 32
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("order", ["minfill", "naive", "spiral", "extrema"])
+@pytest.mark.parametrize("order", ["minfill", "naive", "spiral", "extrema", "repulsion"])
 def test_full_size_blobs128(gp, order):
     """The benchmark's workload in the benchmark's launch configuration:
     counts, per-round new pairs and the selected sources against the
