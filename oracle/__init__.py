@@ -64,10 +64,13 @@ def _ptr(a):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 
 
+KINDS = {"grey": 0, "mask": 1, "l1": 2}
+
+
 def _prep(img, mask, kind):
     img = np.ascontiguousarray(img, dtype=np.uint8)
     H, W = img.shape
-    k = 1 if kind in (1, "mask") else 0
+    k = KINDS[kind] if isinstance(kind, str) else int(kind)
     m = None
     if k == 1:
         if mask is None:
@@ -141,7 +144,7 @@ def parents(img, drow, s, conn=8, kind="grey", mask=None) -> np.ndarray:
 
 def spiral_sequence(H, W, seed, kind="grey", mask=None) -> np.ndarray:
     """Frame-by-frame shuffled pixel sequence (Sec. 3.1, spiral method)."""
-    k = 1 if kind in (1, "mask") else 0
+    k = KINDS[kind] if isinstance(kind, str) else int(kind)
     m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
     out = np.empty(H * W, dtype=np.int32)
     n = _load().or_spiral_sequence(_ptr(m), k, H, W, ctypes.c_uint64(seed & (2**64 - 1)),

@@ -45,11 +45,11 @@
 typedef struct {
     const uint8_t *f;    /* grey values, H*W, row-major */
     const uint8_t *mask; /* 1 = free pixel; NULL means every pixel is free */
-    int H, W, conn, kind; /* kind 0 = grey weights, 1 = mask weights (w = 2) */
+    int H, W, conn, kind; /* kind 0 = sum of grey levels, 1 = mask (w = 2), 2 = L1 */
 } or_graph;
 
 static int or_free(const or_graph *g, int p) {
-    return g->kind == 0 || g->mask == NULL || g->mask[p] != 0;
+    return g->kind != 1 || g->mask == NULL || g->mask[p] != 0;
 }
 
 /* Neighbours of p in increasing linear index. Only free neighbours of a free
@@ -74,9 +74,12 @@ static int or_neighbours(const or_graph *g, int p, int *out) {
 }
 
 /* Edge weight: sum of grey levels plus one (Sec. 2, eq. "distance somme",
- * with +1), or 2 between free pixels of a mask. */
+ * with +1), 2 between free pixels of a mask, or the absolute difference of
+ * grey levels plus one (Sec. 2, pseudo-metric L1, eq. "distance abs
+ * difference", with +1 so that every edge costs at least 1). */
 static uint32_t or_weight(const or_graph *g, int p, int q) {
     if (g->kind == 1) return 2u;
+    if (g->kind == 2) return (uint32_t)(g->f[p] > g->f[q] ? g->f[p] - g->f[q] : g->f[q] - g->f[p]) + 1u;
     return (uint32_t)g->f[p] + (uint32_t)g->f[q] + 1u;
 }
 

@@ -102,6 +102,75 @@ def test_floyd_warshall_mask(conn):
     assert np.array_equal(a, b)
 
 
+def _brute_force_l1(img, conn):
+    """Minimum over all simple paths of the L1 weights |f(p) - f(q)| + 1."""
+    H, W = img.shape
+    N = H * W
+    f = img.reshape(-1).astype(np.int64)
+    D = np.full((N, N), U, dtype=np.uint64)
+    for s in range(N):
+        D[s, s] = 0
+        stack = [(s, 0, 1 << s)]
+        while stack:
+            v, cost, seen = stack.pop()
+            for q in _nbrs(H, W, conn, v):
+                if seen >> q & 1:
+                    continue
+                c2 = cost + int(abs(f[v] - f[q]) + 1)
+                if c2 < D[s, q]:
+                    D[s, q] = c2
+                stack.append((q, c2, seen | (1 << q)))
+    return D.astype(np.uint32)
+
+
+@pytest.mark.parametrize("shape", [(2, 2), (2, 3), (3, 3)])
+@pytest.mark.parametrize("conn", [4, 8])
+def test_l1_brute_force_paths(shape, conn):
+    """Sec. 2, pseudo-metric L1 (eq. 'distance abs difference') with +1 per
+    edge, summed along paths (eq. 'temps') and minimised (eq. 'distance')."""
+    rng = np.random.default_rng(11 + shape[0] * 10 + shape[1] + conn)
+    for _ in range(3):
+        img = rng.integers(0, 256, size=shape).astype(np.uint8)
+        assert np.array_equal(oracle.apsp(img, conn=conn, kind="l1"), _brute_force_l1(img, conn))
+
+
+@pytest.mark.parametrize("W", [1, 2, 9, 40])
+def test_l1_one_row_closed_form(W):
+    """L1 on a 1xW image: the path is unique, so d(i,j) is the total variation
+    of f between i and j plus one per step."""
+    rng = np.random.default_rng(100 + W)
+    f = rng.integers(0, 256, size=W).astype(np.int64)
+    D = oracle.apsp(f.astype(np.uint8).reshape(1, W), conn=4, kind="l1")
+    for i in range(W):
+        for j in range(W):
+            lo, hi = min(i, j), max(i, j)
+            assert D[i, j] == np.abs(np.diff(f[lo:hi + 1])).sum() + (hi - lo)
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_l1_constant_image_and_floyd_warshall(conn):
+    """L1 on a constant image costs one per step (city-block or chessboard);
+    on a random image it agrees with Floyd-Warshall."""
+    H, W = 5, 7
+    D = oracle.apsp(np.full((H, W), 90, dtype=np.uint8), conn=conn, kind="l1")
+    rr, cc = np.divmod(np.arange(H * W), W)
+    dr = np.abs(rr[:, None] - rr[None, :])
+    dc = np.abs(cc[:, None] - cc[None, :])
+    assert np.array_equal(D.astype(np.int64), dr + dc if conn == 4 else np.maximum(dr, dc))
+    img = np.random.default_rng(conn).integers(0, 256, size=(6, 7)).astype(np.uint8)
+    assert np.array_equal(oracle.apsp(img, conn=conn, kind="l1"), oracle.floyd(img, conn=conn, kind="l1"))
+
+
+@pytest.mark.parametrize("order", ["naive", "minfill"])
+def test_l1_fill_invariants(order):
+    """The method is indifferent to the pseudo-metric: with L1 weights the
+    Property-1 array equals the Dijkstra array and every pair is filled."""
+    img = synth.blobs(9, 11, 3, 2.5, 55.0, seed=4)
+    r = oracle.fill(img, order, B=3, conn=8, kind="l1", want_D=True)
+    assert np.array_equal(r.D, oracle.apsp(img, conn=8, kind="l1"))
+    assert r.new_pairs == 99 * 98 // 2
+
+
 @pytest.mark.parametrize("W", [1, 2, 9, 40])
 def test_one_row_closed_form(W):
     """Eq. 'distance geo somme' with the +1 per edge: on a 1xW image the path
