@@ -78,8 +78,9 @@ typedef enum {
 } gapsp_order;
 
 typedef enum {
-    GAPSP_GREY = 0, /* w(p,q) = f(p) + f(q) + 1 */
-    GAPSP_MASK = 1  /* w = 2 between free pixels; obstacles have no edges */
+    GAPSP_GREY = 0, /* w(p,q) = f(p) + f(q) + 1: sum of grey levels (Sec. 2, eq. "distance somme") */
+    GAPSP_MASK = 1, /* w = 2 between free pixels; obstacles have no edges */
+    GAPSP_L1 = 2    /* w(p,q) = |f(p) - f(q)| + 1: pseudo-metric L1 (Sec. 2, eq. "distance abs difference") */
 } gapsp_kind;
 
 typedef struct {
@@ -134,10 +135,10 @@ void gapsp_default_opts(gapsp_opts *opts);
  *   img  : H*W uint8 grey levels, row-major, host or device pointer; read
  *          during the call only (copied).
  *   mask : H*W uint8, 1 = free pixel, 0 = obstacle; host or device; required
- *          for GAPSP_MASK and ignored for GAPSP_GREY.
+ *          for GAPSP_MASK and ignored for GAPSP_GREY and GAPSP_L1.
  *   H, W : 1..GAPSP_MAX_SIDE each, H*W <= GAPSP_MAX_N.
- * The handle owns a device copy of the image, its per-line weight prefix
- * sums and the bookkeeping arrays (marks, fill counts). On error *out is
+ * The handle owns a device copy of the image, its tile geometry and the
+ * bookkeeping arrays (marks, fill counts). On error *out is
  * NULL and nothing is allocated.
  */
 gapsp_status gapsp_create(const uint8_t *img, int H, int W, const uint8_t *mask,
@@ -226,7 +227,7 @@ gapsp_status gapsp_profile_trace(gapsp_handle *h, double *ms, uint64_t *launches
  * device copy of the source list and a status word) is one fixed array of
  * GAPSP_NOALLOC_MAX_SOURCES * 4 + 256 bytes that every GPU loading the
  * library holds until the process exits.
- *   img     : H*W uint8, DEVICE pointer: grey levels (GAPSP_GREY) or free
+ *   img     : H*W uint8, DEVICE pointer: grey levels (GAPSP_GREY, GAPSP_L1) or free
  *             flags, nonzero = free (GAPSP_MASK).
  *   sources : K int32 pixel indices, host or device pointer.
  *   out     : caller-owned DEVICE uint32 K*N; out[k*N + q] = d(sources[k], q).

@@ -19,7 +19,7 @@ from . import _build
 
 UNREACH = 0xFFFFFFFF
 ORDERS = {"naive": 0, "spiral": 1, "minfill": 2, "extrema": 3, "repulsion": 4}
-KINDS = {"grey": 0, "mask": 1}
+KINDS = {"grey": 0, "mask": 1, "l1": 2}
 KERNELS = ("select", "propagate", "tree", "lookahead", "fill", "init", "prepass", "depths", "recount")
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "memory budget exceeded",
           4: "CUDA runtime error", 5: "propagation did not converge", 6: "round limit exceeded",
@@ -179,7 +179,7 @@ class Image:
         lib = load()
         self._lib = lib
         self._h = ctypes.c_void_p()
-        if kind == "grey":
+        if kind != "mask":
             img_a = img if hasattr(img, "data_ptr") else np.ascontiguousarray(img, dtype=np.uint8)
             H, W = int(img_a.shape[0]), int(img_a.shape[1])
         else:

@@ -364,14 +364,14 @@ gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask,
     if (o.B == 0) o.B = 32;
     if (H < 1 || W < 1 || H > GAPSP_MAX_SIDE || W > GAPSP_MAX_SIDE || H * W > GAPSP_MAX_N) return GAPSP_E_INVALID;
     if (o.conn != 4 && o.conn != 8) return GAPSP_E_INVALID;
-    if (o.kind != GAPSP_GREY && o.kind != GAPSP_MASK) return GAPSP_E_INVALID;
+    if (o.kind != GAPSP_GREY && o.kind != GAPSP_MASK && o.kind != GAPSP_L1) return GAPSP_E_INVALID;
     if (o.B < 1 || o.B > 1024) return GAPSP_E_INVALID;
     if (o.sweep_phases < 0 || o.sweep_phases > 4 || o.sweep_phases == 3) return GAPSP_E_INVALID;
     if (o.fill_rows < 0 || o.fill_rows > 32) return GAPSP_E_INVALID;
     if (o.prop_blocks != 0 && o.prop_blocks != 1 && o.prop_blocks != 2 && o.prop_blocks != 4)
         return GAPSP_E_INVALID;
     if (o.lookahead < -1 || o.lookahead > 1024) return GAPSP_E_INVALID;
-    if (o.kind == GAPSP_GREY && !img) return GAPSP_E_INVALID;
+    if (o.kind != GAPSP_MASK && !img) return GAPSP_E_INVALID;
     if (o.kind == GAPSP_MASK && !mask) return GAPSP_E_INVALID;
 
     gapsp_handle* h = new (std::nothrow) gapsp_handle();
@@ -410,7 +410,7 @@ gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask,
     if ((e = cudaEventCreate(&h->ev0)) != cudaSuccess) return fail(e);
     if ((e = cudaEventCreate(&h->ev1)) != cudaSuccess) return fail(e);
     // the kernels read grey levels (grey) or free flags (mask) from h->f
-    const uint8_t* srcimg = o.kind == GAPSP_GREY ? img : mask;
+    const uint8_t* srcimg = o.kind == GAPSP_MASK ? mask : img;
     if ((e = cudaMemcpyAsync(h->f, srcimg, N, cudaMemcpyDefault, h->st)) != cudaSuccess) return fail(e);
     if ((e = cudaMemsetAsync(h->status, 0, sizeof(int), h->st)) != cudaSuccess) return fail(e);
     if (o.kind == GAPSP_MASK) {

@@ -65,7 +65,7 @@ extern "C" gapsp_status gapsp_rows_noalloc(const uint8_t* img, int H, int W, int
                                            const int32_t* sources, int K, uint32_t* out, void* stream) {
     if (H < 1 || W < 1 || H > GAPSP_MAX_SIDE || W > GAPSP_MAX_SIDE || H * W > GAPSP_MAX_N) return GAPSP_E_INVALID;
     if (conn != 4 && conn != 8) return GAPSP_E_INVALID;
-    if (kind != GAPSP_GREY && kind != GAPSP_MASK) return GAPSP_E_INVALID;
+    if (kind != GAPSP_GREY && kind != GAPSP_MASK && kind != GAPSP_L1) return GAPSP_E_INVALID;
     if (K < 0 || K > GAPSP_NOALLOC_MAX_SOURCES) return GAPSP_E_INVALID;
     if (K == 0) return GAPSP_OK;
     if (!img || !sources || !out) return GAPSP_E_INVALID;

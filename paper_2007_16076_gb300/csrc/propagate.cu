@@ -3,7 +3,8 @@
 // Computes d(s, .) = min over paths of the summed edge weights (Sec. 2, eqs.
 // "temps" and "distance"), the "geodesic time function" of Soille that the
 // paper uses with a 3x3 neighbourhood (Sec. 3). Weights are w(p,q) = f(p) +
-// f(q) + 1 (grey) or 2 between free pixels (mask).
+// f(q) + 1 (grey: the sum of grey levels), |f(p) - f(q)| + 1 (the L1
+// pseudo-metric) or 2 between free pixels (mask). KIND 0 / 2 / 1.
 //
 // One block owns one source (or one multi-source seed set). Its distance
 // map sits in shared memory (global memory for images too large), set to 0
@@ -116,10 +117,14 @@ __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int d
     uint8_t* ch_x = (ROWS ? sh.chC : sh.chR) + (round % 3) * len;
     const uint8_t* prev_own = (ROWS ? sh.chR : sh.chC) + ((round + 2) % 3) * nlines;
     const int wrap_at = dir > 0 ? 0 : nlines - 1;  // a sweep restarts here
-    // gp[k]: cost of leaving the previous line's pixel, d + f (grey) or d (mask)
-    int gp[VPL];
+    // gp[k]: cost of leaving the previous line's pixel, d + f (grey) or d
+    // (mask, L1); gf[k]: its grey level (L1)
+    int gp[VPL], gf[VPL];
 #pragma unroll
-    for (int k = 0; k < VPL; ++k) gp[k] = PINF;
+    for (int k = 0; k < VPL; ++k) {
+        gp[k] = PINF;
+        gf[k] = 0;
+    }
     bool has_pred = false;      // this line has a previous line in the sweep
     bool pred_changed = false;  // the previous line changed (it must be relaxed from)
     bool changed = false;
@@ -151,7 +156,8 @@ __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int d
                         const int pos = VPL * lane + k;
                         const int dv = pos < len ? *((volatile const int*)(rmap + rrow * rpitch + pos)) : PINF;
                         const int fg = pos < len ? (int)__ldg(a.f + grow * a.W + pos) : 0;
-                        gp[k] = KIND == 0 ? (pos < len ? dv + fg : dv) : (fg ? dv : PINF);
+                        gp[k] = KIND == 0 ? (pos < len ? dv + fg : dv) : KIND == 2 ? dv : (fg ? dv : PINF);
+                        gf[k] = fg;
                     }
                 }
             }
@@ -167,7 +173,8 @@ __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int d
                 const int pos = VPL * lane + k;
                 const int dv = (EX || pos < len) ? (ROWS ? map.ld(lp, pos) : map.ld(pos, lp)) : PINF;
                 const int fp = (EX || pos < len) ? (int)f_line[lp * len + pos] : 0;
-                gp[k] = KIND == 0 ? dv + fp : (fp ? dv : PINF);
+                gp[k] = KIND == 0 ? dv + fp : KIND == 2 ? dv : (fp ? dv : PINF);
+                gf[k] = fp;
             }
         }
         // lowered in the previous round, or already in this one (seen so far);
@@ -186,7 +193,8 @@ __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int d
             for (int k = 0; k < VPL; ++k) {
                 const int pos = VPL * lane + k;
                 const int dv = (EX || pos < len) ? (ROWS ? map.ld(l, pos) : map.ld(pos, l)) : PINF;
-                gp[k] = KIND == 0 ? dv + fc[k] : (fc[k] ? dv : PINF);
+                gp[k] = KIND == 0 ? dv + fc[k] : KIND == 2 ? dv : (fc[k] ? dv : PINF);
+                gf[k] = fc[k];
             }
             has_pred = true;
             pred_changed = false;
@@ -202,39 +210,55 @@ __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int d
             const int pos = VPL * lane + k;
             const bool valid = EX || pos < len;
             o[k] = valid ? (ROWS ? map.ld(l, pos) : map.ld(pos, l)) : PINF;
-            freep[k] = valid && (KIND == 0 || fc[k] != 0);
+            freep[k] = valid && (KIND != 1 || fc[k] != 0);
         }
-        if (KIND == 0) {
-            // prefix of the line's edge weights f(c) + f(c+1) + 1 from the
-            // lane's first pixel (only differences inside a lane are used)
+        if (KIND == 0 || KIND == 2) {
+            // prefix of the line's edge weights from the lane's first pixel
+            // (only differences inside a lane are used)
             int acc = 0;
 #pragma unroll
             for (int k = 0; k < VPL; ++k) {
                 p[k] = acc;
-                if (k + 1 < VPL) acc += fc[k] + fc[k + 1] + 1;
+                if (k + 1 < VPL) acc += (KIND == 0 ? fc[k] + fc[k + 1] : abs(fc[k + 1] - fc[k])) + 1;
             }
         } else {
 #pragma unroll
             for (int k = 0; k < VPL; ++k) p[k] = 2 * k;
         }
         // 1. relax from the previous line
-        int gl0 = PINF, gr0 = PINF;
+        int gl0 = PINF, gr0 = PINF, fl0 = 0, fr0 = 0;
         if (CONN == 8) {
             gl0 = __shfl_up_sync(FULL, gp[VPL - 1], 1);
             gr0 = __shfl_down_sync(FULL, gp[0], 1);
+            if (KIND == 2) {
+                fl0 = __shfl_up_sync(FULL, gf[VPL - 1], 1);
+                fr0 = __shfl_down_sync(FULL, gf[0], 1);
+            }
             if (lane == 0) gl0 = PINF;
             if (lane == 31) gr0 = PINF;
         }
         int v[VPL];
 #pragma unroll
         for (int k = 0; k < VPL; ++k) {
-            int g = gp[k];
-            if (CONN == 8) {
-                const int gl = k > 0 ? gp[k - 1] : gl0;
-                const int gr = k + 1 < VPL ? gp[k + 1] : gr0;
-                g = min(g, min(gl, gr));
+            int best;
+            if (KIND == 2) {
+                // L1: the weight depends on both ends of the edge
+                int g = gp[k] + abs(gf[k] - fc[k]) + 1;
+                if (CONN == 8) {
+                    const int gl = k > 0 ? gp[k - 1] : gl0, fl = k > 0 ? gf[k - 1] : fl0;
+                    const int gr = k + 1 < VPL ? gp[k + 1] : gr0, fr = k + 1 < VPL ? gf[k + 1] : fr0;
+                    g = min(g, min(gl + abs(fl - fc[k]) + 1, gr + abs(fr - fc[k]) + 1));
+                }
+                best = min(o[k], g);
+            } else {
+                int g = gp[k];
+                if (CONN == 8) {
+                    const int gl = k > 0 ? gp[k - 1] : gl0;
+                    const int gr = k + 1 < VPL ? gp[k + 1] : gr0;
+                    g = min(g, min(gl, gr));
+                }
+                best = min(o[k], g + (KIND == 0 ? fc[k] + 1 : 2));
             }
-            const int best = min(o[k], g + (KIND == 0 ? fc[k] + 1 : 2));
             v[k] = freep[k] ? best : PINF;
         }
         // 2. close the line inside each lane
@@ -264,6 +288,7 @@ __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int d
                 else map.lower(pos, l, d[k]);
             }
             gp[k] = KIND == 0 ? d[k] + fc[k] : d[k];
+            gf[k] = fc[k];
         }
         ++nproc;
         if (mine) {
@@ -603,8 +628,12 @@ cudaError_t launch_propagate(const PropArgs& a, int conn, int kind, int grid, in
     const int vpl = prop_vpl(a.H > a.W ? a.H : a.W);
     const int jobs = grid * wpb;  // one block per job
     if (jobs <= 0) return cudaSuccess;
-    if (conn == 8) return kind == 0 ? launch_vpl<8, 0>(a, vpl, jobs, st) : launch_vpl<8, 1>(a, vpl, jobs, st);
-    return kind == 0 ? launch_vpl<4, 0>(a, vpl, jobs, st) : launch_vpl<4, 1>(a, vpl, jobs, st);
+    if (conn == 8) {
+        if (kind == 0) return launch_vpl<8, 0>(a, vpl, jobs, st);
+        return kind == 1 ? launch_vpl<8, 1>(a, vpl, jobs, st) : launch_vpl<8, 2>(a, vpl, jobs, st);
+    }
+    if (kind == 0) return launch_vpl<4, 0>(a, vpl, jobs, st);
+    return kind == 1 ? launch_vpl<4, 1>(a, vpl, jobs, st) : launch_vpl<4, 2>(a, vpl, jobs, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -634,7 +663,7 @@ __global__ void k_boundary(ImagePrep p) {
     int N = p.H * p.W;
     if (q >= N) return;
     int r = q / p.W, c = q - r * p.W;
-    bool fr = p.kind == 0 || p.f[q];
+    bool fr = p.kind != 1 || p.f[q];
     int n = 0;
     for (int dr = -1; dr <= 1; ++dr)
         for (int dc = -1; dc <= 1; ++dc) {

@@ -52,11 +52,14 @@ __device__ __forceinline__ int canonical_parent(const TreeArgs& a, const uint32_
     if (b == s || db == UNREACH) return -1;
     const int W = a.W;
     const int r = row_of(a, b), c = b - r * W;
-    const uint32_t fb = a.kind == 0 ? (uint32_t)fs[b] + 1u : 2u;  // w(q,b) = f(q) + fb, or 2
+    const int f_b = fs[b];
+    // w(q,b): f(q) + f(b) + 1 (sum), |f(q) - f(b)| + 1 (L1), 2 (mask)
     auto tight = [&](int q) {
         if (a.kind == 1 && !fs[q]) return false;
         const uint32_t dq = drow[q];
-        return dq != UNREACH && dq + (a.kind == 0 ? (uint32_t)fs[q] + fb : 2u) == db;
+        const int fq = fs[q];
+        const uint32_t w = a.kind == 0 ? (uint32_t)(fq + f_b + 1) : a.kind == 2 ? (uint32_t)(abs(fq - f_b) + 1) : 2u;
+        return dq != UNREACH && dq + w == db;
     };
     if (r > 0 && r + 1 < a.H && c > 0 && c + 1 < W) {
         // interior pixel: no bounds tests

@@ -70,6 +70,27 @@ def test_rows_mask(gp, shape, conn):
     assert np.array_equal(out, ref)
 
 
+@pytest.mark.parametrize("shape", [(1, 9), (7, 13), (33, 45), (128, 128), (100, 37)], ids=lambda s: f"{s[0]}x{s[1]}")
+@pytest.mark.parametrize("conn", [4, 8])
+def test_rows_l1(gp, shape, conn):
+    """The L1 pseudo-metric (Sec. 2): w = |f(p) - f(q)| + 1."""
+    H, W = shape
+    img = synth.blobs(H, W, max(1, H * W // 300), max(1.5, (H + W) / 16), 55.0, seed=H * 5 + W)
+    N = H * W
+    rng = np.random.default_rng(N + conn)
+    src = np.unique(np.concatenate([[0, N - 1], rng.integers(0, N, size=min(N, 20))])).astype(np.int32)
+    with gp.Image(img, conn=conn, kind="l1") as im:
+        out = _u32(im.rows(src))
+    assert np.array_equal(out, oracle.rows(img, src, conn=conn, kind="l1"))
+
+
+@pytest.mark.parametrize("order", ["naive", "spiral", "repulsion", "extrema", "minfill"])
+@pytest.mark.parametrize("conn", [4, 8])
+def test_all_pairs_l1(gp, order, conn):
+    img = synth.blobs(17, 23, 3, 2.5, 55.0, seed=conn)
+    _check_fill(gp, img, order, 5, conn, kind="l1")
+
+
 def test_rows_structured_images(gp):
     """Winding corridors and step edges need many sweeps; uniform noise and
     constant images are the other extremes."""
