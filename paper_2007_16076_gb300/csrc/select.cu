@@ -441,6 +441,78 @@ __global__ void k_centroid_mark(ExtremaArgs a) {
     if (c >= 0 && c < a.N) a.cen_flags[c] = 1;
 }
 
+// The same ranks by sorting, for N <= 16384 (one block): the keys
+// (~g, p) of the free pixels are bitonic-sorted in shared memory; a pixel's
+// rank is its position, and the number of free pixels strictly farther from
+// the centroid is the position where its run of equal distances starts.
+constexpr int RANK_THREADS = 1024;
+
+__global__ void __launch_bounds__(RANK_THREADS) k_rank_sort(ExtremaArgs a) {
+    extern __shared__ unsigned long long rk[];
+    __shared__ int s_wmax[RANK_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int n2 = 1;
+    while (n2 < a.N) n2 <<= 1;
+    for (int i = tid; i < n2; i += RANK_THREADS) {
+        unsigned long long k = ~0ull;
+        if (i < a.N) {
+            a.rank[i] = -1;
+            a.grank[i] = -1;
+            if (!a.freef || a.freef[i]) k = ((unsigned long long)(~a.g[i]) << 32) | (unsigned)i;
+        }
+        rk[i] = k;
+    }
+    __syncthreads();
+    for (int k = 2; k <= n2; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < n2; i += RANK_THREADS) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const unsigned long long x = rk[i], y = rk[ixj];
+                    if ((x > y) == ((i & k) == 0)) {
+                        rk[i] = y;
+                        rk[ixj] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    // each thread owns a contiguous block of positions: run starts, then a
+    // block-wide max-scan of them
+    const int per = (n2 + RANK_THREADS - 1) / RANK_THREADS;
+    const int i0 = tid * per, i1 = min(i0 + per, n2);
+    int run = -1;
+    for (int i = i0; i < i1; ++i)
+        if (rk[i] != ~0ull && (i == 0 || (rk[i - 1] >> 32) != (rk[i] >> 32))) run = i;
+    int x = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x = max(x, t);
+    }
+    if (lane == 31) s_wmax[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = s_wmax[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, w, o);
+            if (lane >= o) w = max(w, t);
+        }
+        s_wmax[lane] = w;
+    }
+    __syncthreads();
+    int cur = __shfl_up_sync(FULL, x, 1);  // max over earlier threads of this warp
+    if (lane == 0) cur = -1;
+    if (warp > 0) cur = max(cur, s_wmax[warp - 1]);
+    for (int i = i0; i < i1; ++i) {
+        const unsigned long long k = rk[i];
+        if (k == ~0ull) break;  // the keys of obstacles and padding come last
+        if (i == 0 || (rk[i - 1] >> 32) != (k >> 32)) cur = i;
+        const int p = (int)(k & 0xFFFFFFFFu);
+        a.rank[p] = i;
+        a.grank[p] = cur;
+    }
+}
+
 // Position in the extrema list Ext: free pixels by decreasing distance from
 // the centroid, ties by increasing index; and the number of free pixels
 // strictly farther from the centroid. Counted directly.
@@ -560,7 +632,18 @@ cudaError_t launch_centroids(const ExtremaArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_rank(const ExtremaArgs& a, cudaStream_t st) {
-    k_rank<<<(a.N + 255) / 256, 256, 0, st>>>(a);
+    if (a.N <= 16384) {
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_rank_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 8);
+            attr = true;
+        }
+        int n2 = 1;
+        while (n2 < a.N) n2 <<= 1;
+        k_rank_sort<<<1, RANK_THREADS, (size_t)n2 * 8, st>>>(a);
+    } else {
+        k_rank<<<(a.N + 255) / 256, 256, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
