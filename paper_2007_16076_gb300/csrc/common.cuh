@@ -34,6 +34,15 @@ enum StatSlot {
 // word (r/8)*tiles_w + c/8 of row b says whether the pair {b, (r,c)} is
 // filled.
 
+// Programmatic dependent launch: a kernel launched after another on the
+// same stream with the programmatic-serialization attribute may start while
+// its predecessor drains; it waits here before touching the predecessor's
+// results (a no-op for a kernel launched without the attribute). The trigger
+// lets the successor's blocks be scheduled once every block of this kernel
+// has started.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ int ld_cg(const int* p) {
     int v;
     asm volatile("ld.global.cg.s32 %0, [%1];" : "=r"(v) : "l"(p));

@@ -758,6 +758,14 @@ gapsp_status fill_enqueue(FillRun& r, int chunk) {
             r.sa.cand = h->cand + par * 1024;
             r.sa.ncand = h->ncand + par;
         }
+        if (r.stat) {
+            // this round hands its trees to k_depths through the buffer of
+            // its parity, once the launch that read it two rounds ago is done
+            r.ta.dep_exit = h->dep_exit + (size_t)par * h->B * h->N;
+            r.ta.dep_size = h->dep_size + (size_t)par * h->B * h->N;
+            r.ta.dep_count = h->dep_count + par;
+            CK(cudaStreamWaitEvent(s, r.e_depth[par], 0));
+        }
         {
             ProfScope ps(h, K_SELECT, s);
             if (r.order == GAPSP_REPULSION) CK(launch_select_repulsion(r.sa, r.ra, s));
@@ -786,17 +794,20 @@ gapsp_status fill_enqueue(FillRun& r, int chunk) {
             ProfScope ps(h, K_PROP, s);
             CK(launch_propagate(r.pa, h->conn, h->kind, h->B, 1, s));
         }
-        if (r.stat) {
-            // hand the trees to k_depths through the buffer of this parity,
-            // once the launch that read it two rounds ago is done
-            r.ta.dep_exit = h->dep_exit + (size_t)par * h->B * h->N;
-            r.ta.dep_size = h->dep_size + (size_t)par * h->B * h->N;
-            r.ta.dep_count = h->dep_count + par;
-            CK(cudaStreamWaitEvent(s, r.e_depth[par], 0));
-        }
+        // propagation, tree, fill and recount follow each other directly on
+        // the stream: each later one is a programmatic dependent launch that
+        // may be scheduled while the one before drains
         {
             ProfScope ps(h, K_TREE, s);
-            CK(launch_tree(r.ta, h->B, s));
+            CK(launch_tree(r.ta, h->B, s, true));
+        }
+        {
+            ProfScope ps(h, K_FILL, s);
+            CK(launch_fill(r.ta, h->B, s, true));
+        }
+        {
+            ProfScope ps(h, K_RECOUNT, s);
+            CK(launch_recount(r.ta, s, true));
         }
         if (r.stat) {
             CK(cudaEventRecord(r.e_tree[par], s));
@@ -807,14 +818,6 @@ gapsp_status fill_enqueue(FillRun& r, int chunk) {
             }
             CK(cudaEventRecord(r.e_depth[par], r.stat));
             h->launches += 1;
-        }
-        {
-            ProfScope ps(h, K_FILL, s);
-            CK(launch_fill(r.ta, h->B, s));
-        }
-        {
-            ProfScope ps(h, K_RECOUNT, s);
-            CK(launch_recount(r.ta, s));
         }
         h->launches += 5;
     }

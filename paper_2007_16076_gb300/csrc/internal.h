@@ -73,11 +73,12 @@ struct TreeArgs {
     uint16_t* dep_size;         // [B][N]
     int* dep_count;
 };
-cudaError_t launch_tree(const TreeArgs& a, int B, cudaStream_t st);
+// pdl: launched as a programmatic dependent of the previous kernel on st
+cudaError_t launch_tree(const TreeArgs& a, int B, cudaStream_t st, bool pdl = false);
 // Distance operations of the trees handed over by a tree launch (N <= 16384).
 cudaError_t launch_depths(const TreeArgs& a, int B, cudaStream_t st);
-cudaError_t launch_fill(const TreeArgs& a, int B, cudaStream_t st);
-cudaError_t launch_recount(const TreeArgs& a, cudaStream_t st);
+cudaError_t launch_fill(const TreeArgs& a, int B, cudaStream_t st, bool pdl = false);
+cudaError_t launch_recount(const TreeArgs& a, cudaStream_t st, bool pdl = false);
 
 struct SelectArgs {
     int N, B, order;            // 0 naive / 1 spiral (sequence), 2 minfill, 3 extrema

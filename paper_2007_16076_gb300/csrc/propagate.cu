@@ -421,6 +421,7 @@ __device__ void flag_seed_lines(const PropArgs& a, const Shared& sh, int src) {
 template <int CONN, int KIND, int VPL, bool CL, bool EX>
 __global__ void __launch_bounds__(32 * MAXWARPS) k_propagate_smem(PropArgs a, int pitch, int C) {
     extern __shared__ int smap[];
+    pdl_trigger();  // the tree launch that follows may be scheduled
     __shared__ int s_flag[2], s_rounds;
     const int j = blockIdx.x / C, rank = blockIdx.x % C;
     const int njobs = a.njobs_dev ? *a.njobs_dev : a.njobs;
@@ -496,6 +497,7 @@ __global__ void __launch_bounds__(32 * MAXWARPS) k_propagate_smem(PropArgs a, in
 template <int CONN, int KIND, int VPL>
 __global__ void __launch_bounds__(32 * MAXWARPS) k_propagate_glob(PropArgs a) {
     extern __shared__ int sbuf[];
+    pdl_trigger();
     __shared__ int s_flag[2], s_rounds;
     const int j = blockIdx.x;
     const int njobs = a.njobs_dev ? *a.njobs_dev : a.njobs;

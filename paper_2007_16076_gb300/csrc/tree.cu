@@ -103,6 +103,8 @@ __device__ __forceinline__ int canonical_parent(const TreeArgs& a, const uint32_
 template <bool SMALL>
 __global__ void __launch_bounds__(1024) k_tree(TreeArgs a) {
     extern __shared__ uint16_t sdep[];
+    pdl_wait();
+    pdl_trigger();
     __shared__ int s_any[2];
     const int j = blockIdx.x, B = gridDim.x;
     // the number of trees handed to k_depths (also when there are none)
@@ -257,6 +259,8 @@ struct Tree2Layout {
 
 __global__ void __launch_bounds__(1024) k_tree2(TreeArgs a) {
     extern __shared__ __align__(16) unsigned char sm2[];
+    pdl_wait();
+    pdl_trigger();
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int j = blockIdx.x >> 1;
@@ -389,6 +393,8 @@ __global__ void __launch_bounds__(1024) k_depths(TreeArgs a) {
 // counts come from the marks (k_recount), which hold each pair once per row.
 __global__ void k_fill(TreeArgs a) {
     extern __shared__ unsigned long long srow[];
+    pdl_wait();
+    pdl_trigger();
     __shared__ int s_rows[32], s_tile[32], s_bit[32];
     __shared__ int s_nu;
     __shared__ unsigned s_gain;  // bit i: row s_rows[i] gained marks
@@ -522,6 +528,7 @@ __global__ void k_fill(TreeArgs a) {
 // summed into S_NEW, which thus counts every new pair twice.
 __global__ void k_recount(TreeArgs a) {
     __shared__ unsigned long long s_sum;
+    pdl_wait();
     if (threadIdx.x == 0) s_sum = 0;
     __syncthreads();
     const int x = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -544,34 +551,49 @@ __global__ void k_recount(TreeArgs a) {
 
 }  // namespace
 
-cudaError_t launch_recount(const TreeArgs& a, cudaStream_t st) {
-    k_recount<<<(a.N + 7) / 8, 256, 0, st>>>(a);
-    return cudaGetLastError();
+// cudaLaunchKernelEx with an optional cluster size and the programmatic
+// dependent launch attribute.
+template <typename... KArgs>
+cudaError_t launch_ex(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t st, bool pdl,
+                      int cluster, const TreeArgs& a) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[2];
+    int n = 0;
+    if (cluster > 1) {
+        at[n].id = cudaLaunchAttributeClusterDimension;
+        at[n].val.clusterDim.x = cluster;
+        at[n].val.clusterDim.y = 1;
+        at[n].val.clusterDim.z = 1;
+        ++n;
+    }
+    if (pdl) {
+        at[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[n].val.programmaticStreamSerializationAllowed = 1;
+        ++n;
+    }
+    cfg.attrs = at;
+    cfg.numAttrs = n;
+    return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-cudaError_t launch_tree(const TreeArgs& a, int B, cudaStream_t st) {
+cudaError_t launch_recount(const TreeArgs& a, cudaStream_t st, bool pdl) {
+    return launch_ex(k_recount, (a.N + 7) / 8, 256, 0, st, pdl, 1, a);
+}
+
+cudaError_t launch_tree(const TreeArgs& a, int B, cudaStream_t st, bool pdl) {
     if (a.N <= 16384 && a.dep_exit && a.H >= 16) {
         // two blocks (one cluster) per tree
         const Tree2Layout L(a.H, a.W);
-        const size_t smem = L.bytes();
         static bool attr = false;
         if (!attr) {
             cudaFuncSetAttribute(k_tree2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
             attr = true;
         }
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(2 * B);
-        cfg.blockDim = dim3(1024);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = st;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = 2;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, k_tree2, a);
+        return launch_ex(k_tree2, 2 * B, 1024, L.bytes(), st, pdl, 2, a);
     }
     if (a.N <= 16384) {
         static bool attr = false;
@@ -580,11 +602,9 @@ cudaError_t launch_tree(const TreeArgs& a, int B, cudaStream_t st) {
             attr = true;
         }
         // five 16-bit arrays and the image
-        k_tree<true><<<B, 1024, (size_t)a.N * 11, st>>>(a);
-    } else {
-        k_tree<false><<<B, 1024, 0, st>>>(a);
+        return launch_ex(k_tree<true>, B, 1024, (size_t)a.N * 11, st, pdl, 1, a);
     }
-    return cudaGetLastError();
+    return launch_ex(k_tree<false>, B, 1024, 0, st, pdl, 1, a);
 }
 
 cudaError_t launch_depths(const TreeArgs& a, int B, cudaStream_t st) {
@@ -597,7 +617,7 @@ cudaError_t launch_depths(const TreeArgs& a, int B, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_fill(const TreeArgs& a, int B, cudaStream_t st) {
+cudaError_t launch_fill(const TreeArgs& a, int B, cudaStream_t st, bool pdl) {
     (void)B;
     // mark rows, then one "changed" byte per row word
     const size_t smem = (size_t)a.rows_per_block * a.words * (sizeof(unsigned long long) + 1);
@@ -607,8 +627,7 @@ cudaError_t launch_fill(const TreeArgs& a, int B, cudaStream_t st) {
         attr_set = true;
     }
     const int grid = (a.N + a.rows_per_block - 1) / a.rows_per_block;
-    k_fill<<<grid, 256, smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_ex(k_fill, grid, 256, smem, st, pdl, 1, a);
 }
 
 }  // namespace gapsp
