@@ -60,6 +60,7 @@ struct gapsp_handle {
     int32_t* rank = nullptr;
     int32_t* grank = nullptr;
     uint8_t* row_done = nullptr;  // [N]: row already written by a propagation
+    uint8_t* row_claim = nullptr; // [N]: row handed to a lookahead launch (done or in flight)
     int32_t* rp_ring = nullptr;   // spiral with repulsion: turns, S, draw state
     int32_t* rp_fstart = nullptr;
     uint8_t* rp_fcyc = nullptr;
@@ -215,7 +216,7 @@ size_t fill_state_bytes(const gapsp_handle* h) {
     // rank, grank, round_new, sel_log, emap, gmap, best, cen, row_done per
     // point; the lookahead candidate buffers
     return N * h->words * 8 + B * N * (4 + 16 + 8 + 8) +
-           N * (4 + 4 + 1 + 4 + 4 + 4 + 8 + 4 + 4 + 4 + 8 + 1 + 1 + 4 + 4 + 1 + 1) + 2 * 1024 * 4 + 4096 +
+           N * (4 + 4 + 1 + 4 + 4 + 4 + 8 + 4 + 4 + 4 + 8 + 1 + 1 + 1 + 4 + 4 + 1 + 1) + 2 * 1024 * 4 + 4096 +
            (N <= 16384 ? 8 * B * N : 0);  // trees handed to k_depths
 }
 
@@ -238,6 +239,7 @@ gapsp_status ensure_fill_state(gapsp_handle* h) {
     CK(dalloc(&h->rank, N));
     CK(dalloc(&h->grank, N));
     CK(dalloc(&h->row_done, N));
+    CK(dalloc(&h->row_claim, N));
     CK(dalloc(&h->rp_ring, N));
     CK(dalloc(&h->rp_fstart, N + 2));
     CK(dalloc(&h->rp_fcyc, N + 1));
@@ -269,7 +271,7 @@ void free_all(gapsp_handle* h) {
     dfree(h->comp_size); dfree(h->status); dfree(h->changed);
     dfree(h->cnt); dfree(h->cnt_base); dfree(h->dirty); dfree(h->marks); dfree(h->parent); dfree(h->seg); dfree(h->jmp); dfree(h->acc);
     dfree(h->sel); dfree(h->nsel); dfree(h->cursor); dfree(h->done); dfree(h->seq); dfree(h->rank); dfree(h->grank);
-    dfree(h->row_done); dfree(h->cand); dfree(h->ncand);
+    dfree(h->row_done); dfree(h->row_claim); dfree(h->cand); dfree(h->ncand);
     dfree(h->rp_ring); dfree(h->rp_fstart); dfree(h->rp_fcyc); dfree(h->rp_inS); dfree(h->rp_state);
     dfree(h->rp_taken);
     dfree(h->dep_exit); dfree(h->dep_size); dfree(h->dep_count);
@@ -524,7 +526,7 @@ struct FillRun {
     // second stream while the round's tree and fill run
     int K = 0;
     PropArgs pa_ahead{};
-    cudaStream_t side = nullptr;
+    cudaStream_t side[2] = {nullptr, nullptr};  // lookahead launches of even / odd rounds
     cudaEvent_t e_sel = nullptr;
     cudaEvent_t e_ahead[2] = {nullptr, nullptr};  // lookahead launch of an even / odd round
     // chunks of rounds: the host keeps one chunk queued beyond the one whose
@@ -549,7 +551,8 @@ struct FillRun {
             if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : e_depth)
             if (e) cudaEventDestroy(e);
-        if (side) cudaStreamDestroy(side);
+        for (cudaStream_t x : side)
+            if (x) cudaStreamDestroy(x);
         if (stat) cudaStreamDestroy(stat);
     }
 };
@@ -679,6 +682,7 @@ gapsp_status fill_begin(FillRun& r) {
     }
 
     CK(cudaMemsetAsync(h->row_done, 0, N, s));
+    CK(cudaMemsetAsync(h->row_claim, 0, N, s));
     r.sa = SelectArgs{h->N, h->B, (int)r.order, h->cnt, h->rank, h->grank, h->seq, r.nseq, h->cursor, h->sel, h->nsel,
                       h->stats, h->round_new, h->last_new, h->sel_log, h->done};
     PropArgs& pa = r.pa;
@@ -696,12 +700,14 @@ gapsp_status fill_begin(FillRun& r) {
         r.sa.K = r.K;
         r.sa.KL = 1024 - h->B;
         r.sa.row_done = h->row_done;
+        r.sa.row_claim = h->row_claim;
         r.sa.cand = h->cand;
         r.sa.ncand = h->ncand;
         r.pa_ahead = pa;
         r.pa_ahead.ran = h->stats + S_AHEAD;
         pa.hits = h->stats + S_HITS;
-        CK(cudaStreamCreateWithFlags(&r.side, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&r.side[0], cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&r.side[1], cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&r.e_sel, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&r.e_ahead[0], cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&r.e_ahead[1], cudaEventDisableTiming));
@@ -772,19 +778,19 @@ gapsp_status fill_enqueue(FillRun& r, int chunk) {
             else CK(launch_select(r.sa, s));
         }
         if (r.K > 0) {
-            // this round's candidates go to the second stream, where they
-            // start as soon as the previous round's lookahead is done (the
-            // kernel skips any row that launch computed meanwhile) ...
+            // this round's candidates go to the lookahead stream of its
+            // parity and start at once, beside the previous round's (the
+            // selection never hands out a row already claimed) ...
             CK(cudaEventRecord(r.e_sel, s));
-            CK(cudaStreamWaitEvent(r.side, r.e_sel, 0));
+            CK(cudaStreamWaitEvent(r.side[par], r.e_sel, 0));
             r.pa_ahead.sources = h->cand + par * 1024;
             r.pa_ahead.map_row = h->cand + par * 1024;
             r.pa_ahead.njobs_dev = h->ncand + par;
             {
-                ProfScope ps(h, K_AHEAD, r.side);
-                CK(launch_propagate(r.pa_ahead, h->conn, h->kind, r.K, 1, r.side));
+                ProfScope ps(h, K_AHEAD, r.side[par]);
+                CK(launch_propagate(r.pa_ahead, h->conn, h->kind, r.K, 1, r.side[par]));
             }
-            CK(cudaEventRecord(r.e_ahead[par], r.side));
+            CK(cudaEventRecord(r.e_ahead[par], r.side[par]));
             h->launches += 1;
             // ... and this round's own propagation waits for the previous
             // round's lookahead, which may have computed its sources

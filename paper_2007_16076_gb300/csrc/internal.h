@@ -101,6 +101,7 @@ struct SelectArgs {
     int KL;                     // ranking positions after the selection they are taken
                                 // from (B + KL <= 1024)
     const uint8_t* row_done;    // [N]: rows already computed
+    uint8_t* row_claim;         // [N]: rows handed to a lookahead launch; set for each candidate
 };
 cudaError_t launch_select(const SelectArgs& a, cudaStream_t st);
 

@@ -58,11 +58,15 @@ __global__ void k_select_seq(SelectArgs a) {
         while (nc < a.K && c2 < lim) {
             const int idx = c2 + lane;
             const int p = idx < lim ? a.seq[idx] : -1;
-            const bool ok = p >= 0 && a.cnt[p] < (uint32_t)a.N && !(a.row_done && a.row_done[p]);
+            const bool ok = p >= 0 && a.cnt[p] < (uint32_t)a.N && !(a.row_done && a.row_done[p]) &&
+                            !(a.row_claim && a.row_claim[p]);
             const unsigned m = __ballot_sync(FULL, ok);
             const int take = min(__popc(m), a.K - nc);
             const int before = __popc(m & ((1u << lane) - 1u));
-            if (ok && before < take) a.cand[nc + before] = p;
+            if (ok && before < take) {
+                a.cand[nc + before] = p;
+                if (a.row_claim) a.row_claim[p] = 1;
+            }
             nc += take;
             c2 += 32;
         }
@@ -236,7 +240,9 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
     // candidates: after the selection, points whose rows are not computed
     // yet; when there are more than K, the K smallest keys among them
     auto cand_key = [&](int i) -> unsigned long long {
-        return (s_keys[i] > t1 && !(a.row_done && a.row_done[s_pix[i]])) ? s_keys[i] : ~0ull;
+        const int p = s_pix[i];
+        const bool taken = (a.row_done && a.row_done[p]) || (a.row_claim && a.row_claim[p]);
+        return (s_keys[i] > t1 && !taken) ? s_keys[i] : ~0ull;
     };
     unsigned long long tk = ~0ull - 1;
     if (a.cand) {
@@ -268,7 +274,10 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
         }
         if (in_cand) {
             const int slot = bc + __popc(mc & below);
-            if (slot < a.K) a.cand[slot] = s_pix[tid];
+            if (slot < a.K) {
+                a.cand[slot] = s_pix[tid];
+                if (a.row_claim) a.row_claim[s_pix[tid]] = 1;
+            }
         }
     }
     __syncthreads();
