@@ -240,41 +240,41 @@ __global__ void __launch_bounds__(1024) k_tree(TreeArgs a) {
     if ((threadIdx.x & 31) == 0 && ops) atomicAdd(a.stats + S_OPS, ops);
 }
 
-// The tree of one selected source on a cluster of two blocks (N <= 16384,
-// H >= 16, depth sums left to k_depths): each block owns half of the rows,
-// cut at a multiple of 8 so that no 8x8 tile is split, with the rows next to
-// its half staged for the parent tests. The second exit of a segment chain
-// may lie in the other half; it is read from the other block's shared
-// memory. Same results as k_tree.
-struct Tree2Layout {
-    int hs, smax, pmax;  // rows of the first half; staged and owned pixels of the larger half
-    __host__ __device__ Tree2Layout(int H, int W) {
-        hs = ((H / 2 + 7) / 8) * 8;
-        const int big = hs > H - hs ? hs : H - hs;
-        smax = (big + 2) * W;
-        pmax = big * W;
+// The tree of one selected source on a cluster of C blocks (N <= 16384,
+// depth sums left to k_depths): each block owns a strip of rows, cut at a
+// multiple of 8 so that no 8x8 tile is split, with the rows next to its strip
+// staged for the parent tests. The second exit of a segment chain may lie in
+// another strip; it is read from that block's shared memory. Same results
+// as k_tree.
+struct TreeCLayout {
+    int hs, smax, pmax;  // rows per strip (the last may be shorter or empty); staged, owned pixels
+    __host__ __device__ TreeCLayout(int H, int W, int C) {
+        hs = (((H + C - 1) / C + 7) / 8) * 8;
+        smax = (hs + 2) * W;
+        pmax = hs * W;
     }
     __host__ __device__ size_t bytes() const { return (size_t)smax * 5 + (size_t)pmax * 6 + 16; }
 };
 
-__global__ void __launch_bounds__(1024) k_tree2(TreeArgs a) {
-    extern __shared__ __align__(16) unsigned char sm2[];
+template <int C>
+__global__ void __launch_bounds__(1024) k_treeC(TreeArgs a) {
+    extern __shared__ __align__(16) unsigned char smc[];
     pdl_wait();
     pdl_trigger();
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
-    const int j = blockIdx.x >> 1;
+    const int j = blockIdx.x / C;
     if (blockIdx.x == 0 && threadIdx.x == 0) *a.dep_count = *a.nsel;
-    if (j >= *a.nsel) return;  // both blocks of the cluster leave together
+    if (j >= *a.nsel) return;  // all blocks of the cluster leave together
     const int N = a.N, W = a.W, H = a.H, s = a.sel[j];
-    const Tree2Layout L(H, W);
-    const int r0 = rank ? L.hs : 0, r1 = rank ? H : L.hs;
+    const TreeCLayout L(H, W, C);
+    const int r0 = min(rank * L.hs, H), r1 = min(r0 + L.hs, H);
     const int hr0 = r0 > 0 ? r0 - 1 : 0, hr1 = r1 < H ? r1 + 1 : H;
-    const int base = hr0 * W, S = (hr1 - hr0) * W;  // staged pixels [base, base + S)
-    const int p0 = r0 * W, P = (r1 - r0) * W;        // owned pixels [p0, p0 + P)
-    uint32_t* srow = reinterpret_cast<uint32_t*>(sm2);
-    uint8_t* sf = sm2 + (size_t)L.smax * 4;
-    uint16_t* spar = reinterpret_cast<uint16_t*>(sm2 + (((size_t)L.smax * 5 + 15) & ~(size_t)15));
+    const int base = hr0 * W, S = r1 > r0 ? (hr1 - hr0) * W : 0;  // staged pixels [base, base + S)
+    const int p0 = r0 * W, P = (r1 - r0) * W;                     // owned pixels [p0, p0 + P)
+    uint32_t* srow = reinterpret_cast<uint32_t*>(smc);
+    uint8_t* sf = smc + (size_t)L.smax * 4;
+    uint16_t* spar = reinterpret_cast<uint16_t*>(smc + (((size_t)L.smax * 5 + 15) & ~(size_t)15));
     uint16_t* acc = spar + L.pmax;
     uint16_t* jx = acc + L.pmax;
     const uint32_t* drow = a.D + (size_t)s * N;
@@ -312,14 +312,18 @@ __global__ void __launch_bounds__(1024) k_tree2(TreeArgs a) {
         acc[i] = reached ? (uint16_t)__popcll(m) : 0;
         jx[i] = reached ? (uint16_t)(x + 1) : 0;
     }
-    cl.sync();  // both halves' exits are complete
-    const uint16_t* jx_other = cl.map_shared_rank(jx, rank ^ 1);
-    const int p0_other = rank ? 0 : L.hs * W;
+    cl.sync();  // every strip's exits are complete
+    const uint16_t* jx_of[C];
+#pragma unroll
+    for (int r = 0; r < C; ++r) jx_of[r] = cl.map_shared_rank(jx, r);
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         const int v = p0 + i;
         const int e1 = (int)jx[i] - 1;
         int e2 = -1;
-        if (e1 >= 0) e2 = (e1 >= p0 && e1 < p0 + P) ? (int)jx[e1 - p0] - 1 : (int)jx_other[e1 - p0_other] - 1;
+        if (e1 >= 0) {
+            const int re = min(row_of(a, e1) / L.hs, C - 1);
+            e2 = (int)jx_of[re][e1 - re * L.hs * W] - 1;
+        }
         unsigned long long y = 0;
         if (e1 >= 0) y = (unsigned long long)(e1 + 1) | ((unsigned long long)(tile_bit(a, e1) >> 8) << 17);
         if (e2 >= 0) y |= ((unsigned long long)(e2 + 1) << 27) | ((unsigned long long)(tile_bit(a, e2) >> 8) << 44);
@@ -327,7 +331,7 @@ __global__ void __launch_bounds__(1024) k_tree2(TreeArgs a) {
         a.dep_exit[(size_t)j * N + v] = jx[i];
         a.dep_size[(size_t)j * N + v] = acc[i];
     }
-    cl.sync();  // no block leaves while the other may read its exits
+    cl.sync();  // no block leaves while another may read its exits
 }
 
 // Distance operations of one tree from its segment exits and sizes (N <=
@@ -586,14 +590,24 @@ cudaError_t launch_recount(const TreeArgs& a, cudaStream_t st, bool pdl) {
 
 cudaError_t launch_tree(const TreeArgs& a, int B, cudaStream_t st, bool pdl) {
     if (a.N <= 16384 && a.dep_exit && a.H >= 16) {
-        // two blocks (one cluster) per tree
-        const Tree2Layout L(a.H, a.W);
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_tree2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            attr = true;
+        // several blocks (one cluster) per tree: four strips when they are
+        // 16 rows or more, else two
+        if (a.H >= 64) {
+            const TreeCLayout L(a.H, a.W, 4);
+            static bool attr4 = false;
+            if (!attr4) {
+                cudaFuncSetAttribute(k_treeC<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                attr4 = true;
+            }
+            return launch_ex(k_treeC<4>, 4 * B, 1024, L.bytes(), st, pdl, 4, a);
         }
-        return launch_ex(k_tree2, 2 * B, 1024, L.bytes(), st, pdl, 2, a);
+        const TreeCLayout L(a.H, a.W, 2);
+        static bool attr2 = false;
+        if (!attr2) {
+            cudaFuncSetAttribute(k_treeC<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr2 = true;
+        }
+        return launch_ex(k_treeC<2>, 2 * B, 1024, L.bytes(), st, pdl, 2, a);
     }
     if (a.N <= 16384) {
         static bool attr = false;
