@@ -103,6 +103,11 @@ typedef struct {
                           at the round's start; a later round whose source was
                           computed ahead skips that propagation. D and every count
                           are the same with or without it. */
+    int warm_start;    /* gapsp_all_pairs: 0 = on, -1 = off. A propagation starts from
+                          the complete rows of its source's filled neighbours q
+                          (d(s,x) <= d(q,s) + d(q,x)) instead of from the source
+                          alone; exact once every neighbour is filled. D and every
+                          count are the same either way. */
 } gapsp_opts;
 
 typedef struct {
@@ -149,10 +154,11 @@ gapsp_status gapsp_create(const uint8_t *img, int H, int W, const uint8_t *mask,
  * propagations from sources chosen in `order`, B per round, plus the
  * geodesic-tree fill of Property 1.
  *   D  : caller-owned uint32 N*N, device pointer or host pointer (a host
- *        array is filled through a device buffer the call allocates).
+ *        array is filled through a device buffer the call allocates). A
+ *        device D must be 16-byte aligned (rows move 16 bytes at a time).
  *   st : may be NULL; otherwise receives the counts, which equal those of
  *        the same order simulated on the CPU.
- * Errors: GAPSP_E_INVALID (order, NULL D), GAPSP_E_BUDGET, GAPSP_E_NOMEM,
+ * Errors: GAPSP_E_INVALID (order, NULL or misaligned D), GAPSP_E_BUDGET, GAPSP_E_NOMEM,
  * GAPSP_E_NOT_CONVERGED, GAPSP_E_TIMEOUT, GAPSP_E_CUDA. On error the content
  * of D is unspecified.
  */
@@ -178,8 +184,10 @@ gapsp_status gapsp_all_pairs_batch(gapsp_handle *const *h, int n, gapsp_order or
  * Single-source propagations (Sec. 1: "geodesic propagation"): out[k*N + q]
  * = d(sources[k], q) for k < K. No tree, marks or selection.
  *   sources : K int32 pixel indices, host or device pointer.
- *   out     : caller-owned uint32 K*N, device or host pointer.
- * Errors: GAPSP_E_INVALID (K < 0, a source outside [0, N), NULL pointers),
+ *   out     : caller-owned uint32 K*N, device or host pointer; a device
+ *             out must be 16-byte aligned.
+ * Errors: GAPSP_E_INVALID (K < 0, a source outside [0, N), NULL pointers, a
+ * misaligned device out),
  * GAPSP_E_BUDGET, GAPSP_E_NOMEM, GAPSP_E_NOT_CONVERGED, GAPSP_E_CUDA. With
  * an invalid source nothing is written.
  */
@@ -230,12 +238,13 @@ gapsp_status gapsp_profile_trace(gapsp_handle *h, double *ms, uint64_t *launches
  *   img     : H*W uint8, DEVICE pointer: grey levels (GAPSP_GREY, GAPSP_L1) or free
  *             flags, nonzero = free (GAPSP_MASK).
  *   sources : K int32 pixel indices, host or device pointer.
- *   out     : caller-owned DEVICE uint32 K*N; out[k*N + q] = d(sources[k], q).
+ *   out     : caller-owned DEVICE uint32 K*N, 16-byte aligned; out[k*N + q] =
+ *             d(sources[k], q).
  *   stream  : cudaStream_t the work runs on (NULL = default stream); the call
  *             returns when the rows are complete.
  * Limits: 0 <= K <= GAPSP_NOALLOC_MAX_SOURCES; H, W and N as gapsp_create.
- * Errors: GAPSP_E_INVALID for sizes beyond the limits, a NULL pointer or a
- * source outside [0, N) (nothing is written then); GAPSP_E_NOT_CONVERGED;
+ * Errors: GAPSP_E_INVALID for sizes beyond the limits, a NULL pointer, a
+ * misaligned out or a source outside [0, N) (nothing is written then); GAPSP_E_NOT_CONVERGED;
  * GAPSP_E_CUDA.
  * Every call shares the one array and it keeps the last call's contents:
  * calls that overlap on the GPU race, so order them on one stream. The first

@@ -39,7 +39,7 @@ class Opts(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("mem_budget", ctypes.c_size_t),
                 ("sweep_phases", ctypes.c_int), ("fill_rows", ctypes.c_int), ("checked", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("prop_blocks", ctypes.c_int),
-                ("lookahead", ctypes.c_int)]
+                ("lookahead", ctypes.c_int), ("warm_start", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -175,7 +175,8 @@ class Image:
 
     def __init__(self, img, conn: int = 8, kind: str = "grey", mask=None, B: int = 32,
                  seed: int = 0, mem_budget: int = 0, stream=None, sweep_phases: int = 0,
-                 fill_rows: int = 0, prop_blocks: int = 0, lookahead: int = 0):
+                 fill_rows: int = 0, prop_blocks: int = 0, lookahead: int = 0,
+                 warm_start: int = 0):
         lib = load()
         self._lib = lib
         self._h = ctypes.c_void_p()
@@ -199,6 +200,7 @@ class Image:
         o.fill_rows = fill_rows
         o.prop_blocks = prop_blocks
         o.lookahead = lookahead
+        o.warm_start = warm_start
         o.stream = _torch_stream(stream)
         self.H, self.W, self.N, self.conn, self.kind, self.B = H, W, H * W, conn, kind, B
         rc = lib.gapsp_create(_ptr(img_a), H, W, _ptr(mask_a), ctypes.byref(o), ctypes.byref(self._h))

@@ -31,6 +31,7 @@ struct gapsp_handle {
     int fill_rows = 0;
     int prop_blocks = 0;
     int lookahead = 0;  // option: 0 auto, -1 off, else candidates per round
+    bool warm = true;   // option: propagations start from complete neighbour rows
     int sms = 0;        // multiprocessors of the device
     uint64_t launches = 0;
     // image
@@ -373,6 +374,7 @@ gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask,
     if (o.prop_blocks != 0 && o.prop_blocks != 1 && o.prop_blocks != 2 && o.prop_blocks != 4)
         return GAPSP_E_INVALID;
     if (o.lookahead < -1 || o.lookahead > 1024) return GAPSP_E_INVALID;
+    if (o.warm_start != 0 && o.warm_start != -1) return GAPSP_E_INVALID;
     if (o.kind != GAPSP_MASK && !img) return GAPSP_E_INVALID;
     if (o.kind == GAPSP_MASK && !mask) return GAPSP_E_INVALID;
 
@@ -384,6 +386,7 @@ gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask,
     h->fill_rows = o.fill_rows;
     h->prop_blocks = o.prop_blocks;
     h->lookahead = o.lookahead;
+    h->warm = o.warm_start == 0;
     {
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -462,6 +465,7 @@ gapsp_status gapsp_rows(gapsp_handle* h, const int32_t* sources, int K, uint32_t
     for (int k = 0; k < K; ++k)
         if (hs[k] < 0 || hs[k] >= h->N) return GAPSP_E_INVALID;
     const bool out_dev = is_device_ptr(out);
+    if (out_dev && (reinterpret_cast<uintptr_t>(out) & 15)) return GAPSP_E_INVALID;  // 16-byte row stores
     const size_t out_bytes = (size_t)K * N * sizeof(uint32_t);
     if (h->budget && (out_dev ? 0 : out_bytes) + (size_t)K * 4 > h->budget) return GAPSP_E_BUDGET;
     if (K > h->src_cap) {
@@ -560,7 +564,9 @@ struct FillRun {
 // Candidates propagated ahead per round: one block (cluster) for each
 // multiprocessor the round's own sources leave free, unless set by option.
 int lookahead_count(const gapsp_handle* h, const PropArgs& pa) {
-    if (h->lookahead < 0) return 0;
+    // a map in global memory is the output row itself, which the round's
+    // fill may write while a lookahead launch sweeps it: no lookahead then
+    if (h->lookahead < 0 || !prop_map_in_smem(pa)) return 0;
     int K = h->lookahead;
     if (K == 0) {
         const int per = prop_blocks_per_job(pa);
@@ -574,6 +580,8 @@ gapsp_status fill_begin(FillRun& r) {
     gapsp_handle* h = r.h;
     const size_t N = h->N;
     r.d_dev = is_device_ptr(r.D);
+    // rows of D are stored and read 16 bytes at a time
+    if (r.d_dev && (reinterpret_cast<uintptr_t>(r.D) & 15)) return GAPSP_E_INVALID;
     const size_t dbytes = N * N * sizeof(uint32_t);
     const size_t need = fill_state_bytes(h) + (r.d_dev ? 0 : dbytes);
     if (h->budget && need > h->budget) return GAPSP_E_BUDGET;
@@ -639,7 +647,9 @@ gapsp_status fill_begin(FillRun& r) {
     CK(cudaMemsetAsync(h->done, 0, sizeof(int), s));
     CK(cudaMemsetAsync(h->nsel, 0, sizeof(int), s));
     CK(cudaMemsetAsync(h->marks, 0, N * h->words * sizeof(unsigned long long), s));
-    InitArgs ia{h->N, Dd, h->cnt, h->comp, h->comp_size, h->kind == GAPSP_MASK};
+    // D starts as UNREACH everywhere when a mask may leave pairs unjoined,
+    // and when propagations start warm from it
+    InitArgs ia{h->N, Dd, h->cnt, h->comp, h->comp_size, h->kind == GAPSP_MASK || h->warm};
     {
         ProfScope ps(h, K_INIT, s);
         CK(launch_init(ia, s));
@@ -694,6 +704,7 @@ gapsp_status fill_begin(FillRun& r) {
     pa.convert = h->kind == GAPSP_MASK;
     pa.sweeps = h->stats + S_SWEEPS;
     pa.row_done = h->row_done;
+    if (h->warm) pa.warm_rows = Dd;
     // the repulsion order's draws cannot be foreseen: no lookahead
     r.K = r.order == GAPSP_REPULSION ? 0 : lookahead_count(h, pa);
     if (r.K > 0) {

@@ -26,6 +26,12 @@ struct PropArgs {
                                 // output; set the flag once a row is written
     unsigned long long* ran;    // or NULL: counts the jobs that were not skipped
     unsigned long long* hits;   // or NULL: counts the jobs skipped by row_done
+    // Warm start (fills only; NULL: the map starts from the seeds alone): the
+    // distances array, row q at warm_rows + q * N, holding at every entry
+    // either an upper bound of the distance (a path's cost, mostly the exact
+    // distance) or UNREACH. The map of source s starts from row s and from
+    // d(s,q) + d(q,x) for its neighbours q.
+    const uint32_t* warm_rows;
 };
 
 // Picks the per-lane width and launches kernel (a).
@@ -35,12 +41,15 @@ cudaError_t launch_propagate(const PropArgs& a, int conn, int kind, int grid, in
 int prop_vpl(int side);
 // Blocks (one cluster) a single-source propagation of this image uses.
 int prop_blocks_per_job(const PropArgs& a);
+// Whether the distance map of a propagation lives in shared memory (else it
+// is the output row itself, in global memory).
+bool prop_map_in_smem(const PropArgs& a);
 
 struct ImagePrep {
     const uint8_t* f;
     int H, W, conn, kind;
     uint8_t* bound;  // boundary flags: free pixels with fewer free neighbours than conn
-    uint32_t* pgeo;  // [N]: tile << 8 | bit of each pixel (see TileGeom)
+    uint32_t* pgeo;  // [N]: tile << 8 | bit of each pixel (from k_geometry)
     int32_t* tbase;  // [tiles]: pixel index of each tile's top-left pixel
     int tiles_w, tiles;
 };

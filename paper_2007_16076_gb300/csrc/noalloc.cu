@@ -69,6 +69,7 @@ extern "C" gapsp_status gapsp_rows_noalloc(const uint8_t* img, int H, int W, int
     if (K < 0 || K > GAPSP_NOALLOC_MAX_SOURCES) return GAPSP_E_INVALID;
     if (K == 0) return GAPSP_OK;
     if (!img || !sources || !out) return GAPSP_E_INVALID;
+    if (reinterpret_cast<uintptr_t>(out) & 15) return GAPSP_E_INVALID;  // 16-byte row stores
     const int N = H * W;
     cudaStream_t st = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lock(g_mu);

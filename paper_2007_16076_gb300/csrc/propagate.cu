@@ -415,6 +415,123 @@ __device__ void flag_seed_lines(const PropArgs& a, const Shared& sh, int src) {
     }
 }
 
+// Warm start. During a fill every entry of D is UNREACH (set before the
+// first round) or the cost of a real path, exact once the pair is filled:
+// the fills and the propagations write nothing else. Any entry therefore
+// bounds its distance from above, even one read while another launch is
+// writing it (the old and the new value are both bounds), and so do the
+// sums d(s,q) + d(q,x) over a neighbour q of s (triangle inequality). The
+// map of source s starts from the least of these bounds instead of
+// "unreached": the sweeps reach the same unique fixpoint from any upper
+// bounds, and most pairs of a late source are filled already. Warp 0 picks
+// the neighbours whose d(s,q) is known (axial first); returns how many.
+constexpr int MAXHELP = 8;
+struct Helpers {
+    const uint32_t* row[MAXHELP];  // row q of D
+    int d[MAXHELP];                // bound of d(s, q)
+    int n;
+};
+
+__device__ int pick_helpers(const PropArgs& a, int src, Helpers& h) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        bool ok = false;
+        const uint32_t* row = nullptr;
+        int dq = 0;
+        if (a.warm_rows && src >= 0 && lane < a.conn && (!a.kind_mask || a.f[src])) {
+            const int r = src / a.W, c = src - r * a.W;
+            const int rr = r + (lane < 4 ? (lane == 0 ? -1 : lane == 1 ? 1 : 0) : (lane < 6 ? -1 : 1));
+            const int cc = c + (lane < 4 ? (lane == 2 ? -1 : lane == 3 ? 1 : 0) : ((lane & 1) ? 1 : -1));
+            if (rr >= 0 && rr < a.H && cc >= 0 && cc < a.W) {
+                const int q = rr * a.W + cc;
+                const uint32_t v = __ldcg(a.warm_rows + (size_t)src * a.N + q);
+                if (v < (uint32_t)PINF && (!a.kind_mask || a.f[q])) {
+                    ok = true;
+                    row = a.warm_rows + (size_t)q * a.N;
+                    dq = (int)v;
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(FULL, ok);
+        if (ok) {
+            const int i = __popc(m & ((1u << lane) - 1u));
+            h.row[i] = row;
+            h.d[i] = dq;
+        }
+        if (lane == 0) h.n = __popc(m);
+    }
+    __syncthreads();
+    return h.n;
+}
+
+__device__ __forceinline__ int warm_bound(uint32_t dx, int dq) {
+    return dx < (uint32_t)PINF ? (int)dx + dq : PINF;
+}
+
+// The strip's map before the first round: the seeds at 0, elsewhere
+// "unreached" or, warm, the least bound from row s and the neighbours' rows
+// (obstacles stay unreached). Warm, a line is flagged for the first round
+// when it holds a finite value (flag slot 2 is the one round 0 reads as
+// "previous round"); returns whether the map is warm.
+template <int KIND>
+__device__ bool init_map(const PropArgs& a, int* smap, int pitch, uint8_t* flags, int r0, int hs, int src,
+                         const Helpers& h, int nh) {
+    const int n = hs * a.W, g0 = r0 * a.W;
+    const bool warm = a.warm_rows && src >= 0;
+    if (!warm) {
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+            const int r = p / a.W, c = p - r * a.W;
+            smap[r * pitch + c] = is_seed(a, src, g0 + p) ? 0 : PINF;
+        }
+        return false;
+    }
+    uint8_t* fr = flags + 2 * hs;            // row lines of the strip
+    uint8_t* fc = flags + 3 * hs + 2 * a.W;  // column lines
+    const uint32_t* own = a.warm_rows + (size_t)src * a.N + g0;
+    if ((a.W & 3) == 0) {
+        // rows start on 16-byte boundaries (the array is 16-byte aligned)
+        for (int p = 4 * threadIdx.x; p < n; p += 4 * blockDim.x) {
+            const uint4 u0 = __ldcg(reinterpret_cast<const uint4*>(own + p));
+            int v[4] = {warm_bound(u0.x, 0), warm_bound(u0.y, 0), warm_bound(u0.z, 0), warm_bound(u0.w, 0)};
+            for (int k = 0; k < nh; ++k) {
+                const uint4 u = __ldcg(reinterpret_cast<const uint4*>(h.row[k] + g0 + p));
+                v[0] = min(v[0], warm_bound(u.x, h.d[k]));
+                v[1] = min(v[1], warm_bound(u.y, h.d[k]));
+                v[2] = min(v[2], warm_bound(u.z, h.d[k]));
+                v[3] = min(v[3], warm_bound(u.w, h.d[k]));
+            }
+            const int r = p / a.W, c = p - r * a.W;  // 4 pixels of one row (W % 4 = 0)
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                int x = v[k];
+                if (KIND == 1 && !a.f[g0 + p + k]) x = PINF;
+                if (is_seed(a, src, g0 + p + k)) x = 0;
+                smap[r * pitch + c + k] = x;
+                if (x < PINF) {
+                    any = true;
+                    fc[c + k] = 1;
+                }
+            }
+            if (any) fr[r] = 1;
+        }
+    } else {
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+            int x = warm_bound(__ldcg(own + p), 0);
+            for (int k = 0; k < nh; ++k) x = min(x, warm_bound(__ldcg(h.row[k] + g0 + p), h.d[k]));
+            if (KIND == 1 && !a.f[g0 + p]) x = PINF;
+            if (is_seed(a, src, g0 + p)) x = 0;
+            const int r = p / a.W, c = p - r * a.W;
+            smap[r * pitch + c] = x;
+            if (x < PINF) {
+                fr[r] = 1;
+                fc[c] = 1;
+            }
+        }
+    }
+    return true;
+}
+
 // Map in shared memory. One block per job, or a cluster of C blocks per job
 // (CL), each owning a strip of rows; the strips see each other's edge rows
 // through distributed shared memory.
@@ -437,14 +554,14 @@ __global__ void __launch_bounds__(32 * MAXWARPS) k_propagate_smem(PropArgs a, in
         return;
     }
     int* out = a.map_base + (size_t)(a.map_row ? a.map_row[j] : j) * (size_t)a.N;
-    for (int p = threadIdx.x; p < hs * a.W; p += blockDim.x) {
-        const int r = p / a.W, c = p - r * a.W;
-        smap[r * pitch + c] = is_seed(a, src, r0 * a.W + p) ? 0 : PINF;
-    }
+    __shared__ Helpers s_help;
+    const int nh = pick_helpers(a, src, s_help);
+    // the flags are cleared by setup_shared: it comes first, then the map
     Shared sh = setup_shared<KIND, VPL>(a, reinterpret_cast<char*>(smap + hs * pitch), r0, hs);
     if (threadIdx.x == 0) { s_flag[0] = 0; s_flag[1] = 0; }
     __syncthreads();
-    flag_seed_lines(a, sh, src);
+    const bool warm = init_map<KIND>(a, smap, pitch, sh.chR, r0, hs, src, s_help, nh);
+    if (!warm) flag_seed_lines(a, sh, src);
     if (CL) {
         cg::cluster_group cl = cg::this_cluster();
         if (rank > 0) {
@@ -617,6 +734,8 @@ int prop_blocks_per_job(const PropArgs& a) {
     const int C = strips_per_job(a);
     return C > 0 ? C : 1;
 }
+
+bool prop_map_in_smem(const PropArgs& a) { return strips_per_job(a) > 0; }
 
 int prop_vpl(int side) {
     if (side <= 32) return 1;

@@ -88,5 +88,8 @@ def test_invalid_arguments_rejected_without_gpu(lib_path):
     o.conn = 8
     o.kind = 1  # mask kind without a mask
     assert lib.gapsp_create(img, 2, 2, None, ctypes.byref(o), ctypes.byref(h)) == 1
+    o.kind = 0
+    o.warm_start = 1  # 0 (on) or -1 (off) only
+    assert lib.gapsp_create(img, 2, 2, None, ctypes.byref(o), ctypes.byref(h)) == 1
     assert not h
     lib.gapsp_destroy(None)  # NULL-safe

@@ -229,12 +229,70 @@ def test_lookahead_changes_nothing(gp, order, lookahead):
         assert st["lookahead_propagations"] > 0
 
 
+@pytest.mark.parametrize("shape,conn,kind,prop_blocks", [
+    ((37, 29), 8, "grey", 0),   # odd width: one value at a time
+    ((32, 40), 8, "grey", 0),   # width a multiple of 4: 16-byte loads
+    ((40, 32), 4, "l1", 0),
+    ((33, 36), 8, "mask", 0),   # obstacles: neither helpers nor bounds through them
+    ((48, 48), 8, "grey", 2),   # row strips on a cluster of two blocks
+    ((64, 24), 4, "grey", 4),
+])
+@pytest.mark.parametrize("warm", [0, -1])
+def test_warm_start_changes_nothing(gp, shape, conn, kind, prop_blocks, warm):
+    """Propagations started from the complete rows of filled neighbours (or
+    from the source alone) give the oracle's D, counts and source order."""
+    H, W = shape
+    img = synth.blobs(H, W, 5, 3.0, 55.0, seed=H + W)
+    mask = synth.disk_mask(H, W, 0.3, 2, 4, seed=5) if kind == "mask" else None
+    with gp.Image(img, conn=conn, kind=kind, mask=mask, B=5, warm_start=warm,
+                  prop_blocks=prop_blocks) as im:
+        D, st = im.all_pairs("minfill", want_log=True)
+    ref = oracle.fill(img, "minfill", B=5, conn=conn, kind=kind, mask=mask)
+    assert np.array_equal(_u32(D), oracle.apsp(img, conn=conn, kind=kind, mask=mask))
+    for k in ("propagations", "prepass_propagations", "distance_ops", "new_pairs", "rounds"):
+        assert st[k] == getattr(ref, k), k
+    assert np.array_equal(st["sources"], ref.sources)
+
+
+def test_warm_start_sweeps_fewer_lines(gp):
+    """The warm start is taken: with it the propagations process fewer lines."""
+    img = synth.blobs(64, 64, 8, 4.0, 55.0, seed=3)
+    lines = {}
+    for warm in (0, -1):
+        with gp.Image(img, conn=8, B=16, warm_start=warm) as im:
+            _, st = im.all_pairs("minfill")
+        lines[warm] = st["lines"] / (st["propagations"] + st["lookahead_propagations"])
+    assert lines[0] < 0.8 * lines[-1], lines
+
+
 def test_lookahead_rejects_bad_counts(gp):
     img = synth.blobs(8, 8, 2, 2.0, 55.0, seed=1)
     for bad in (-2, 1025):
         with pytest.raises(gp.GapspError) as e:
             gp.Image(img, conn=8, B=4, lookahead=bad)
         assert e.value.code == 1
+
+
+def test_misaligned_device_arrays_rejected(gp):
+    """Rows of D move 16 bytes at a time: a device array that does not start
+    on a 16-byte boundary is refused before any launch, and left alone."""
+    import torch
+    img = synth.blobs(8, 8, 2, 2.0, 55.0, seed=1)
+    N = 64
+    buf = torch.full((N * N + 4,), 7, dtype=torch.int32, device="cuda")
+    with gp.Image(img, conn=8, B=4) as im:
+        with pytest.raises(gp.GapspError) as e:
+            im.all_pairs("minfill", out=buf[1:1 + N * N].view(N, N))
+        assert e.value.code == 1
+        with pytest.raises(gp.GapspError) as e:
+            im.rows(np.array([0, 5], dtype=np.int32), out=buf[1:1 + 2 * N].view(2, N))
+        assert e.value.code == 1
+        with pytest.raises(gp.GapspError) as e:
+            gp.rows_noalloc(torch.from_numpy(img).cuda(), np.array([3], dtype=np.int32),
+                            buf[2:2 + N].view(1, N))
+        assert e.value.code == 1
+    torch.cuda.synchronize()
+    assert bool((buf == 7).all())
 
 
 def test_budget_rejected_before_allocation(gp):
