@@ -76,6 +76,7 @@ struct gapsp_handle {
     unsigned long long* stats = nullptr;
     unsigned long long* round_new = nullptr;
     unsigned long long* last_new = nullptr;
+    uint32_t* vfloor = nullptr;   // selection: least leading key field at the previous round
     int32_t* sel_log = nullptr;
     uint32_t* emap = nullptr;
     uint32_t* gmap = nullptr;
@@ -257,6 +258,7 @@ gapsp_status ensure_fill_state(gapsp_handle* h) {
     CK(dalloc(&h->stats, S_SLOTS));
     CK(dalloc(&h->round_new, N + 1));
     CK(dalloc(&h->last_new, 1));
+    CK(dalloc(&h->vfloor, 1));
     CK(dalloc(&h->sel_log, N + 1));
     CK(dalloc(&h->emap, N));
     CK(dalloc(&h->gmap, N));
@@ -276,7 +278,7 @@ void free_all(gapsp_handle* h) {
     dfree(h->rp_ring); dfree(h->rp_fstart); dfree(h->rp_fcyc); dfree(h->rp_inS); dfree(h->rp_state);
     dfree(h->rp_taken);
     dfree(h->dep_exit); dfree(h->dep_size); dfree(h->dep_count);
-    dfree(h->stats); dfree(h->round_new); dfree(h->last_new); dfree(h->sel_log);
+    dfree(h->stats); dfree(h->round_new); dfree(h->last_new); dfree(h->vfloor); dfree(h->sel_log);
     dfree(h->emap); dfree(h->gmap); dfree(h->best); dfree(h->cen);
     dfree(h->Dtmp); dfree(h->src_dev); dfree(h->out_tmp);
     if (h->h_done) cudaFreeHost(h->h_done);
@@ -643,6 +645,7 @@ gapsp_status fill_begin(FillRun& r) {
     CK(cudaMemsetAsync(h->status, 0, sizeof(int), s));
     CK(cudaMemsetAsync(h->stats, 0, S_SLOTS * sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(h->last_new, 0, sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(h->vfloor, 0, sizeof(uint32_t), s));
     CK(cudaMemsetAsync(h->cursor, 0, sizeof(int), s));
     CK(cudaMemsetAsync(h->done, 0, sizeof(int), s));
     CK(cudaMemsetAsync(h->nsel, 0, sizeof(int), s));
@@ -695,6 +698,7 @@ gapsp_status fill_begin(FillRun& r) {
     CK(cudaMemsetAsync(h->row_claim, 0, N, s));
     r.sa = SelectArgs{h->N, h->B, (int)r.order, h->cnt, h->rank, h->grank, h->seq, r.nseq, h->cursor, h->sel, h->nsel,
                       h->stats, h->round_new, h->last_new, h->sel_log, h->done};
+    r.sa.vfloor = h->vfloor;
     PropArgs& pa = r.pa;
     pa = base_prop(h);
     pa.map_base = (int*)Dd;

@@ -111,6 +111,9 @@ struct SelectArgs {
                                 // from (B + KL <= 1024)
     const uint8_t* row_done;    // [N]: rows already computed
     uint8_t* row_claim;         // [N]: rows handed to a lookahead launch; set for each candidate
+    uint32_t* vfloor;           // minfill / extrema (N <= 16384): the least leading key field (cnt,
+                                // or grank) among the unfilled points at the previous selection;
+                                // 0 at the start. It never decreases.
 };
 cudaError_t launch_select(const SelectArgs& a, cudaStream_t st);
 

@@ -99,13 +99,14 @@ __global__ void k_select_seq(SelectArgs a) {
 // that a smaller grank is a farther point and equal distances share it.
 constexpr int SEL_THREADS = 1024;
 
-__device__ __forceinline__ unsigned long long mf_key(const SelectArgs& a, int p) {
-    const uint32_t c = a.cnt[p];
-    const int32_t r = a.rank[p];
-    if (c >= (uint32_t)a.N || r < 0) return ~0ull;
-    if (a.order == 3)
-        return ((unsigned long long)a.grank[p] << 34) | ((unsigned long long)c << 17) | (unsigned long long)p;
+__device__ __forceinline__ unsigned long long key_of(int order, int N, uint32_t c, int32_t r, int32_t g, int p) {
+    if (c >= (uint32_t)N || r < 0) return ~0ull;
+    if (order == 3) return ((unsigned long long)g << 34) | ((unsigned long long)c << 17) | (unsigned long long)p;
     return ((unsigned long long)c << 17) | (unsigned long long)r;
+}
+
+__device__ __forceinline__ unsigned long long mf_key(const SelectArgs& a, int p) {
+    return key_of(a.order, a.N, a.cnt[p], a.rank[p], a.order == 3 ? a.grank[p] : 0, p);
 }
 
 // Radix selection, 11 bits a pass from the top bit a key can have: the
@@ -116,15 +117,17 @@ constexpr int RB = 11, NBIN = 1 << RB;
 struct SelScratch {
     unsigned hist[NBIN];
     unsigned wsum[32];
+    unsigned long long wlo[32], whi[32];
     unsigned long long prefix;
     int need;
 };
 
 template <class KeyF>
-__device__ unsigned long long radix_select(KeyF keyf, int n, int need, int top, SelScratch& sc) {
+__device__ unsigned long long radix_select(KeyF keyf, int n, int need, int top, SelScratch& sc,
+                                           unsigned long long prefix0 = 0) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    unsigned long long prefix = 0;
-    if (tid == 0) { sc.need = need; sc.prefix = 0; }
+    unsigned long long prefix = prefix0;
+    if (tid == 0) { sc.need = need; sc.prefix = prefix0; }
     for (int shift = ((top - 1) / RB) * RB; shift >= 0; shift -= RB) {
         for (int i = tid; i < NBIN; i += SEL_THREADS) sc.hist[i] = 0;
         __syncthreads();
@@ -174,90 +177,125 @@ __device__ unsigned long long radix_select(KeyF keyf, int n, int need, int top, 
     return prefix;
 }
 
-// Keys of the unfilled points are cached in shared memory when N <= 16384
-// (CACHED), and read from the counts otherwise.
-template <bool CACHED>
-__global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
-    extern __shared__ unsigned long long skeys[];
-    __shared__ SelScratch sc;
-    __shared__ int s_count, s_unfilled, s_nsel, s_ncand;
-    __shared__ unsigned long long s_keys[1024], s_selk[1024];
-    __shared__ int s_pix[1024], s_selp[1024];
-    __shared__ int s_wcount[32];
+// The bits in which the valid keys keyf(0 .. n-1) differ: the radix
+// selection then starts at the highest of them (`top` = its position + 1),
+// with `prefix0` holding the bits all keys share above the first digit.
+template <class KeyF>
+__device__ void key_span(KeyF keyf, int n, SelScratch& sc, int& top, unsigned long long& prefix0) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (*a.done) {
-        if (tid == 0) {
-            *a.nsel = 0;
-            if (a.ncand) *a.ncand = 0;
+    unsigned long long lo = ~0ull, hi = 0;
+    for (int i = tid; i < n; i += SEL_THREADS) {
+        const unsigned long long k = keyf(i);
+        if (k != ~0ull) {
+            lo = min(lo, k);
+            hi = max(hi, k);
         }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(FULL, lo, o));
+        hi = max(hi, __shfl_xor_sync(FULL, hi, o));
+    }
+    if (lane == 0) { sc.wlo[warp] = lo; sc.whi[warp] = hi; }
+    __syncthreads();
+    lo = sc.wlo[lane];
+    hi = sc.whi[lane];
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(FULL, lo, o));
+        hi = max(hi, __shfl_xor_sync(FULL, hi, o));
+    }
+    __syncthreads();  // wlo / whi are free again
+    if (lo > hi) {  // no valid key
+        top = 1;
+        prefix0 = 0;
         return;
     }
-    if (tid == 0) { s_unfilled = 0; s_count = 0; s_nsel = 0; s_ncand = 0; }
-    __syncthreads();
-    int mine = 0;
-    for (int p = tid; p < a.N; p += SEL_THREADS) {
-        const unsigned long long k = mf_key(a, p);
-        if (CACHED) skeys[p] = k;
-        mine += k != ~0ull;
+    const unsigned long long diff = lo ^ hi;
+    top = diff ? 64 - __clzll((long long)diff) : 1;
+    const int first = ((top - 1) / RB) * RB + RB;  // bits below this are selected digit by digit
+    prefix0 = first >= 64 ? 0 : (lo & ~((1ull << first) - 1ull));
+}
+
+// The end of a minfill / extrema selection, once the keys of a window at
+// the front of the ranking (at least the (B + KL) smallest, at most WIN)
+// are gathered in s_keys / s_pix (s_count of them): the B selected in key
+// order, and the lookahead candidates (the K smallest keys of the window
+// after the selection whose rows are neither computed nor claimed).
+constexpr int WIN = 2048;
+
+// Exclusive prefix sum over the block of one value per thread; `total`
+// receives the sum. Every thread calls it.
+__device__ __forceinline__ int block_excl_scan(int v, SelScratch& sc, int& total) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += t;
     }
-    for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(FULL, mine, o);
-    if (lane == 0 && mine) atomicAdd(&s_unfilled, mine);
+    if (lane == 31) sc.wsum[warp] = (unsigned)x;
     __syncthreads();
-    auto key = [&](int p) -> unsigned long long { return CACHED ? skeys[p] : mf_key(a, p); };
-    const int unfilled = s_unfilled;
-    const int want = min(unfilled, a.B);
-    // the selection, then the next KL points in key order, from which the
-    // lookahead candidates are taken
-    const int wantc = min(unfilled, a.B + (a.K > 0 ? a.KL : 0));
-    // keys have 17 bits per field below the top one
-    int top = a.order == 3 ? 34 : 17;
-    for (int n = a.N - 1; n > 0; n >>= 1) ++top;
-    unsigned long long thr = ~0ull - 1;  // gather keys <= thr
-    if (wantc > 0 && wantc < unfilled) thr = radix_select(key, a.N, wantc, top, sc);
-    // gather (one shared atomic per warp)
-    if (want > 0) {
-        for (int p0 = 0; p0 < a.N; p0 += SEL_THREADS) {
-            const int p = p0 + tid;
-            const unsigned long long k = p < a.N ? key(p) : ~0ull;
-            const bool take = k != ~0ull && k <= thr;
-            const unsigned m = __ballot_sync(FULL, take);
-            int base = 0;
-            if (lane == 0 && m) base = atomicAdd(&s_count, __popc(m));
-            base = __shfl_sync(FULL, base, 0);
-            if (take) {
-                const int slot = base + __popc(m & ((1u << lane) - 1u));
-                if (slot < 1024) { s_keys[slot] = k; s_pix[slot] = p; }
-            }
+    if (warp == 0) {
+        const int w = (int)sc.wsum[lane];
+        int y = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, y, o);
+            if (lane >= o) y += t;
         }
+        sc.wsum[lane] = (unsigned)(y - w);
+        if (lane == 31) sc.need = y;
     }
     __syncthreads();
-    const int nall = min(s_count, wantc);
-    // the selection: the `want` smallest gathered keys (a second radix
-    // selection over at most 1024 keys), in key order
+    const int r = (int)sc.wsum[warp] + x - v;
+    total = sc.need;
+    __syncthreads();  // wsum / need are free again
+    return r;
+}
+
+__device__ void finish_selection(const SelectArgs& a, int want, int top, SelScratch& sc, int& s_count,
+                                 unsigned long long* s_keys, int* s_pix, unsigned long long* s_selk, int* s_selp,
+                                 int& s_nsel, int& s_ncand, bool have_t1 = false,
+                                 unsigned long long t1_known = 0) {
+    __shared__ unsigned long long s_ck[WIN];  // candidate keys (~0: not a candidate)
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int nall = min(s_count, WIN);
+    // the radix selections below start at the highest bit in which the
+    // window's keys differ
+    unsigned long long prefix0 = 0;
+    key_span([&](int i) -> unsigned long long { return s_keys[i]; }, nall, sc, top, prefix0);
+    // the selection: the `want` smallest keys of the window, in key order
     unsigned long long t1 = ~0ull - 1;
-    if (want > 0 && want < nall)
-        t1 = radix_select([&](int i) -> unsigned long long { return s_keys[i]; }, nall, want, top, sc);
+    if (have_t1) t1 = t1_known;
+    else if (want > 0 && want < nall)
+        t1 = radix_select([&](int i) -> unsigned long long { return s_keys[i]; }, nall, want, top, sc, prefix0);
     // candidates: after the selection, points whose rows are not computed
     // yet; when there are more than K, the K smallest keys among them
-    auto cand_key = [&](int i) -> unsigned long long {
-        const int p = s_pix[i];
-        const bool taken = (a.row_done && a.row_done[p]) || (a.row_claim && a.row_claim[p]);
-        return (s_keys[i] > t1 && !taken) ? s_keys[i] : ~0ull;
-    };
+    int ncnd = 0;
+    if (a.cand) {
+        for (int e = tid; e < nall; e += SEL_THREADS) {
+            const int p = s_pix[e];
+            const bool taken = (a.row_done && a.row_done[p]) || (a.row_claim && a.row_claim[p]);
+            const bool c = s_keys[e] > t1 && !taken;
+            s_ck[e] = c ? s_keys[e] : ~0ull;
+            ncnd += c;
+        }
+    }
     unsigned long long tk = ~0ull - 1;
     if (a.cand) {
-        const unsigned m = __ballot_sync(FULL, tid < nall && cand_key(tid) != ~0ull);
-        if (lane == 0 && m) atomicAdd(&s_ncand, __popc(m));
+        for (int o = 16; o > 0; o >>= 1) ncnd += __shfl_down_sync(FULL, ncnd, o);
+        if (lane == 0 && ncnd) atomicAdd(&s_ncand, ncnd);
         __syncthreads();
         const int nc = s_ncand;
         __syncthreads();
         if (tid == 0) s_ncand = 0;
-        if (nc > a.K) tk = radix_select(cand_key, nall, a.K, top, sc);
+        if (nc > a.K)
+            tk = radix_select([&](int i) -> unsigned long long { return s_ck[i]; }, nall, a.K, top, sc, prefix0);
         __syncthreads();
     }
-    const bool in_sel = tid < nall && s_keys[tid] <= t1;
-    const bool in_cand = tid < nall && a.cand && cand_key(tid) <= tk;
-    {
+    for (int e0 = 0; e0 < nall; e0 += SEL_THREADS) {
+        const int e = e0 + tid;
+        const bool in_sel = e < nall && s_keys[e] <= t1;
+        const bool in_cand = e < nall && a.cand && s_ck[e] <= tk;
         const unsigned ms = __ballot_sync(FULL, in_sel), mc = __ballot_sync(FULL, in_cand);
         int bs = 0, bc = 0;
         if (lane == 0) {
@@ -269,14 +307,16 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
         const unsigned below = (1u << lane) - 1u;
         if (in_sel) {
             const int slot = bs + __popc(ms & below);
-            s_selk[slot] = s_keys[tid];
-            s_selp[slot] = s_pix[tid];
+            if (slot < 1024) {
+                s_selk[slot] = s_keys[e];
+                s_selp[slot] = s_pix[e];
+            }
         }
         if (in_cand) {
             const int slot = bc + __popc(mc & below);
             if (slot < a.K) {
-                a.cand[slot] = s_pix[tid];
-                if (a.row_claim) a.row_claim[s_pix[tid]] = 1;
+                a.cand[slot] = s_pix[e];
+                if (a.row_claim) a.row_claim[s_pix[e]] = 1;
             }
         }
     }
@@ -304,7 +344,284 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
             a.stats[S_PROPAGATIONS] += ns;
         }
     }
-    (void)warp;
+}
+
+// Minfill / extrema selection for N > 16384: the keys are recomputed from
+// the counts at every pass.
+__global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
+    __shared__ SelScratch sc;
+    __shared__ int s_count, s_unfilled, s_nsel, s_ncand;
+    __shared__ unsigned long long s_keys[1024], s_selk[1024];
+    __shared__ int s_pix[1024], s_selp[1024];
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (*a.done) {
+        if (tid == 0) {
+            *a.nsel = 0;
+            if (a.ncand) *a.ncand = 0;
+        }
+        return;
+    }
+    if (tid == 0) { s_unfilled = 0; s_count = 0; s_nsel = 0; s_ncand = 0; }
+    __syncthreads();
+    int mine = 0;
+    for (int p = tid; p < a.N; p += SEL_THREADS) {
+        mine += mf_key(a, p) != ~0ull;
+    }
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(FULL, mine, o);
+    if (lane == 0 && mine) atomicAdd(&s_unfilled, mine);
+    __syncthreads();
+    auto key = [&](int p) -> unsigned long long { return mf_key(a, p); };
+    const int unfilled = s_unfilled;
+    const int want = min(unfilled, a.B);
+    // the selection, then the next KL points in key order, from which the
+    // lookahead candidates are taken
+    const int wantc = min(unfilled, a.B + (a.K > 0 ? a.KL : 0));
+    // keys have 17 bits per field below the top one
+    int top = a.order == 3 ? 34 : 17;
+    for (int n = a.N - 1; n > 0; n >>= 1) ++top;
+    unsigned long long thr = ~0ull - 1;  // gather keys <= thr
+    if (wantc > 0 && wantc < unfilled) thr = radix_select(key, a.N, wantc, top, sc);
+    // gather (one shared atomic per warp)
+    if (want > 0) {
+        for (int p0 = 0; p0 < a.N; p0 += SEL_THREADS) {
+            const int p = p0 + tid;
+            const unsigned long long k = p < a.N ? key(p) : ~0ull;
+            const bool take = k != ~0ull && k <= thr;
+            const unsigned m = __ballot_sync(FULL, take);
+            int base = 0;
+            if (lane == 0 && m) base = atomicAdd(&s_count, __popc(m));
+            base = __shfl_sync(FULL, base, 0);
+            if (take) {
+                const int slot = base + __popc(m & ((1u << lane) - 1u));
+                if (slot < 1024) { s_keys[slot] = k; s_pix[slot] = p; }
+            }
+        }
+    }
+    __syncthreads();
+    finish_selection(a, want, top, sc, s_count, s_keys, s_pix, s_selk, s_selp, s_nsel, s_ncand);
+}
+
+// The same selection for N <= 16384, with fewer passes over the points.
+// Keys order first by a leading field v (cnt for minfill, grank for extrema)
+// that never decreases for a point, and the unfilled set only shrinks, so
+// the least v among the unfilled points never decreases from round to round
+// (a.vfloor keeps last round's). One pass computes the keys, packs the
+// unfilled ones (with their point) into shared memory, and counts them by
+// v - vfloor (2048 bins, the last one for everything beyond). When the
+// (B + KL)-th smallest key falls in a bin below the last and at most WIN
+// keys have a v up to that bin's, those keys are the window the selection
+// and the candidates come from (every key with a smaller v is smaller, so
+// the B smallest are among them); otherwise the window is the (B + KL)
+// smallest keys, found by radix selection over all of them.
+template <int ORDER>
+__device__ __forceinline__ unsigned long long packed_key(unsigned long long k, int p) {
+    // extrema keys end with the point already; minfill keys get it below them
+    return ORDER == 3 ? k : ((k << 16) | (unsigned)p);
+}
+template <int ORDER>
+__device__ __forceinline__ unsigned long long unpack_key(unsigned long long pk) {
+    return ORDER == 3 ? pk : (pk >> 16);
+}
+template <int ORDER>
+__device__ __forceinline__ int unpack_point(unsigned long long pk) {
+    return ORDER == 3 ? (int)(pk & 0x1FFFFull) : (int)(pk & 0xFFFFull);
+}
+template <int ORDER>
+__device__ __forceinline__ uint32_t lead_field(unsigned long long k) {
+    return ORDER == 3 ? (uint32_t)(k >> 34) : (uint32_t)(k >> 17);
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(SEL_THREADS) k_select_small(SelectArgs a) {
+    extern __shared__ unsigned long long spk[];  // packed keys of the unfilled points
+    __shared__ SelScratch sc;
+    __shared__ int s_count, s_nsel, s_ncand;
+    __shared__ unsigned s_vmin;
+    __shared__ int s_below;  // some v below the floor: take the general path
+    __shared__ int s_bsel, s_below_sel, s_nt;
+    __shared__ unsigned long long s_t1, s_tie[256];
+    __shared__ unsigned long long s_keys[WIN], s_selk[1024];
+    __shared__ int s_pix[WIN], s_selp[1024];
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (*a.done) {
+        if (tid == 0) {
+            *a.nsel = 0;
+            if (a.ncand) *a.ncand = 0;
+        }
+        return;
+    }
+    const uint32_t vfloor = *a.vfloor;
+    if (tid == 0) { s_count = 0; s_nsel = 0; s_ncand = 0; s_vmin = 0xFFFFFFFFu; s_below = 0; }
+    for (int i = tid; i < NBIN; i += SEL_THREADS) sc.hist[i] = 0;
+    __syncthreads();
+    // pass 1, LD points per thread at a time: their counts and ranks are
+    // loaded before any is used (the latencies overlap); the unfilled ones
+    // are packed in order of a block-wide prefix sum (no shared counter) and
+    // binned by v - vfloor.
+    constexpr int LD = 8;
+    unsigned vmin = 0xFFFFFFFFu;
+    int unfilled = 0;
+    for (int b0 = 0; b0 < a.N; b0 += LD * SEL_THREADS) {
+        uint32_t cv[LD];
+        int32_t rv[LD], gv[LD];
+#pragma unroll
+        for (int u = 0; u < LD; ++u) {
+            const int q = b0 + u * SEL_THREADS + tid;
+            cv[u] = (uint32_t)a.N;
+            rv[u] = -1;
+            gv[u] = 0;
+            if (q < a.N) {
+                cv[u] = __ldcg(a.cnt + q);
+                rv[u] = __ldg(a.rank + q);
+                if (ORDER == 3) gv[u] = __ldg(a.grank + q);
+            }
+        }
+        int nv = 0;
+#pragma unroll
+        for (int u = 0; u < LD; ++u) nv += cv[u] < (uint32_t)a.N && rv[u] >= 0;
+        int total;
+        int w = unfilled + block_excl_scan(nv, sc, total);
+#pragma unroll
+        for (int u = 0; u < LD; ++u) {
+            const int q = b0 + u * SEL_THREADS + tid;
+            const unsigned long long k = q < a.N ? key_of(ORDER, a.N, cv[u], rv[u], gv[u], q) : ~0ull;
+            const bool in = k != ~0ull;
+            unsigned dig = (unsigned)(NBIN - 1);
+            if (in) {
+                spk[w++] = packed_key<ORDER>(k, q);
+                const uint32_t v = lead_field<ORDER>(k);
+                vmin = min(vmin, v);
+                if (v < vfloor) s_below = 1;  // not expected: the floor never passes a key
+                dig = v < vfloor ? (unsigned)(NBIN - 1) : min(v - vfloor, (uint32_t)(NBIN - 1));
+            }
+            // the last bin is not counted: only the bins below it are
+            // searched, and few keys share one of them
+            if (dig < (unsigned)(NBIN - 1)) atomicAdd(&sc.hist[dig], 1u);
+        }
+        unfilled += total;
+    }
+    for (int o = 16; o > 0; o >>= 1) vmin = min(vmin, __shfl_down_sync(FULL, vmin, o));
+    if (lane == 0 && vmin != 0xFFFFFFFFu) atomicMin(&s_vmin, vmin);
+    __syncthreads();
+    const int want = min(unfilled, a.B);
+    const int wantc = min(unfilled, a.B + (a.K > 0 ? a.KL : 0));
+    if (tid == 0 && s_vmin != 0xFFFFFFFFu) *a.vfloor = s_vmin;
+    int top = ORDER == 3 ? 34 : 17;
+    for (int n = a.N - 1; n > 0; n >>= 1) ++top;
+    // the bins that hold the wantc-th and the want-th key (the last bin when
+    // beyond the counted ones), how many keys lie up to the first and below
+    // the second
+    int bstar = NBIN - 1, bsel = NBIN - 1;
+    unsigned upto = 0, below_sel = 0;
+    if (tid == 0) { sc.need = NBIN - 1; s_bsel = NBIN - 1; }
+    if (wantc > 0) {
+        const unsigned h0 = sc.hist[2 * tid], h1 = sc.hist[2 * tid + 1];
+        unsigned v = h0 + h1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(FULL, v, o);
+            if (lane >= o) v += t;
+        }
+        if (lane == 31) sc.wsum[tid >> 5] = v;
+        __syncthreads();
+        if (tid < 32) {
+            const unsigned w0 = sc.wsum[lane];
+            unsigned x = w0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned t = __shfl_up_sync(FULL, x, o);
+                if (lane >= o) x += t;
+            }
+            sc.wsum[lane] = x - w0;
+        }
+        __syncthreads();
+        const unsigned incl = v + sc.wsum[tid >> 5], excl = incl - h0 - h1;
+        if (excl < (unsigned)wantc && (unsigned)wantc <= incl) {
+            const bool first = excl + h0 >= (unsigned)wantc;
+            sc.need = first ? 2 * tid : 2 * tid + 1;
+            sc.prefix = first ? excl + h0 : incl;
+        }
+        if (excl < (unsigned)want && (unsigned)want <= incl) {
+            const bool first = excl + h0 >= (unsigned)want;
+            s_bsel = first ? 2 * tid : 2 * tid + 1;
+            s_below_sel = first ? excl : excl + h0;
+        }
+        __syncthreads();
+        bstar = sc.need;
+        upto = (unsigned)sc.prefix;
+        bsel = s_bsel;
+        below_sel = (unsigned)s_below_sel;
+        __syncthreads();
+    }
+    bool have_t1 = false;
+    unsigned long long t1 = ~0ull - 1;
+    if (wantc > 0 && !s_below && bstar < NBIN - 1 && upto <= (unsigned)WIN) {
+        // the window: every key whose v is at most that bin's (the
+        // (B + KL)-th key among them), gathered in one pass
+        const uint32_t vmax = vfloor + (uint32_t)bstar;
+        for (int i0 = 0; i0 < unfilled; i0 += SEL_THREADS) {
+            const int i = i0 + tid;
+            const unsigned long long pk = i < unfilled ? spk[i] : ~0ull;
+            const bool take = i < unfilled && lead_field<ORDER>(unpack_key<ORDER>(pk)) <= vmax;
+            const unsigned m = __ballot_sync(FULL, take);
+            int base = 0;
+            if (lane == 0 && m) base = atomicAdd(&s_count, __popc(m));
+            base = __shfl_sync(FULL, base, 0);
+            if (take) {
+                const int slot = base + __popc(m & ((1u << lane) - 1u));
+                s_keys[slot] = unpack_key<ORDER>(pk);
+                s_pix[slot] = unpack_point<ORDER>(pk);
+            }
+        }
+        __syncthreads();
+        const int ng = s_count;
+        if (want > 0 && want < ng && bsel < NBIN - 1) {
+            // the want-th key: keys of smaller v are selected, and among
+            // those of its own v (few) it has rank want - below_sel
+            const uint32_t vsel = vfloor + (uint32_t)bsel;
+            if (tid == 0) { s_nt = 0; s_t1 = ~0ull - 1; }
+            __syncthreads();
+            for (int e = tid; e < ng; e += SEL_THREADS)
+                if (lead_field<ORDER>(s_keys[e]) == vsel) {
+                    const int slot = atomicAdd(&s_nt, 1);
+                    if (slot < 256) s_tie[slot] = s_keys[e];
+                }
+            __syncthreads();
+            const int nt = s_nt;
+            if (nt <= 256) {
+                if (tid < nt) {
+                    const unsigned long long k = s_tie[tid];
+                    int r = 0;
+                    for (int i = 0; i < nt; ++i) r += s_tie[i] < k;
+                    if (r == want - (int)below_sel - 1) s_t1 = k;
+                }
+                __syncthreads();
+                t1 = s_t1;
+                have_t1 = true;
+            }
+        }
+    } else if (want > 0) {
+        // the window: the (B + KL) smallest keys, by radix selection over
+        // all of them
+        auto keyf = [&](int i) -> unsigned long long { return unpack_key<ORDER>(spk[i]); };
+        unsigned long long thr = ~0ull - 1;
+        if (wantc < unfilled) thr = radix_select(keyf, unfilled, wantc, top, sc);
+        for (int i0 = 0; i0 < unfilled; i0 += SEL_THREADS) {
+            const int i = i0 + tid;
+            const unsigned long long k = i < unfilled ? keyf(i) : ~0ull;
+            const bool take = k != ~0ull && k <= thr;
+            const unsigned m = __ballot_sync(FULL, take);
+            int base = 0;
+            if (lane == 0 && m) base = atomicAdd(&s_count, __popc(m));
+            base = __shfl_sync(FULL, base, 0);
+            if (take) {
+                const int slot = base + __popc(m & ((1u << lane) - 1u));
+                if (slot < WIN) { s_keys[slot] = k; s_pix[slot] = unpack_point<ORDER>(spk[i]); }
+            }
+        }
+    }
+    __syncthreads();
+    finish_selection(a, want, top, sc, s_count, s_keys, s_pix, s_selk, s_selp, s_nsel, s_ncand, have_t1, t1);
 }
 
 // Spiral method with repulsion (Algorithm "spiral method with repulsion",
@@ -603,13 +920,14 @@ cudaError_t launch_select(const SelectArgs& a, cudaStream_t st) {
         if (a.N <= 16384) {
             static bool attr = false;
             if (!attr) {
-                cudaFuncSetAttribute(k_select_minfill<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     16384 * 8);
+                cudaFuncSetAttribute(k_select_small<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 8);
+                cudaFuncSetAttribute(k_select_small<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 8);
                 attr = true;
             }
-            k_select_minfill<true><<<1, SEL_THREADS, (size_t)a.N * 8, st>>>(a);
+            if (a.order == 2) k_select_small<2><<<1, SEL_THREADS, (size_t)a.N * 8, st>>>(a);
+            else k_select_small<3><<<1, SEL_THREADS, (size_t)a.N * 8, st>>>(a);
         } else {
-            k_select_minfill<false><<<1, SEL_THREADS, 0, st>>>(a);
+            k_select_minfill<<<1, SEL_THREADS, 0, st>>>(a);
         }
     }
     else k_select_seq<<<1, 32, 0, st>>>(a);
