@@ -738,7 +738,7 @@ gapsp_status fill_begin(FillRun& r) {
     ta.marks = h->marks; ta.cnt = h->cnt; ta.Dw = Dd; ta.stats = h->stats;
     ta.cnt_base = h->cnt_base; ta.dirty = h->dirty;
     {
-        const size_t row_bytes = (size_t)h->words * 9;  // marks + changed flags
+        const size_t row_bytes = fill_smem_bytes(1, h->words);  // marks + changed flags
         int rpb = (int)((96 * 1024) / row_bytes);
         // 8 rows per block: enough blocks per SM to hide the latency of the
         // tree walks (measured best on the 128x128 workload)

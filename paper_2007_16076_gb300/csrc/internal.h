@@ -87,6 +87,13 @@ cudaError_t launch_tree(const TreeArgs& a, int B, cudaStream_t st, bool pdl = fa
 // Distance operations of the trees handed over by a tree launch (N <= 16384).
 cudaError_t launch_depths(const TreeArgs& a, int B, cudaStream_t st);
 cudaError_t launch_fill(const TreeArgs& a, int B, cudaStream_t st, bool pdl = false);
+// Shared memory of a fill block: its rows of marks (padded by one word) and
+// one "changed" byte per word (rows padded by four bytes).
+__host__ __device__ inline int fill_row_stride(int words) { return words + 1; }
+__host__ __device__ inline int fill_chg_stride(int words) { return words + 4; }
+__host__ __device__ inline size_t fill_smem_bytes(int rows, int words) {
+    return (size_t)rows * (fill_row_stride(words) * 8 + fill_chg_stride(words));
+}
 cudaError_t launch_recount(const TreeArgs& a, cudaStream_t st, bool pdl = false);
 
 struct SelectArgs {

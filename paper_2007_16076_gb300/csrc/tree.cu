@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(1024) k_depths(TreeArgs a) {
 // value; the shared rows are ORed back at the end. A pair found from both of
 // its rows in the same round is written twice with the same value; the
 // counts come from the marks (k_recount), which hold each pair once per row.
-__global__ void k_fill(TreeArgs a) {
+__global__ void __launch_bounds__(256, 4) k_fill(TreeArgs a) {
     extern __shared__ unsigned long long srow[];
     pdl_wait();
     pdl_trigger();
@@ -426,11 +426,14 @@ __global__ void k_fill(TreeArgs a) {
     const int nu = s_nu;
     if (nu == 0) return;
     const int words = a.words;
-    uint8_t* chg = reinterpret_cast<uint8_t*>(srow + (size_t)a.rows_per_block * words);
+    // the shared rows are padded by one word (and their "changed" bytes by
+    // four) so that the same tile of different rows falls in different banks
+    const int rs = fill_row_stride(words), cs = fill_chg_stride(words);
+    uint8_t* chg = reinterpret_cast<uint8_t*>(srow + (size_t)a.rows_per_block * rs);
     for (int i = threadIdx.x; i < nu * words; i += blockDim.x) {
         const int r = i / words, w = i - r * words;
-        srow[i] = ld_cg64(a.marks + (size_t)s_rows[r] * words + w);
-        chg[i] = 0;
+        srow[r * rs + w] = ld_cg64(a.marks + (size_t)s_rows[r] * words + w);
+        chg[r * cs + w] = 0;
     }
     __syncthreads();
     const int items = nu * nsel;
@@ -441,8 +444,8 @@ __global__ void k_fill(TreeArgs a) {
         const uint32_t db = __ldg(drow + b);
         if (b == s || db == UNREACH) continue;
         const ulonglong2* seg = a.seg + (size_t)j * a.N;
-        unsigned long long* myrow = srow + (size_t)bl * words;
-        uint8_t* mychg = chg + (size_t)bl * words;
+        unsigned long long* myrow = srow + (size_t)bl * rs;
+        uint8_t* mychg = chg + (size_t)bl * cs;
         const int tb = s_tile[bl];
         const unsigned long long bbit = 1ull << s_bit[bl];
         bool gained = false;
@@ -518,11 +521,10 @@ __global__ void k_fill(TreeArgs a) {
         if (gained) atomicOr(&s_gain, 1u << bl);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nu * words; i += blockDim.x)
-        if (chg[i]) {
-            const int r = i / words, w = i - r * words;
-            atomicOr(a.marks + (size_t)s_rows[r] * words + w, srow[i]);
-        }
+    for (int i = threadIdx.x; i < nu * words; i += blockDim.x) {
+        const int r = i / words, w = i - r * words;
+        if (chg[r * cs + w]) atomicOr(a.marks + (size_t)s_rows[r] * words + w, srow[r * rs + w]);
+    }
     if (threadIdx.x < nu && ((s_gain >> threadIdx.x) & 1u)) a.dirty[s_rows[threadIdx.x]] = 1;
 }
 
@@ -634,7 +636,7 @@ cudaError_t launch_depths(const TreeArgs& a, int B, cudaStream_t st) {
 cudaError_t launch_fill(const TreeArgs& a, int B, cudaStream_t st, bool pdl) {
     (void)B;
     // mark rows, then one "changed" byte per row word
-    const size_t smem = (size_t)a.rows_per_block * a.words * (sizeof(unsigned long long) + 1);
+    const size_t smem = fill_smem_bytes(a.rows_per_block, a.words);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
