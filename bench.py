@@ -108,11 +108,11 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-# DRAM bytes (read + write) of one k_propagate_smem launch of this workload,
-# from the ncu capture summarised in profiles/k_propagate_smem_blobs128.md
-# (50.4 KB per launch at commit 42d17fe). None whenever the kernel has
-# changed since that capture.
-PROP_DRAM_BYTES = None
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one
+# k_propagate_smem launch of this workload (a lookahead launch at round 40,
+# cold caches), from an ncu capture of the kernel as of commit bd41e49. Set
+# to None whenever the kernel changes.
+PROP_DRAM_BYTES = 33_051_136
 
 
 def rank_max(dist, world: int, x: float, device: str) -> float:
