@@ -334,6 +334,147 @@ __global__ void __launch_bounds__(1024) k_treeC(TreeArgs a) {
     cl.sync();  // no block leaves while another may read its exits
 }
 
+// The tree of one selected source on a cluster of C blocks for larger images
+// (N > 16384, up to 65536): the same strips, parents and records as
+// k_treeC, with 32-bit parents and exits, and the depth sums done in place:
+// pointer jumping over the segment exits, each block owning its strip's
+// entries and reading the others' through distributed shared memory, one
+// cluster barrier per jump. Shared memory: the staged D rows (later the
+// second exit buffer), the staged image, the parents (later the second
+// count buffer), the first count and exit buffers.
+struct TreeWLayout {
+    int hs, smax, pmax;
+    size_t o_par;  // byte offset of the parents
+    __host__ __device__ TreeWLayout(int H, int W, int C) {
+        hs = (((H + C - 1) / C + 7) / 8) * 8;
+        smax = (hs + 2) * W;
+        pmax = hs * W;
+        o_par = ((size_t)smax * 5 + 15) & ~(size_t)15;
+    }
+    __host__ __device__ size_t bytes() const { return o_par + (size_t)pmax * 12 + 16; }
+};
+
+template <int C>
+__global__ void __launch_bounds__(1024) k_treeW(TreeArgs a) {
+    extern __shared__ __align__(16) unsigned char smw[];
+    __shared__ int s_more[2];
+    pdl_wait();
+    pdl_trigger();
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int j = blockIdx.x / C;
+    if (j >= *a.nsel) return;  // all blocks of the cluster leave together
+    const int N = a.N, W = a.W, H = a.H, s = a.sel[j];
+    const TreeWLayout L(H, W, C);
+    const int r0 = min(rank * L.hs, H), r1 = min(r0 + L.hs, H);
+    const int hr0 = r0 > 0 ? r0 - 1 : 0, hr1 = r1 < H ? r1 + 1 : H;
+    const int base = hr0 * W, S = r1 > r0 ? (hr1 - hr0) * W : 0;  // staged pixels [base, base + S)
+    const int p0 = r0 * W, P = (r1 - r0) * W;                     // owned pixels [p0, p0 + P)
+    const int span = L.hs * W;                                    // pixels per strip
+    uint32_t* srow = reinterpret_cast<uint32_t*>(smw);
+    uint8_t* sf = smw + (size_t)L.smax * 4;
+    uint32_t* spar = reinterpret_cast<uint32_t*>(smw + L.o_par);
+    uint32_t* accA = spar + L.pmax;
+    uint32_t* jxA = accA + L.pmax;
+    uint32_t* accB = spar;  // the parents are not needed once the segments are done
+    uint32_t* jxB = srow;   // nor the staged rows once the parents are
+    const uint32_t* drow = a.D + (size_t)s * N;
+    ulonglong2* seg = a.seg + (size_t)j * N;
+    if (threadIdx.x == 0) { s_more[0] = 0; s_more[1] = 0; }
+    for (int v = threadIdx.x; v < S; v += blockDim.x) {
+        srow[v] = __ldcg(drow + base + v);
+        sf[v] = a.f[base + v];
+    }
+    __syncthreads();
+    // parents of the owned pixels (neighbours within the staged rows); parent
+    // + 1, 0 for the root, all ones for unreached pixels
+    const uint32_t* drow_l = srow - base;
+    const uint8_t* sf_l = sf - base;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int b = p0 + i;
+        const int pb = canonical_parent(a, drow_l, sf_l, s, b);
+        spar[i] = drow_l[b] == UNREACH ? 0xFFFFFFFFu : (uint32_t)(pb + 1);
+    }
+    __syncthreads();
+    // segments: a tile's pixels and their in-tile ancestors are all owned
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int v = p0 + i;
+        const uint32_t gv = tile_bit(a, v);
+        const uint32_t t = gv >> 8;
+        unsigned long long m = 1ull << (gv & 63);
+        const uint32_t sv = spar[i];
+        int x = sv == 0xFFFFFFFFu ? -1 : (int)sv - 1;
+        uint32_t gx = x >= 0 ? tile_bit(a, x) : 0;
+        for (int guard = 0; x >= 0 && guard < 64 && (gx >> 8) == t; ++guard) {
+            m |= 1ull << (gx & 63);
+            x = (int)spar[x - p0] - 1;
+            gx = x >= 0 ? tile_bit(a, x) : 0;
+        }
+        const bool reached = sv != 0xFFFFFFFFu;
+        reinterpret_cast<unsigned long long*>(seg + v)[0] = m;
+        accA[i] = reached ? (uint32_t)__popcll(m) : 0u;
+        jxA[i] = reached ? (uint32_t)(x + 1) : 0u;
+    }
+    cl.sync();  // every strip's exits are complete (and its parents dead)
+    // the exits one and two segments ahead
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int v = p0 + i;
+        const int e1 = (int)jxA[i] - 1;
+        int e2 = -1;
+        if (e1 >= 0) {
+            const int re = min(row_of(a, e1) / L.hs, C - 1);
+            e2 = (int)cl.map_shared_rank(jxA, re)[e1 - re * span] - 1;
+        }
+        unsigned long long y = 0;
+        if (e1 >= 0) y = (unsigned long long)(e1 + 1) | ((unsigned long long)(tile_bit(a, e1) >> 8) << 17);
+        if (e2 >= 0) y |= ((unsigned long long)(e2 + 1) << 27) | ((unsigned long long)(tile_bit(a, e2) >> 8) << 44);
+        reinterpret_cast<unsigned long long*>(seg + v)[1] = y;
+    }
+    // depth sums: acc(v) = vertices from v up to the root, summed along the
+    // chain of segment exits by pointer jumping (A -> B -> A ...); the A
+    // buffers are only read until the first cluster barrier below
+    int cur = 0;
+    for (int pass = 0; pass < 32; ++pass) {
+        uint32_t* ac = cur ? accB : accA;
+        uint32_t* jc = cur ? jxB : jxA;
+        uint32_t* an = cur ? accA : accB;
+        uint32_t* jn = cur ? jxA : jxB;
+        int any = 0;
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            const uint32_t j1 = jc[i];
+            uint32_t c = ac[i], j2 = 0;
+            if (j1) {
+                const int e = (int)j1 - 1;
+                const int re = min(row_of(a, e) / L.hs, C - 1);
+                const int li = e - re * span;
+                c += cl.map_shared_rank(ac, re)[li];
+                j2 = cl.map_shared_rank(jc, re)[li];
+            }
+            any |= j2 != 0;
+            an[i] = c;
+            jn[i] = j2;
+        }
+        if (any) s_more[pass & 1] = 1;
+        cl.sync();  // every strip has jumped once; no one reads the old buffers any more
+        int more = 0;
+#pragma unroll
+        for (int r = 0; r < C; ++r) more |= *((volatile int*)cl.map_shared_rank(s_more + (pass & 1), r));
+        if (threadIdx.x == 0) s_more[(pass + 1) & 1] = 0;
+        cur ^= 1;
+        __syncthreads();  // the flag of the next pass is clear before anyone sets it
+        if (!more) break;
+    }
+    const uint32_t* af = cur ? accB : accA;
+    unsigned long long ops = 0;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const uint32_t c = af[i];
+        if (c > 1) ops += (unsigned long long)(c - 1);  // unreached vertices hold 0, the root 1
+    }
+    for (int o = 16; o > 0; o >>= 1) ops += __shfl_down_sync(FULL, ops, o);
+    if ((threadIdx.x & 31) == 0 && ops) atomicAdd(a.stats + S_OPS, ops);
+    cl.sync();  // no block leaves while another may read its shared memory
+}
+
 // Distance operations of one tree from its segment exits and sizes (N <=
 // 16384): acc(v) = number of vertices from v up to the root, summed along
 // the chain of segment exits by pointer jumping; depth(b) = acc(b) - 1.
@@ -619,6 +760,33 @@ cudaError_t launch_tree(const TreeArgs& a, int B, cudaStream_t st, bool pdl) {
         }
         // five 16-bit arrays and the image
         return launch_ex(k_tree<true>, B, 1024, (size_t)a.N * 11, st, pdl, 1, a);
+    }
+    if (a.H >= 64) {
+        // N > 16384 (so H > 64): eight strips of whole tiles, when a cluster
+        // of eight such blocks can be resident at all
+        const TreeWLayout L(a.H, a.W, 8);
+        static bool attr8 = false;
+        if (!attr8) {
+            cudaFuncSetAttribute(k_treeW<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr8 = true;
+        }
+        if (L.bytes() <= 200 * 1024) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(8);
+            cfg.blockDim = dim3(1024);
+            cfg.dynamicSmemBytes = L.bytes();
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = 8;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int clusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&clusters, k_treeW<8>, &cfg) == cudaSuccess && clusters > 0)
+                return launch_ex(k_treeW<8>, 8 * B, 1024, L.bytes(), st, pdl, 8, a);
+            cudaGetLastError();
+        }
     }
     return launch_ex(k_tree<false>, B, 1024, 0, st, pdl, 1, a);
 }

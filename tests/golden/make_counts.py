@@ -23,6 +23,9 @@ WORKLOADS = {
     "blobs128": lambda: synth.batched_128(0),
     "steps256": lambda: synth.steps_256(0),
     "mask256": lambda: synth.mask_256(0),
+    # just above 16384 pixels, width not a multiple of 4: the code paths of
+    # the larger images at a size the oracle simulates in minutes
+    "blobs136x121": lambda: synth.scaled_blobs(136, 121, 8, seed=0, B=32),
 }
 
 

@@ -342,6 +342,34 @@ def test_full_size_blobs128(gp, order):
 
 
 # --------------------------------------------------------------------------
+# Just above 16384 pixels: the larger images' code paths (eight-strip tree
+# clusters with their own depth sums, selection without the key cache,
+# one value per lane where the width is not a multiple of 4)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("order", ["minfill", "extrema"])
+def test_counts_blobs136x121(gp, order):
+    """136x121 (N = 16456), 8-connected, B = 32: counts, per-round new pairs
+    and the selected sources against the oracle's stored simulation, and the
+    whole array against Dijkstra from every pixel."""
+    path = os.path.join(GOLDEN, "counts_blobs136x121.json")
+    if not os.path.exists(path):
+        pytest.skip("counts fixture not generated")
+    gold_all = json.load(open(path))["orders"]
+    if order not in gold_all:
+        pytest.skip(f"{order} counts not generated")
+    gold = gold_all[order]
+    w = synth.scaled_blobs(136, 121, 8, seed=0, B=32)
+    with gp.Image(w.img, conn=w.conn, B=w.B, seed=0) as im:
+        D, st = im.all_pairs(order, want_log=True)
+    for k in ("propagations", "prepass_propagations", "distance_ops", "new_pairs", "rounds"):
+        assert st[k] == gold[k], k
+    assert [int(x) for x in st["round_new"]] == gold["round_new"]
+    assert hashlib.sha256(st["sources"].astype("<i4").tobytes()).hexdigest() == gold["sources_sha256"]
+    assert np.array_equal(_u32(D), oracle.apsp(w.img, conn=w.conn))
+
+
+# --------------------------------------------------------------------------
 # Full-size 256x256 workloads (17.2 GB array on the device)
 # --------------------------------------------------------------------------
 
