@@ -346,68 +346,13 @@ __device__ void finish_selection(const SelectArgs& a, int want, int top, SelScra
     }
 }
 
-// Minfill / extrema selection for N > 16384: the keys are recomputed from
-// the counts at every pass.
-__global__ void __launch_bounds__(SEL_THREADS) k_select_minfill(SelectArgs a) {
-    __shared__ SelScratch sc;
-    __shared__ int s_count, s_unfilled, s_nsel, s_ncand;
-    __shared__ unsigned long long s_keys[1024], s_selk[1024];
-    __shared__ int s_pix[1024], s_selp[1024];
-    const int tid = threadIdx.x, lane = tid & 31;
-    if (*a.done) {
-        if (tid == 0) {
-            *a.nsel = 0;
-            if (a.ncand) *a.ncand = 0;
-        }
-        return;
-    }
-    if (tid == 0) { s_unfilled = 0; s_count = 0; s_nsel = 0; s_ncand = 0; }
-    __syncthreads();
-    int mine = 0;
-    for (int p = tid; p < a.N; p += SEL_THREADS) {
-        mine += mf_key(a, p) != ~0ull;
-    }
-    for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(FULL, mine, o);
-    if (lane == 0 && mine) atomicAdd(&s_unfilled, mine);
-    __syncthreads();
-    auto key = [&](int p) -> unsigned long long { return mf_key(a, p); };
-    const int unfilled = s_unfilled;
-    const int want = min(unfilled, a.B);
-    // the selection, then the next KL points in key order, from which the
-    // lookahead candidates are taken
-    const int wantc = min(unfilled, a.B + (a.K > 0 ? a.KL : 0));
-    // keys have 17 bits per field below the top one
-    int top = a.order == 3 ? 34 : 17;
-    for (int n = a.N - 1; n > 0; n >>= 1) ++top;
-    unsigned long long thr = ~0ull - 1;  // gather keys <= thr
-    if (wantc > 0 && wantc < unfilled) thr = radix_select(key, a.N, wantc, top, sc);
-    // gather (one shared atomic per warp)
-    if (want > 0) {
-        for (int p0 = 0; p0 < a.N; p0 += SEL_THREADS) {
-            const int p = p0 + tid;
-            const unsigned long long k = p < a.N ? key(p) : ~0ull;
-            const bool take = k != ~0ull && k <= thr;
-            const unsigned m = __ballot_sync(FULL, take);
-            int base = 0;
-            if (lane == 0 && m) base = atomicAdd(&s_count, __popc(m));
-            base = __shfl_sync(FULL, base, 0);
-            if (take) {
-                const int slot = base + __popc(m & ((1u << lane) - 1u));
-                if (slot < 1024) { s_keys[slot] = k; s_pix[slot] = p; }
-            }
-        }
-    }
-    __syncthreads();
-    finish_selection(a, want, top, sc, s_count, s_keys, s_pix, s_selk, s_selp, s_nsel, s_ncand);
-}
-
-// The same selection for N <= 16384, with fewer passes over the points.
-// Keys order first by a leading field v (cnt for minfill, grank for extrema)
+// Minfill / extrema selection, one block. Keys order first by a leading field v (cnt for minfill, grank for extrema)
 // that never decreases for a point, and the unfilled set only shrinks, so
 // the least v among the unfilled points never decreases from round to round
 // (a.vfloor keeps last round's). One pass computes the keys, packs the
-// unfilled ones (with their point) into shared memory, and counts them by
-// v - vfloor (2048 bins, the last one for everything beyond). When the
+// unfilled ones (with their point) into shared memory when they fit (CACHE,
+// N <= 16384; otherwise later passes read the counts again), and counts
+// them by v - vfloor (2048 bins, the last one for everything beyond). When the
 // (B + KL)-th smallest key falls in a bin below the last and at most WIN
 // keys have a v up to that bin's, those keys are the window the selection
 // and the candidates come from (every key with a smaller v is smaller, so
@@ -431,9 +376,9 @@ __device__ __forceinline__ uint32_t lead_field(unsigned long long k) {
     return ORDER == 3 ? (uint32_t)(k >> 34) : (uint32_t)(k >> 17);
 }
 
-template <int ORDER>
+template <int ORDER, bool CACHE>
 __global__ void __launch_bounds__(SEL_THREADS) k_select_small(SelectArgs a) {
-    extern __shared__ unsigned long long spk[];  // packed keys of the unfilled points
+    extern __shared__ unsigned long long spk[];  // CACHE: packed keys of the unfilled points
     __shared__ SelScratch sc;
     __shared__ int s_count, s_nsel, s_ncand;
     __shared__ unsigned s_vmin;
@@ -488,7 +433,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_small(SelectArgs a) {
             const bool in = k != ~0ull;
             unsigned dig = (unsigned)(NBIN - 1);
             if (in) {
-                spk[w++] = packed_key<ORDER>(k, q);
+                if (CACHE) spk[w++] = packed_key<ORDER>(k, q);
                 const uint32_t v = lead_field<ORDER>(k);
                 vmin = min(vmin, v);
                 if (v < vfloor) s_below = 1;  // not expected: the floor never passes a key
@@ -559,18 +504,47 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_small(SelectArgs a) {
         // the window: every key whose v is at most that bin's (the
         // (B + KL)-th key among them), gathered in one pass
         const uint32_t vmax = vfloor + (uint32_t)bstar;
-        for (int i0 = 0; i0 < unfilled; i0 += SEL_THREADS) {
-            const int i = i0 + tid;
-            const unsigned long long pk = i < unfilled ? spk[i] : ~0ull;
-            const bool take = i < unfilled && lead_field<ORDER>(unpack_key<ORDER>(pk)) <= vmax;
+        auto gather = [&](bool take, unsigned long long k, int p) {
             const unsigned m = __ballot_sync(FULL, take);
             int base = 0;
             if (lane == 0 && m) base = atomicAdd(&s_count, __popc(m));
             base = __shfl_sync(FULL, base, 0);
             if (take) {
                 const int slot = base + __popc(m & ((1u << lane) - 1u));
-                s_keys[slot] = unpack_key<ORDER>(pk);
-                s_pix[slot] = unpack_point<ORDER>(pk);
+                s_keys[slot] = k;
+                s_pix[slot] = p;
+            }
+        };
+        if (CACHE) {
+            for (int i0 = 0; i0 < unfilled; i0 += SEL_THREADS) {
+                const int i = i0 + tid;
+                const unsigned long long pk = i < unfilled ? spk[i] : ~0ull;
+                const bool take = i < unfilled && lead_field<ORDER>(unpack_key<ORDER>(pk)) <= vmax;
+                gather(take, unpack_key<ORDER>(pk), unpack_point<ORDER>(pk));
+            }
+        } else {
+            // the keys again from the counts, LD points per thread at a time
+            for (int b0 = 0; b0 < a.N; b0 += LD * SEL_THREADS) {
+                uint32_t cv[LD];
+                int32_t rv[LD], gv[LD];
+#pragma unroll
+                for (int u = 0; u < LD; ++u) {
+                    const int q = b0 + u * SEL_THREADS + tid;
+                    cv[u] = (uint32_t)a.N;
+                    rv[u] = -1;
+                    gv[u] = 0;
+                    if (q < a.N) {
+                        cv[u] = __ldcg(a.cnt + q);
+                        rv[u] = __ldg(a.rank + q);
+                        if (ORDER == 3) gv[u] = __ldg(a.grank + q);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < LD; ++u) {
+                    const int q = b0 + u * SEL_THREADS + tid;
+                    const unsigned long long k = q < a.N ? key_of(ORDER, a.N, cv[u], rv[u], gv[u], q) : ~0ull;
+                    gather(k != ~0ull && lead_field<ORDER>(k) <= vmax, k, q);
+                }
             }
         }
         __syncthreads();
@@ -603,12 +577,16 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_small(SelectArgs a) {
     } else if (want > 0) {
         // the window: the (B + KL) smallest keys, by radix selection over
         // all of them
-        auto keyf = [&](int i) -> unsigned long long { return unpack_key<ORDER>(spk[i]); };
+        // (over the cache, or over the counts again at every pass)
+        const int n = CACHE ? unfilled : a.N;
+        auto keyf = [&](int i) -> unsigned long long {
+            return CACHE ? unpack_key<ORDER>(spk[i]) : mf_key(a, i);
+        };
         unsigned long long thr = ~0ull - 1;
-        if (wantc < unfilled) thr = radix_select(keyf, unfilled, wantc, top, sc);
-        for (int i0 = 0; i0 < unfilled; i0 += SEL_THREADS) {
+        if (wantc < unfilled) thr = radix_select(keyf, n, wantc, top, sc);
+        for (int i0 = 0; i0 < n; i0 += SEL_THREADS) {
             const int i = i0 + tid;
-            const unsigned long long k = i < unfilled ? keyf(i) : ~0ull;
+            const unsigned long long k = i < n ? keyf(i) : ~0ull;
             const bool take = k != ~0ull && k <= thr;
             const unsigned m = __ballot_sync(FULL, take);
             int base = 0;
@@ -616,7 +594,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select_small(SelectArgs a) {
             base = __shfl_sync(FULL, base, 0);
             if (take) {
                 const int slot = base + __popc(m & ((1u << lane) - 1u));
-                if (slot < WIN) { s_keys[slot] = k; s_pix[slot] = unpack_point<ORDER>(spk[i]); }
+                if (slot < WIN) { s_keys[slot] = k; s_pix[slot] = CACHE ? unpack_point<ORDER>(spk[i]) : i; }
             }
         }
     }
@@ -920,14 +898,16 @@ cudaError_t launch_select(const SelectArgs& a, cudaStream_t st) {
         if (a.N <= 16384) {
             static bool attr = false;
             if (!attr) {
-                cudaFuncSetAttribute(k_select_small<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 8);
-                cudaFuncSetAttribute(k_select_small<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 8);
+                cudaFuncSetAttribute(k_select_small<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 8);
+                cudaFuncSetAttribute(k_select_small<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 8);
                 attr = true;
             }
-            if (a.order == 2) k_select_small<2><<<1, SEL_THREADS, (size_t)a.N * 8, st>>>(a);
-            else k_select_small<3><<<1, SEL_THREADS, (size_t)a.N * 8, st>>>(a);
+            if (a.order == 2) k_select_small<2, true><<<1, SEL_THREADS, (size_t)a.N * 8, st>>>(a);
+            else k_select_small<3, true><<<1, SEL_THREADS, (size_t)a.N * 8, st>>>(a);
         } else {
-            k_select_minfill<<<1, SEL_THREADS, 0, st>>>(a);
+            // the keys do not fit in shared memory: read from the counts
+            if (a.order == 2) k_select_small<2, false><<<1, SEL_THREADS, 0, st>>>(a);
+            else k_select_small<3, false><<<1, SEL_THREADS, 0, st>>>(a);
         }
     }
     else k_select_seq<<<1, 32, 0, st>>>(a);
