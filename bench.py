@@ -115,6 +115,21 @@ class Clocks:
 PROP_DRAM_BYTES = 33_051_136
 
 
+THROTTLE = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
+
+
+def clocks_rejected(clk: dict) -> bool:
+    """Whether a timed region's clock record disqualifies it: a hardware or
+    thermal slowdown was active, or the SM clock stayed well below its
+    maximum with no reason given (a clock left locked). sw_power_cap alone
+    is kept (and shows in the record)."""
+    reasons = clk.get("reasons") or []
+    if any(r in reasons for r in THROTTLE):
+        return True
+    sm, smax = clk.get("sm_mhz"), clk.get("sm_max_mhz")
+    return bool(sm and smax and sm < 0.85 * smax and "sw_power_cap" not in reasons)
+
+
 def rank_max(dist, world: int, x: float, device: str) -> float:
     """The largest value of x over the ranks (the slowest rank's time)."""
     if world == 1:
@@ -292,31 +307,46 @@ def run_ours(a):
         flush.fill_(1)  # the first use of the flush kernel loads its module: not in the timed steps
         _, st = im.all_pairs("minfill", out=D)
 
-    l0 = im.kernel_launches
-    barrier()
-    ev_a = torch.cuda.Event(enable_timing=True)
-    ev_b = torch.cuda.Event(enable_timing=True)
-    step_ms = []
-    ev_a.record(stream)
-    for _ in range(a.steps):
-        flush.fill_(1)  # L2 (129 MB) flushed between steps
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        _, st = im.all_pairs("minfill", out=D)
-        e1.record(stream)
-        step_ms.append((e0, e1))
-    ev_b.record(stream)
-    barrier()
+    def timed():
+        """The timed steps: (total ms, per-step event pairs, launches, last stats)."""
+        l0 = im.kernel_launches
+        barrier()
+        ev_a = torch.cuda.Event(enable_timing=True)
+        ev_b = torch.cuda.Event(enable_timing=True)
+        pairs = []
+        st = None
+        ev_a.record(stream)
+        for _ in range(a.steps):
+            flush.fill_(1)  # L2 (129 MB) flushed between steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, st = im.all_pairs("minfill", out=D)
+            e1.record(stream)
+            pairs.append((e0, e1))
+        ev_b.record(stream)
+        barrier()
+        return ev_a.elapsed_time(ev_b), pairs, im.kernel_launches - l0, st
+
+    total_ms, step_ms, launches, st = timed()
     if a.timed_only:
         clocks.stop()
         im.close()
         if world > 1:
             dist.destroy_process_group()
         return
-    total_ms = ev_a.elapsed_time(ev_b)
-    launches = im.kernel_launches - l0
     clk = clocks.stop()
+    remeasured = None
+    # a throttled or clock-locked run is measured once more (every rank
+    # decides alike: the flag is taken over the ranks)
+    if allmax(1.0 if clocks_rejected(clk) else 0.0) > 0.0:
+        remeasured = {"first_clocks": clk, "first_ms_per_step": total_ms / a.steps}
+        clocks = Clocks(local)
+        clocks.start()
+        time.sleep(1.0)
+        im.all_pairs("minfill", out=D)
+        total_ms, step_ms, launches, st = timed()
+        clk = clocks.stop()
     fill_ms = sum(e0.elapsed_time(e1) for e0, e1 in step_ms)
     total_ms = allmax(total_ms)
     ms_per_step = total_ms / a.steps
@@ -473,6 +503,8 @@ def run_ours(a):
             "gpu_launches": int(launches),
             "clocks": clk,
         }
+        if remeasured is not None:
+            line["remeasured"] = remeasured
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

@@ -63,3 +63,16 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.rank_max(None, 1, 42.0, "cpu") == 42.0
     assert bench.job_throughput(100.0, 2, 1, 1000.0) == pytest.approx(200.0)
+
+
+def test_clock_records_rejected():
+    """Throttled or clock-locked timed regions are measured again; a power
+    cap alone is kept."""
+    import bench
+    ok = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}
+    assert not bench.clocks_rejected(ok)
+    assert not bench.clocks_rejected({**ok, "reasons": ["sw_power_cap"], "sm_mhz": 1500.0})
+    for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
+        assert bench.clocks_rejected({**ok, "reasons": [r]})
+    assert bench.clocks_rejected({**ok, "sm_mhz": 1200.0})  # locked well below the maximum
+    assert not bench.clocks_rejected({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]})
