@@ -24,8 +24,10 @@
  *     filling rate"); the last two take the extrema pre-pass of Sec. 3.3 (two
  *     more propagations).
  *
- * An obstacle-mask variant is included: w = 2 between free pixels, obstacle
- * pixels have no edges, and pairs that no path joins hold GAPSP_UNREACH.
+ * Two more edge costs are included: the L1 pseudo-metric of Sec. 2 (eq.
+ * "distance abs difference"), w = |f(p) - f(q)| + 1, and an obstacle mask:
+ * w = 2 between free pixels, obstacle pixels have no edges, and pairs that no
+ * path joins hold GAPSP_UNREACH.
  *
  * Data layout. Images are H x W, row-major, pixel p = r*W + c, N = H*W.
  * D is row-major uint32 N x N: D[p*N + q] = d(p,q). D[p][p] = 0, D is
