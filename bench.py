@@ -1,15 +1,18 @@
 #!/usr/bin/env python
 """Benchmark: exact all-pairs geodesic distance entries per second on GB300.
 
-Workload: the 128x128 blob image (N = 16384, 268M-entry uint32 array),
-8-connected, w(p,q) = f(p) + f(q) + 1, B = 32 sources per round. One step is
-one complete gapsp_all_pairs fill in the minimum-filling-rate order (the
-paper's method: extrema pre-pass, then rounds of selection, propagation,
-tree and fill). `value` = N^2 entries per step / step time, summed over
-ranks. The naive, spiral, spiral-with-repulsion and extrema orders and the naive method without the tree
-(one propagation per pixel, gapsp_rows) are timed beside it.
+Default workload: the 256x256 image of blobs and 20 step edges (N = 65536,
+4.29e9-entry uint32 array, 17.2 GB), 8-connected, w(p,q) = f(p) + f(q) + 1,
+B = 32 sources per round. One step is one complete gapsp_all_pairs fill in
+the minimum-filling-rate order (the paper's method: extrema pre-pass, then
+rounds of selection, propagation, tree and fill). `value` = N^2 entries per
+step / step time, summed over ranks. Beside it: the naive, spiral,
+spiral-with-repulsion and extrema orders, the naive method without the tree
+(one propagation per pixel, gapsp_rows), the 256x256 obstacle-mask and the
+128x128 blob workloads, the batched form and the serving run.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload steps256|mask256|blobs128]
 Multi-GPU runs are independent replicas (the fill does not shard), launched
 with torch.distributed.run; rank 0 prints one JSON line.
 """
@@ -38,7 +41,8 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--side", type=int, default=128, help="image side (128 = the workload)")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="steps256",
+                    help="the timed image (default: 256x256 blobs with step edges)")
     ap.add_argument("--no-extras", action="store_true", help="skip the side measurements")
     ap.add_argument("--serve-seconds", type=float, default=4.0,
                     help="length of the simulated serving run among the side measurements")
@@ -47,13 +51,19 @@ def _args():
     return ap.parse_args()
 
 
-def _workload(side: int, rank: int):
+# name -> synth factory (every one 8-connected, B = 32)
+WORKLOADS = {"steps256": "steps_256", "mask256": "mask_256", "blobs128": "batched_128"}
+
+
+def _workload(name: str, rank: int):
     from paper_2007_16076_gb300 import synth
-    if side == 128:
-        w = synth.batched_128(seed=rank)
-    else:
-        w = synth.scaled_blobs(side, side, 8, seed=rank, B=32)
-    return w
+    return getattr(synth, WORKLOADS[name])(seed=rank)
+
+
+def _image(gp, w, stream, **kw):
+    """A handle on workload w (grey or mask kind)."""
+    img = w.img if w.kind != "mask" else None
+    return gp.Image(img, conn=w.conn, kind=w.kind, mask=w.mask, B=w.B, seed=0, stream=stream, **kw)
 
 
 class Clocks:
@@ -108,11 +118,10 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one
-# k_propagate_smem launch of this workload (a lookahead launch at round 40,
-# cold caches), from an ncu capture of the kernel as of commit bd41e49. Set
-# to None whenever the kernel changes.
-PROP_DRAM_BYTES = 33_051_136
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the dominant kernel per workload, from an ncu capture, with the launch it
+# came from; None when no capture of the kernel as it stands exists.
+DRAM_BYTES = {}
 
 
 THROTTLE = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
@@ -220,18 +229,21 @@ def _peaks():
         return {}
 
 
-def _cpu_baseline(img, conn, N, budget_s=12.0):
-    """The oracle as it stands: Dijkstra rows on all host cores, bounded."""
+def _cpu_baseline(w, budget_s=12.0):
+    """The oracle as it stands: Dijkstra rows on all host cores, a bounded
+    sample of the workload's sources (entries/s of the rows it computes)."""
     import numpy as np
 
     import oracle
+    N = w.N
     threads = os.cpu_count() or 1
     k = max(threads, 64)
     done = 0
     t0 = time.perf_counter()
     while True:
-        src = (np.arange(k, dtype=np.int32) * 7919 + done) % N
-        oracle.rows(img, src, conn=conn, threads=threads)
+        src = (np.arange(k, dtype=np.int64) * 7919 + done) % N
+        oracle.rows(w.img, src.astype(np.int32), conn=w.conn, kind=w.kind, mask=w.mask,
+                    threads=threads)
         done += k
         el = time.perf_counter() - t0
         if el > budget_s or done >= N:
@@ -247,12 +259,11 @@ def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import numpy as np  # noqa: F401
-    w = _workload(a.side, 0)
+    w = _workload(a.workload, 0)
     per = []
     base = None
     for i in range(a.warmup + a.steps):
-        cb = _cpu_baseline(w.img, w.conn, w.N, budget_s=8.0)
+        cb = _cpu_baseline(w, budget_s=8.0 if i >= a.warmup else 2.0)
         if i >= a.warmup:
             per.append(cb["value"])
             base = cb
@@ -262,10 +273,167 @@ def run_reference(a):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
             "config": {"workload": w.name, "H": w.H, "W": w.W, "N": w.N, "conn": w.conn, "B": w.B,
-                       "order": "minfill", "note": "oracle Dijkstra rows, bounded sample per step"},
+                       "kind": w.kind, "order": "minfill",
+                       "note": "oracle Dijkstra rows, bounded sample per step"},
             "cpu_baseline": {**base, "value": v},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _timed_call(torch, stream, flush, fn):
+    """Device time (ms) of fn() on `stream`, L2 flushed first; returns (ms, fn's result)."""
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    flush.fill_(1)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def _free_pixels(w) -> int:
+    return int(w.mask.astype(bool).sum()) if w.kind == "mask" else w.N
+
+
+def roofline(w, st, prof, ms_per_step, peaks, dram=None) -> dict:
+    """Roofline entries of one fill from its counts `st` and the per-kernel
+    device time `prof` ({kernel: (ms, launches)}) of `nfill` profiled fills.
+
+    - step: the array itself, 4 N^2 bytes written once per fill, over the step time;
+    - fill (k_fill): 8 bytes per new pair (D[a][b] and D[b][a]) over the fill
+      launches' time: the kernel's algorithmic DRAM bytes;
+    - propagate (k_propagate_*, the rounds' own launches and the lookahead
+      launches): 2 conn relaxations per free pixel (every edge once from each
+      end) for each of the method's own P + 2 propagations, over the time of
+      every propagation launch (rows computed ahead and never used count as
+      time, not as work), against the plain int32 add/min rate.
+    The dominant kernel (most device time) is the line's `roofline`.
+    """
+    nfill = prof.pop("_fills")
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    N = w.N
+    step = {"bound": "hbm", "achieved": 4.0 * N * N / (ms_per_step / 1e3) / 1e9, "peak": hbm,
+            "unit": "GB/s", "algorithmic_bytes": 4.0 * N * N, "peak_source": peak_src}
+    step["frac"] = step["achieved"] / hbm
+    fill_ms, fill_n = prof["fill"]
+    alg_fill = 8.0 * st["new_pairs"] * nfill
+    fill = {"kernel": "k_fill", "bound": "hbm",
+            "achieved": alg_fill / (fill_ms / 1e3) / 1e9 if fill_ms else 0.0, "peak": hbm,
+            "unit": "GB/s", "peak_source": peak_src,
+            "algorithmic_bytes_per_launch": alg_fill / max(fill_n, 1),
+            "avg_launch_ms": fill_ms / max(fill_n, 1), "traffic": None}
+    fill["frac"] = fill["achieved"] / hbm
+    ghz = (peaks.get("sm_max_mhz") or 2070.0) / 1e3
+    peak_relax = 152 * 128 * ghz * 1e9 / 2 / 1e12
+    prop_ms = prof["propagate"][0] + prof["lookahead"][0]
+    prop_n = prof["propagate"][1] + prof["lookahead"][1]
+    own = (st["propagations"] + st["prepass_propagations"]) * nfill
+    relax = 2.0 * w.conn * _free_pixels(w) * own
+    prop = {"kernel": "k_propagate", "bound": "alu",
+            "achieved": relax / (prop_ms / 1e3) / 1e12 if prop_ms else 0.0, "peak": peak_relax,
+            "unit": "T relax/s",
+            "peak_source": "derived: 152 SMs x 128 int32 lanes x max SM clock, 2 ops per relaxation",
+            "algorithmic_relaxations_per_launch": relax / max(prop_n, 1),
+            "avg_launch_ms": prop_ms / max(prop_n, 1), "traffic": None,
+            "rows_counted": "the method's own P + 2 propagations per fill"}
+    prop["frac"] = prop["achieved"] / peak_relax
+    if dram:
+        tgt = fill if dram["kernel"] == "k_fill" else prop
+        tgt["traffic"] = dram["bytes"]
+        tgt["traffic_launch"] = dram["launch"]
+    tot = sum(v[0] for v in prof.values())
+    dom = fill if fill_ms >= prop_ms else prop
+    out = dict(dom)
+    out["step_hbm"] = step
+    out["kernels"] = {"fill": fill, "propagate": prop}
+    out["kernel_share"] = {k: round(v[0] / tot, 4) for k, v in prof.items() if v[1]}
+    out["kernel_ms_per_fill"] = {k: round(v[0] / nfill, 3) for k, v in prof.items() if v[1]}
+    out["kernel_launches_per_fill"] = {k: v[1] // nfill for k, v in prof.items() if v[1]}
+    return out
+
+
+def _profile(im, D, flush, nfill=2):
+    """Per-kernel device time over `nfill` fills (a separate, event-bracketed pass)."""
+    im.profile(True)
+    im.profile_read()
+    for _ in range(nfill):
+        flush.fill_(1)
+        im.all_pairs("minfill", out=D)
+    prof = im.profile_read()
+    im.profile(False)
+    prof["_fills"] = nfill
+    return prof
+
+
+def _extras(a, gp, torch, w, im, D, flush, stream) -> dict:
+    """Side measurements on the same GPU: the other orders, the naive method
+    without trees, the other workloads, the batched form and serving."""
+    import numpy as np
+
+    from paper_2007_16076_gb300 import synth
+    N = w.N
+    entries = float(N) * N
+    ex = {}
+    for order in ("naive", "spiral", "extrema", "repulsion"):
+        ms, (_, so) = _timed_call(torch, stream, flush, lambda: im.all_pairs(order, out=D))
+        ex[order] = {"ms": ms, "entries_per_s": entries / (ms / 1e3),
+                     "propagations": so["propagations"], "rounds": so["rounds"],
+                     "distance_ops": so["distance_ops"]}
+    src = torch.arange(N, dtype=torch.int32, device="cuda")
+    im.rows(src[:64], out=D)
+    ms, _ = _timed_call(torch, stream, flush, lambda: im.rows(src, out=D))
+    ex["naive_full_rows"] = {"ms": ms, "entries_per_s": entries / (ms / 1e3), "propagations": N,
+                             "propagations_per_s": N / (ms / 1e3),
+                             "note": "gapsp_rows over all N sources: one propagation per pixel, no tree"}
+    # the other workloads of the same family, minimum filling rate
+    others = {}
+    for name in WORKLOADS:
+        if name == a.workload:
+            continue
+        wo = _workload(name, 0)
+        Do = D.view(-1)[: wo.N * wo.N].view(wo.N, wo.N)
+        with _image(gp, wo, stream) as io:
+            io.all_pairs("minfill", out=Do)
+            ms, (_, so) = _timed_call(torch, stream, flush, lambda: io.all_pairs("minfill", out=Do))
+            rec = {"ms": ms, "entries_per_s": float(wo.N) ** 2 / (ms / 1e3),
+                   "propagations": so["propagations"], "rounds": so["rounds"]}
+            srco = torch.arange(wo.N, dtype=torch.int32, device="cuda")
+            msr, _ = _timed_call(torch, stream, flush, lambda: io.rows(srco, out=Do))
+            rec["naive_full_rows_ms"] = msr
+            rec["naive_full_rows_entries_per_s"] = float(wo.N) ** 2 / (msr / 1e3)
+        others[wo.name] = rec
+    ex["other_workloads"] = others
+    # batched form: 64 images of uneven sizes filled side by side, against
+    # the same images one at a time
+    ws = synth.batch_64(seed=0)
+    ims = [gp.Image(b.img, conn=b.conn, B=b.B, stream=stream) for b in ws]
+    outs = [torch.empty((b.N, b.N), dtype=torch.int32, device="cuda") for b in ws]
+    gp.all_pairs_batch(ims, "minfill", outs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, bst = gp.all_pairs_batch(ims, "minfill", outs)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for imb, ob in zip(ims, outs):
+        imb.all_pairs("minfill", out=ob)
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t0
+    ent = float(sum(b.N * b.N for b in ws))
+    ex["batch64_minfill"] = {
+        "images": len(ws), "entries": ent, "array_bytes": 4 * ent,
+        "ms": tb * 1e3, "entries_per_s": ent / tb, "one_at_a_time_ms": ts * 1e3,
+        "one_at_a_time_entries_per_s": ent / ts,
+        "propagations": int(sum(x["propagations"] for x in bst))}
+    for imb in ims:
+        imb.close()
+    del outs
+    ex["serve"] = _serve(gp, torch, stream, seconds=a.serve_seconds)
+    return ex
 
 
 def run_ours(a):
@@ -290,10 +458,10 @@ def run_ours(a):
     def allmax(x: float) -> float:
         return rank_max(dist, world, x, "cuda")
 
-    w = _workload(a.side, rank)
+    w = _workload(a.workload, rank)
     N = w.N
     stream = torch.cuda.current_stream()
-    im = gp.Image(w.img, conn=w.conn, B=w.B, seed=0, stream=stream)
+    im = _image(gp, w, stream)
     D = torch.empty((N, N), dtype=torch.int32, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
 
@@ -354,134 +522,37 @@ def run_ours(a):
     value = job_throughput(entries, a.steps, world, total_ms)
     props = st["propagations"]
 
-    # per-kernel device time (a separate, event-bracketed pass)
-    im.profile(True)
-    im.profile_read()
-    for _ in range(2):
-        flush.fill_(1)
-        im.all_pairs("minfill", out=D)
-    prof = im.profile_read()
-    im.profile(False)
-    ksum = {k: v for k, v in prof.items() if v[1] > 0}
-    tot_k = sum(v[0] for v in ksum.values())
-    dom = max(ksum, key=lambda k: ksum[k][0])
-    if dom == "lookahead":
-        dom = "propagate"
-    peaks = _peaks()
-    hbm = peaks.get("hbm_gbs")
-    peak_src = "measured" if hbm else "fallback"
-    hbm = hbm or 6800.0
-    # Algorithmic bytes of the tree fill: every off-diagonal entry of D is
-    # written exactly once per fill, 4 (N^2 - N) bytes, spread over the
-    # fill launches of the rounds that did work.
-    rounds = st["rounds"]
-    fill_ms_k, fill_n = prof["fill"]
-    # the propagation kernel runs both for the round's own sources and, on a
-    # second stream, for the candidates computed ahead: both count
-    prop_ms_k = prof["propagate"][0] + prof["lookahead"][0]
-    prop_n = prof["propagate"][1] + prof["lookahead"][1]
-    if dom == "fill":
-        alg = 2 * 4.0 * (N * N - N)
-        achieved = alg / (fill_ms_k / 1e3) / 1e9 if fill_ms_k else 0.0
-        roof = {"kernel": "k_fill", "bound": "hbm", "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "traffic": None, "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": alg / (2 * rounds),
-                "avg_launch_ms": fill_ms_k / (2 * rounds)}
-    else:
-        # the relaxation is plain int32 add/min work: peak from the unit counts
-        ghz = (peaks.get("sm_max_mhz") or 2070.0) / 1e3
-        peak_relax = 152 * 128 * ghz * 1e9 / 2 / 1e12  # T relaxations/s, 2 ops each
-        # rows actually computed in the two profiled fills: the round's own
-        # sources not computed ahead, the lookahead rows, the pre-pass
-        rows_run = props - st["lookahead_hits"] + st["lookahead_propagations"] + st["prepass_propagations"]
-        relax = 2.0 * w.conn * N * rows_run
-        achieved = relax / (prop_ms_k / 1e3) / 1e12 if prop_ms_k else 0.0
-        roof = {"kernel": "k_propagate", "bound": "alu", "achieved": achieved, "peak": peak_relax,
-                "unit": "T relax/s", "frac": achieved / peak_relax, "traffic": PROP_DRAM_BYTES,
-                "peak_source": "derived: 152 SMs x 128 int32 lanes x max SM clock, 2 ops each",
-                "algorithmic_relaxations_per_launch": relax / max(prop_n, 1),
-                "avg_launch_ms": prop_ms_k / max(prop_n, 1)}
-    roof["kernel_share"] = {k: round(v[0] / tot_k, 4) for k, v in ksum.items()}
-    roof["kernel_ms_per_fill"] = {k: round(v[0] / 2, 3) for k, v in ksum.items()}
-    roof["kernel_launches_per_fill"] = {k: v[1] // 2 for k, v in ksum.items()}
+    prof = _profile(im, D, flush)
+    roof = roofline(w, st, prof, ms_per_step, _peaks(), DRAM_BYTES.get(a.workload))
 
-    extras = {}
-    if not a.no_extras:
-        for order in ("naive", "spiral", "repulsion", "extrema"):
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            flush.fill_(1)
-            e0.record(stream)
-            _, so = im.all_pairs(order, out=D)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1)
-            extras[order] = {"ms": ms, "entries_per_s": entries / (ms / 1e3),
-                             "propagations": so["propagations"], "rounds": so["rounds"],
-                             "distance_ops": so["distance_ops"]}
-        src = torch.arange(N, dtype=torch.int32, device="cuda")
-        im.rows(src, out=D)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        flush.fill_(1)
-        e0.record(stream)
-        im.rows(src, out=D)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        extras["naive_full_rows"] = {"ms": ms, "entries_per_s": entries / (ms / 1e3),
-                                     "propagations": N, "propagations_per_s": N / (ms / 1e3)}
-        # batched form: 64 images of uneven sizes filled side by side, against
-        # the same images one at a time
-        from paper_2007_16076_gb300 import synth
-        ws = synth.batch_64(seed=0)
-        ims = [gp.Image(b.img, conn=b.conn, B=b.B, stream=stream) for b in ws]
-        outs = [torch.empty((b.N, b.N), dtype=torch.int32, device="cuda") for b in ws]
-        gp.all_pairs_batch(ims, "minfill", outs)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        _, bst = gp.all_pairs_batch(ims, "minfill", outs)
-        torch.cuda.synchronize()
-        tb = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        for imb, ob in zip(ims, outs):
-            imb.all_pairs("minfill", out=ob)
-        torch.cuda.synchronize()
-        ts = time.perf_counter() - t0
-        ent = float(sum(b.N * b.N for b in ws))
-        extras["batch64_minfill"] = {
-            "images": len(ws), "entries": ent, "array_bytes": 4 * ent,
-            "ms": tb * 1e3, "entries_per_s": ent / tb, "one_at_a_time_ms": ts * 1e3,
-            "one_at_a_time_entries_per_s": ent / ts,
-            "propagations": int(sum(x["propagations"] for x in bst))}
-        for imb in ims:
-            imb.close()
-        del outs
-        extras["serve"] = _serve(gp, torch, stream, seconds=a.serve_seconds)
+    extras = {} if a.no_extras else _extras(a, gp, torch, w, im, D, flush, stream)
 
     # end to end through the C ABI with host buffers: create from a host image,
     # fill into pinned host memory, destroy
+    del D
+    torch.cuda.empty_cache()
     host_D = torch.empty((N, N), dtype=torch.int32, pin_memory=True)
-    host_img = np.ascontiguousarray(w.img)
+    host_img = np.ascontiguousarray(w.img if w.kind != "mask" else w.mask)
+    hw = type(w)(w.name, np.ascontiguousarray(w.img), w.conn, w.kind,
+                 None if w.mask is None else np.ascontiguousarray(w.mask), w.B)
     e2e_steps = max(1, min(a.steps, 3))
-    with gp.Image(host_img, conn=w.conn, B=w.B, stream=stream) as im2:
+    with _image(gp, hw, stream) as im2:
         im2.all_pairs("minfill", out=host_D.numpy())
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        with gp.Image(host_img, conn=w.conn, B=w.B, stream=stream) as im2:
+        with _image(gp, hw, stream) as im2:
             im2.all_pairs("minfill", out=host_D.numpy())
     barrier()
     e2e_s = allmax(time.perf_counter() - t0)
     e2e = {"value": entries * e2e_steps * world / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(host_img.nbytes), "d2h_bytes_per_step": int(4 * N * N),
            "note": "gapsp_create(host image) + gapsp_all_pairs(pinned host D) + gapsp_destroy"}
+    del host_D
 
     cpu = None
     if rank == 0 and world == 1:
-        cpu = _cpu_baseline(w.img, w.conn, N)
+        cpu = _cpu_baseline(w)
 
     im.close()
     if rank == 0:
@@ -490,8 +561,9 @@ def run_ours(a):
             "warmup": max(3, a.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": w.name, "H": w.H, "W": w.W, "N": N, "conn": w.conn, "B": w.B,
-                       "order": "minfill", "parallelism": f"replicas{world}",
-                       "l2": "256 MiB buffer written between steps; D (1.07 GB) exceeds L2"},
+                       "kind": w.kind, "order": "minfill", "parallelism": f"replicas{world}",
+                       "l2": f"256 MiB buffer written between steps; D ({4 * N * N / 1e9:.2f} GB) "
+                             "exceeds L2"},
             "propagations_per_s": props * a.steps * world / (total_ms / 1e3),
             "counts": {k: st[k] for k in ("propagations", "prepass_propagations", "distance_ops",
                                            "new_pairs", "rounds", "lookahead_propagations",

@@ -68,7 +68,7 @@ typedef enum {
     GAPSP_E_CUDA = 4,           /* a CUDA runtime call failed */
     GAPSP_E_NOT_CONVERGED = 5,  /* a propagation hit its sweep limit */
     GAPSP_E_TIMEOUT = 6,        /* a round loop hit its round limit */
-    GAPSP_E_CANCELLED = 7       /* reserved for cancellable calls */
+    GAPSP_E_CANCELLED = 7       /* gapsp_cancel stopped the call */
 } gapsp_status;
 
 typedef enum {
@@ -110,6 +110,16 @@ typedef struct {
                           (d(s,x) <= d(q,s) + d(q,x)) instead of from the source
                           alone; exact once every neighbour is filled. D and every
                           count are the same either way. */
+    int max_sweep_rounds; /* iteration limit of one propagation: rounds in which every
+                          line is swept once in each of the four directions; 0 = N + 2,
+                          which no propagation needs to reach (a shortest path has at
+                          most N - 1 turns). Reaching it ends the propagation and the
+                          call returns GAPSP_E_NOT_CONVERGED. */
+    int max_rounds;    /* gapsp_all_pairs: limit on the rounds of the loop; 0 = N + 66,
+                          above what any order needs (every round fills at least its
+                          first source's row). Reaching it ends the call with
+                          GAPSP_E_TIMEOUT. Both limits are checked between chunks of
+                          8 rounds. */
 } gapsp_opts;
 
 typedef struct {
@@ -195,8 +205,19 @@ gapsp_status gapsp_all_pairs_batch(gapsp_handle *const *h, int n, gapsp_order or
  */
 gapsp_status gapsp_rows(gapsp_handle *h, const int32_t *sources, int K, uint32_t *out);
 
-/* Releases the handle and its device memory. NULL is accepted. */
+/* Releases the handle and its device memory. NULL is accepted. Waits for
+ * the handle's work in flight first. */
 void gapsp_destroy(gapsp_handle *h);
+
+/*
+ * Asks the gapsp_all_pairs or gapsp_all_pairs_batch call running on h in
+ * another host thread to stop. The request is seen between chunks of 8
+ * rounds: the call then waits for the work it has queued and returns
+ * GAPSP_E_CANCELLED, and D is unspecified. Each all-pairs call clears the
+ * request when it starts, so a cancel with no call running has no effect.
+ * Safe to call from any thread while the handle is alive.
+ */
+gapsp_status gapsp_cancel(gapsp_handle *h);
 
 /* Static text for a status code. */
 const char *gapsp_strerror(gapsp_status s);
@@ -243,11 +264,11 @@ gapsp_status gapsp_profile_trace(gapsp_handle *h, double *ms, uint64_t *launches
  *   out     : caller-owned DEVICE uint32 K*N, 16-byte aligned; out[k*N + q] =
  *             d(sources[k], q).
  *   stream  : cudaStream_t the work runs on (NULL = default stream); the call
- *             returns when the rows are complete.
+ *             waits for it and returns when the rows are complete.
  * Limits: 0 <= K <= GAPSP_NOALLOC_MAX_SOURCES; H, W and N as gapsp_create.
- * Errors: GAPSP_E_INVALID for sizes beyond the limits, a NULL pointer, a
- * misaligned out or a source outside [0, N) (nothing is written then); GAPSP_E_NOT_CONVERGED;
- * GAPSP_E_CUDA.
+ * Errors: GAPSP_E_INVALID for sizes beyond the limits, a NULL pointer, an
+ * img or out that is not device memory, a misaligned out or a source outside
+ * [0, N) (nothing is written then); GAPSP_E_NOT_CONVERGED; GAPSP_E_CUDA.
  * Every call shares the one array and it keeps the last call's contents:
  * calls that overlap on the GPU race, so order them on one stream. The first
  * call on a device looks up the array's address on that device; make it
@@ -256,6 +277,18 @@ gapsp_status gapsp_profile_trace(gapsp_handle *h, double *ms, uint64_t *launches
 #define GAPSP_NOALLOC_MAX_SOURCES 4096
 gapsp_status gapsp_rows_noalloc(const uint8_t *img, int H, int W, int conn, gapsp_kind kind,
                                 const int32_t *sources, int K, uint32_t *out, void *stream);
+
+/*
+ * Host-side fault injection, for tests of the error paths: after n more
+ * successful device or pinned-host allocations made by the library, the
+ * next one fails as if the device were out of memory (the call returns
+ * GAPSP_E_NOMEM and frees what it had allocated). n < 0 turns it off (the
+ * default). Process-wide; nothing on the GPU is made to fail. Returns the
+ * number of device and pinned-host allocations the library holds (all
+ * handles together), so that a test can see that a failed call leaked
+ * nothing.
+ */
+long long gapsp_debug_fail_alloc(int n);
 
 #ifdef __cplusplus
 }

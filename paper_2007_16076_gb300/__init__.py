@@ -39,7 +39,8 @@ class Opts(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("mem_budget", ctypes.c_size_t),
                 ("sweep_phases", ctypes.c_int), ("fill_rows", ctypes.c_int), ("checked", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("prop_blocks", ctypes.c_int),
-                ("lookahead", ctypes.c_int), ("warm_start", ctypes.c_int)]
+                ("lookahead", ctypes.c_int), ("warm_start", ctypes.c_int),
+                ("max_sweep_rounds", ctypes.c_int), ("max_rounds", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -93,6 +94,10 @@ def load(build_if_missing: bool = True):
     lib.gapsp_rows_noalloc.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        P, ctypes.c_int, P, P]
     lib.gapsp_rows_noalloc.restype = ctypes.c_int
+    lib.gapsp_cancel.argtypes = [P]
+    lib.gapsp_cancel.restype = ctypes.c_int
+    lib.gapsp_debug_fail_alloc.argtypes = [ctypes.c_int]
+    lib.gapsp_debug_fail_alloc.restype = ctypes.c_longlong
     _lib = lib
     return lib
 
@@ -152,18 +157,44 @@ def all_pairs_batch(images, order: str = "minfill", outs=None):
 NOALLOC_MAX_SOURCES = 4096
 
 
+def debug_fail_alloc(n: int) -> int:
+    """Host-side fault injection (gapsp_debug_fail_alloc): the library's
+    allocation after n more successful ones fails; n < 0 turns it off.
+    Returns the number of allocations the library holds."""
+    return int(load().gapsp_debug_fail_alloc(int(n)))
+
+
 def rows_noalloc(img, sources, out, conn: int = 8, kind: str = "grey", stream=None):
     """gapsp_rows_noalloc: rows d(sources[k], .) into `out` with no allocation.
 
-    `img` (uint8, H x W; free flags for the mask kind) and `out` (K x N) must
-    be CUDA tensors the caller owns; `sources` is host or device int32. For
-    callers that cannot allocate device memory at call time; calls share one
-    fixed scratch array, so order them on one stream.
+    `img` (uint8, H x W; free flags for the mask kind) and `out` (K x N,
+    int32 or uint32) must be contiguous CUDA tensors the caller owns;
+    `sources` is a host array (converted to int32) or a CUDA int32 tensor.
+    For callers that cannot allocate device memory at call time; calls share
+    one fixed scratch array, so order them on one stream.
     """
     lib = load()
+    if not (hasattr(img, "is_cuda") and img.is_cuda and img.dim() == 2 and
+            str(img.dtype) == "torch.uint8" and img.is_contiguous()):
+        raise ValueError("img must be a contiguous 2-D CUDA uint8 tensor")
     H, W = int(img.shape[0]), int(img.shape[1])
-    K = int(sources.numel()) if hasattr(sources, "numel") else int(np.asarray(sources).size)
-    rc = lib.gapsp_rows_noalloc(_ptr(img), H, W, conn, KINDS[kind], _ptr(sources), K, _ptr(out),
+    if hasattr(sources, "data_ptr"):
+        if not sources.is_cuda or str(sources.dtype) != "torch.int32" or not sources.is_contiguous():
+            raise ValueError("a tensor of sources must be a contiguous CUDA int32 tensor")
+        src = sources
+        K = int(src.numel())
+    else:
+        src = np.ascontiguousarray(np.asarray(sources).reshape(-1))
+        if src.size and (src.min() < np.iinfo(np.int32).min or src.max() > np.iinfo(np.int32).max):
+            raise ValueError("source index out of the int32 range")
+        src = src.astype(np.int32)
+        K = int(src.size)
+    if not (hasattr(out, "is_cuda") and out.is_cuda and str(out.dtype) in ("torch.int32", "torch.uint32")
+            and out.is_contiguous()):
+        raise ValueError("out must be a contiguous CUDA int32 (or uint32) tensor")
+    if int(out.numel()) < K * H * W:
+        raise ValueError(f"out holds {int(out.numel())} entries, {K * H * W} needed")
+    rc = lib.gapsp_rows_noalloc(_ptr(img), H, W, conn, KINDS[kind], _ptr(src), K, _ptr(out),
                                 _torch_stream(stream))
     if rc != 0:
         raise GapspError(rc, "gapsp_rows_noalloc")
@@ -176,7 +207,7 @@ class Image:
     def __init__(self, img, conn: int = 8, kind: str = "grey", mask=None, B: int = 32,
                  seed: int = 0, mem_budget: int = 0, stream=None, sweep_phases: int = 0,
                  fill_rows: int = 0, prop_blocks: int = 0, lookahead: int = 0,
-                 warm_start: int = 0):
+                 warm_start: int = 0, max_sweep_rounds: int = 0, max_rounds: int = 0):
         lib = load()
         self._lib = lib
         self._h = ctypes.c_void_p()
@@ -201,6 +232,8 @@ class Image:
         o.prop_blocks = prop_blocks
         o.lookahead = lookahead
         o.warm_start = warm_start
+        o.max_sweep_rounds = max_sweep_rounds
+        o.max_rounds = max_rounds
         o.stream = _torch_stream(stream)
         self.H, self.W, self.N, self.conn, self.kind, self.B = H, W, H * W, conn, kind, B
         rc = lib.gapsp_create(_ptr(img_a), H, W, _ptr(mask_a), ctypes.byref(o), ctypes.byref(self._h))
@@ -224,6 +257,13 @@ class Image:
 
     def __exit__(self, *exc):
         self.close()
+
+    def cancel(self):
+        """Asks the all-pairs call running on this handle in another thread to
+        stop (gapsp_cancel); that call then raises with status 7."""
+        rc = self._lib.gapsp_cancel(self._h)
+        if rc != 0:
+            raise GapspError(rc, "gapsp_cancel")
 
     @property
     def kernel_launches(self) -> int:
@@ -290,6 +330,8 @@ class Image:
     def rows(self, sources, out=None):
         """out[k] = d(sources[k], .) (gapsp_rows)."""
         if hasattr(sources, "data_ptr"):
+            if str(sources.dtype) != "torch.int32":
+                raise ValueError("a tensor of sources must hold int32")
             src = sources
             K = int(src.numel())
         else:

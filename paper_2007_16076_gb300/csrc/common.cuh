@@ -49,22 +49,6 @@ __device__ __forceinline__ int ld_cg(const int* p) {
     return v;
 }
 
-// Shared-memory load with acquire semantics at block scope: later loads of
-// this thread are not performed before it.
-__device__ __forceinline__ int ld_acquire_smem(const int* p) {
-    int v;
-    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ld.acquire.cta.shared.b32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
-    return v;
-}
-
-// Shared-memory add with release semantics at block scope: earlier writes of
-// this thread are visible before it.
-__device__ __forceinline__ void red_release_smem(int* p, int v) {
-    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("red.release.cta.shared.add.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
-}
-
 __device__ __forceinline__ unsigned long long ld_cg64(const unsigned long long* p) {
     unsigned long long v;
     asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(v) : "l"(p));

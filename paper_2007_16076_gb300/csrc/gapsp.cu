@@ -9,6 +9,7 @@
 // so rounds are enqueued in chunks and the host only checks the device
 // "done" flag between chunks.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -32,6 +33,9 @@ struct gapsp_handle {
     int prop_blocks = 0;
     int lookahead = 0;  // option: 0 auto, -1 off, else candidates per round
     bool warm = true;   // option: propagations start from complete neighbour rows
+    int max_sweep_rounds = 0;  // option: 0 = N + 2
+    int max_rounds = 0;        // option: 0 = N + 66
+    std::atomic<int> cancel{0};  // gapsp_cancel: stop the all-pairs call in progress
     int sms = 0;        // multiprocessors of the device
     uint64_t launches = 0;
     // image
@@ -82,7 +86,8 @@ struct gapsp_handle {
     uint32_t* gmap = nullptr;
     unsigned long long* best = nullptr;
     uint8_t* cen = nullptr;
-    int* h_done = nullptr;  // pinned, [2]: "done" flag after an even / odd chunk of rounds
+    int* h_done = nullptr;  // pinned, [4]: "done" flag, then the status word, after an even /
+                            // odd chunk of rounds
     // scratch for host-side arrays
     uint32_t* Dtmp = nullptr;
     size_t Dtmp_bytes = 0;
@@ -98,9 +103,7 @@ struct gapsp_handle {
     std::vector<cudaEvent_t> pool;
 };
 
-namespace {
-
-bool is_device_ptr(const void* p) {
+bool gapsp::is_device_ptr(const void* p) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
@@ -109,14 +112,57 @@ bool is_device_ptr(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+namespace {
+
+// Host-side fault injection (gapsp_debug_fail_alloc): allocations left
+// before one fails; negative = never.
+std::atomic<int> g_fail_after{-1};
+// Device and pinned host allocations the library holds (gapsp_debug_fail_alloc).
+std::atomic<long long> g_live{0};
+
+bool injected_failure() {
+    int n = g_fail_after.load();
+    while (n >= 0) {
+        if (g_fail_after.compare_exchange_weak(n, n - 1)) return n == 0;
+    }
+    return false;
+}
+
 template <class T>
 cudaError_t dalloc(T** p, size_t count) {
-    return cudaMalloc((void**)p, count * sizeof(T) > 0 ? count * sizeof(T) : 1);
+    if (injected_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    const cudaError_t e = cudaMalloc((void**)p, count * sizeof(T) > 0 ? count * sizeof(T) : 1);
+    if (e == cudaSuccess) g_live.fetch_add(1);
+    return e;
+}
+
+cudaError_t halloc(int** p, size_t count) {
+    if (injected_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    const cudaError_t e = cudaMallocHost((void**)p, count * sizeof(int));
+    if (e == cudaSuccess) g_live.fetch_add(1);
+    return e;
 }
 
 template <class T>
 void dfree(T*& p) {
-    if (p) cudaFree(p);
+    if (p) {
+        cudaFree(p);
+        g_live.fetch_sub(1);
+    }
+    p = nullptr;
+}
+
+void hfree(int*& p) {
+    if (p) {
+        cudaFreeHost(p);
+        g_live.fetch_sub(1);
+    }
     p = nullptr;
 }
 
@@ -203,7 +249,7 @@ PropArgs base_prop(const gapsp_handle* h) {
     a.kind_mask = h->kind == GAPSP_MASK;
     a.f = h->f;
     a.status = h->status;
-    a.max_sweeps = 4 * (h->N + 2);
+    a.max_sweeps = 4 * (h->max_sweep_rounds ? h->max_sweep_rounds : h->N + 2);
     a.phases = h->sweep_phases ? h->sweep_phases : 4;
     // one block per source unless its map does not fit in one block's shared
     // memory (then the launch splits it into row strips over a cluster);
@@ -222,8 +268,24 @@ size_t fill_state_bytes(const gapsp_handle* h) {
            (N <= 16384 ? 8 * B * N : 0);  // trees handed to k_depths
 }
 
+void free_fill_state(gapsp_handle* h);
+
+gapsp_status alloc_fill_state(gapsp_handle* h);
+
+// The fill state is allocated on the first all-pairs call and kept; a
+// failed allocation frees whatever part of it was made.
 gapsp_status ensure_fill_state(gapsp_handle* h) {
     if (h->fill_ready) return GAPSP_OK;
+    const gapsp_status gs = alloc_fill_state(h);
+    if (gs != GAPSP_OK) {
+        free_fill_state(h);
+        return gs;
+    }
+    h->fill_ready = true;
+    return GAPSP_OK;
+}
+
+gapsp_status alloc_fill_state(gapsp_handle* h) {
     const size_t N = h->N, B = h->B;
     CK(dalloc(&h->cnt, N));
     CK(dalloc(&h->cnt_base, N));
@@ -264,14 +326,11 @@ gapsp_status ensure_fill_state(gapsp_handle* h) {
     CK(dalloc(&h->gmap, N));
     CK(dalloc(&h->best, N));
     CK(dalloc(&h->cen, N));
-    CK(cudaMallocHost((void**)&h->h_done, 2 * sizeof(int)));
-    h->fill_ready = true;
+    CK(halloc(&h->h_done, 4));
     return GAPSP_OK;
 }
 
-void free_all(gapsp_handle* h) {
-    dfree(h->f); dfree(h->pgeo); dfree(h->tbase); dfree(h->bound); dfree(h->comp);
-    dfree(h->comp_size); dfree(h->status); dfree(h->changed);
+void free_fill_state(gapsp_handle* h) {
     dfree(h->cnt); dfree(h->cnt_base); dfree(h->dirty); dfree(h->marks); dfree(h->parent); dfree(h->seg); dfree(h->jmp); dfree(h->acc);
     dfree(h->sel); dfree(h->nsel); dfree(h->cursor); dfree(h->done); dfree(h->seq); dfree(h->rank); dfree(h->grank);
     dfree(h->row_done); dfree(h->row_claim); dfree(h->cand); dfree(h->ncand);
@@ -280,9 +339,15 @@ void free_all(gapsp_handle* h) {
     dfree(h->dep_exit); dfree(h->dep_size); dfree(h->dep_count);
     dfree(h->stats); dfree(h->round_new); dfree(h->last_new); dfree(h->vfloor); dfree(h->sel_log);
     dfree(h->emap); dfree(h->gmap); dfree(h->best); dfree(h->cen);
+    hfree(h->h_done);
+    h->fill_ready = false;
+}
+
+void free_all(gapsp_handle* h) {
+    dfree(h->f); dfree(h->pgeo); dfree(h->tbase); dfree(h->bound); dfree(h->comp);
+    dfree(h->comp_size); dfree(h->status); dfree(h->changed);
+    free_fill_state(h);
     dfree(h->Dtmp); dfree(h->src_dev); dfree(h->out_tmp);
-    if (h->h_done) cudaFreeHost(h->h_done);
-    h->h_done = nullptr;
     for (auto& t : h->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
     h->timed.clear();
     for (auto e : h->pool) cudaEventDestroy(e);
@@ -322,13 +387,6 @@ struct ProfScope {
     }
     cudaStream_t stream = nullptr;
 };
-
-gapsp_status status_from_word(int w) {
-    if (w & ST_NOT_CONVERGED) return GAPSP_E_NOT_CONVERGED;
-    if (w & ST_TIMEOUT) return GAPSP_E_TIMEOUT;
-    if (w & ST_BAD_SOURCE) return GAPSP_E_INVALID;
-    return GAPSP_OK;
-}
 
 }  // namespace
 
@@ -377,6 +435,7 @@ gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask,
         return GAPSP_E_INVALID;
     if (o.lookahead < -1 || o.lookahead > 1024) return GAPSP_E_INVALID;
     if (o.warm_start != 0 && o.warm_start != -1) return GAPSP_E_INVALID;
+    if (o.max_sweep_rounds < 0 || o.max_rounds < 0) return GAPSP_E_INVALID;
     if (o.kind != GAPSP_MASK && !img) return GAPSP_E_INVALID;
     if (o.kind == GAPSP_MASK && !mask) return GAPSP_E_INVALID;
 
@@ -389,6 +448,8 @@ gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask,
     h->prop_blocks = o.prop_blocks;
     h->lookahead = o.lookahead;
     h->warm = o.warm_start == 0;
+    h->max_sweep_rounds = o.max_sweep_rounds;
+    h->max_rounds = o.max_rounds;
     {
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -472,6 +533,7 @@ gapsp_status gapsp_rows(gapsp_handle* h, const int32_t* sources, int K, uint32_t
     if (h->budget && (out_dev ? 0 : out_bytes) + (size_t)K * 4 > h->budget) return GAPSP_E_BUDGET;
     if (K > h->src_cap) {
         dfree(h->src_dev);
+        h->src_cap = 0;
         CK(dalloc(&h->src_dev, K));
         h->src_cap = K;
     }
@@ -845,20 +907,38 @@ gapsp_status fill_enqueue(FillRun& r, int chunk) {
     r.rounds += chunk;
     const int par = r.chunks & 1;
     CK(cudaMemcpyAsync(h->h_done + par, h->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->h_done + 2 + par, h->status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaEventRecord(r.chunk_ev[par], s));
     ++r.chunks;
     return GAPSP_OK;
 }
 
-// Waits for the oldest chunk not yet waited for and reads its "done" flag.
-// Rounds enqueued after the fill is done return at once.
+// Waits for the oldest chunk not yet waited for and reads its "done" flag
+// and the status word. Rounds enqueued after the fill is done return at
+// once. A device error (a propagation that hit its sweep limit), the round
+// limit and a cancel request end the fill here.
 gapsp_status fill_poll(FillRun& r) {
+    gapsp_handle* h = r.h;
     const int par = r.polled & 1;
     CK(cudaEventSynchronize(r.chunk_ev[par]));
     ++r.polled;
-    r.finished = r.h->h_done[par] != 0;
-    if (!r.finished && r.rounds > r.h->N + 2 + 64) return GAPSP_E_TIMEOUT;
+    r.finished = h->h_done[par] != 0;
+    const gapsp_status dev = status_from_word(h->h_done[2 + par]);
+    if (dev != GAPSP_OK) return dev;
+    if (h->cancel.load()) return GAPSP_E_CANCELLED;
+    const int cap = h->max_rounds ? h->max_rounds : h->N + 2 + 64;
+    if (!r.finished && r.rounds - kChunk >= cap) return GAPSP_E_TIMEOUT;
     return GAPSP_OK;
+}
+
+// After an error: waits for everything the fill queued on its streams, so
+// that no round still writes the caller's array once the call returns.
+void fill_drain(FillRun& r) {
+    if (r.s) cudaStreamSynchronize(r.s);
+    for (cudaStream_t x : r.side)
+        if (x) cudaStreamSynchronize(x);
+    if (r.stat) cudaStreamSynchronize(r.stat);
+    cudaGetLastError();
 }
 
 gapsp_status fill_finish(FillRun& r, gapsp_stats* st) {
@@ -934,14 +1014,26 @@ gapsp_status gapsp_all_pairs(gapsp_handle* h, gapsp_order order, uint32_t* D, ga
     r.order = order;
     r.D = D;
     r.s = h->st;
+    h->cancel.store(0);
     gapsp_status gs = fill_begin(r);
-    if (gs != GAPSP_OK) return gs;
-    if ((gs = fill_enqueue(r, kChunk)) != GAPSP_OK) return gs;
-    while (!r.finished) {
-        if ((gs = fill_enqueue(r, kChunk)) != GAPSP_OK) return gs;
-        if ((gs = fill_poll(r)) != GAPSP_OK) return gs;
+    if (gs == GAPSP_OK) gs = fill_enqueue(r, kChunk);
+    while (gs == GAPSP_OK && !r.finished) {
+        if ((gs = fill_enqueue(r, kChunk)) == GAPSP_OK) gs = fill_poll(r);
     }
-    return fill_finish(r, st);
+    if (gs == GAPSP_OK) gs = fill_finish(r, st);
+    if (gs != GAPSP_OK) fill_drain(r);
+    return gs;
+}
+
+gapsp_status gapsp_cancel(gapsp_handle* h) {
+    if (!h) return GAPSP_E_INVALID;
+    h->cancel.store(1);
+    return GAPSP_OK;
+}
+
+long long gapsp_debug_fail_alloc(int n) {
+    g_fail_after.store(n < 0 ? -1 : n);
+    return g_live.load();
 }
 
 gapsp_status gapsp_all_pairs_batch(gapsp_handle* const* hs, int n, gapsp_order order, uint32_t* const* Ds,
@@ -954,6 +1046,7 @@ gapsp_status gapsp_all_pairs_batch(gapsp_handle* const* hs, int n, gapsp_order o
             if (hs[k] == hs[i]) return GAPSP_E_INVALID;  // one fill per handle
     }
     if (n == 0) return GAPSP_OK;
+    for (int i = 0; i < n; ++i) hs[i]->cancel.store(0);
     // one worker stream per image, ordered after the handle's own stream
     std::vector<cudaStream_t> ws(n, nullptr);
     std::vector<FillRun> runs(n);
@@ -986,6 +1079,8 @@ gapsp_status gapsp_all_pairs_batch(gapsp_handle* const* hs, int n, gapsp_order o
             }
     }
     for (int i = 0; i < n && result == GAPSP_OK; ++i) result = fill_finish(runs[i], st ? st + i : nullptr);
+    if (result != GAPSP_OK)
+        for (int i = 0; i < n; ++i) fill_drain(runs[i]);
     for (int i = 0; i < n; ++i) {
         if (!ws[i]) continue;
         cudaEvent_t e = nullptr;

@@ -1,11 +1,44 @@
 // Internal interfaces between the host runtime and the kernel translation
 // units of gapsp. Not part of the public C ABI.
 #pragma once
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "gapsp.h"
+#include "common.cuh"
+
 namespace gapsp {
+
+// Whether p is device (or managed) memory that kernels may address.
+bool is_device_ptr(const void* p);
+
+// Status of a call from the device status word (ST_* bits).
+inline gapsp_status status_from_word(int w) {
+    if (w & ST_NOT_CONVERGED) return GAPSP_E_NOT_CONVERGED;
+    if (w & ST_TIMEOUT) return GAPSP_E_TIMEOUT;
+    if (w & ST_BAD_SOURCE) return GAPSP_E_INVALID;
+    return GAPSP_OK;
+}
+
+// Runs set() once per device, the device current at the call: kernel
+// attributes such as the dynamic shared-memory limit belong to a device, so
+// a process that uses several GPUs sets them on each. `done` holds one bit
+// per device (devices beyond 63 set them on every call). Two threads may
+// both run set() the first time; the attribute calls are idempotent.
+template <class F>
+inline void once_per_device(std::atomic<unsigned long long>& done, F&& set) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = 64;
+    }
+    const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return;
+    set();
+    if (bit) done.fetch_or(bit, std::memory_order_release);
+}
 
 struct PropArgs {
     int* map_base;              // distance maps (int32 view of uint32 rows)

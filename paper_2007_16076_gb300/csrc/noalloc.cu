@@ -16,7 +16,8 @@
 //    threads with no ordering between them) race: order them on one stream;
 //  - the first call on a device looks up the array's device address on that
 //    device (the device current at the call); make that first call before
-//    any stream capture.
+//    any stream capture;
+//  - every call waits for its stream: it returns when the rows are complete.
 #include <cstring>
 #include <mutex>
 
@@ -70,6 +71,8 @@ extern "C" gapsp_status gapsp_rows_noalloc(const uint8_t* img, int H, int W, int
     if (K == 0) return GAPSP_OK;
     if (!img || !sources || !out) return GAPSP_E_INVALID;
     if (reinterpret_cast<uintptr_t>(out) & 15) return GAPSP_E_INVALID;  // 16-byte row stores
+    // the kernels address the image and the rows directly
+    if (!is_device_ptr(img) || !is_device_ptr(out)) return GAPSP_E_INVALID;
     const int N = H * W;
     cudaStream_t st = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lock(g_mu);
@@ -119,6 +122,5 @@ extern "C" gapsp_status gapsp_rows_noalloc(const uint8_t* img, int H, int W, int
         cudaGetLastError();
         return GAPSP_E_CUDA;
     }
-    if (sw & ST_NOT_CONVERGED) return GAPSP_E_NOT_CONVERGED;
-    return sw ? GAPSP_E_INVALID : GAPSP_OK;
+    return status_from_word(sw);
 }

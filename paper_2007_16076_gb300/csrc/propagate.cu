@@ -673,8 +673,8 @@ template <int CONN, int KIND, int VPL>
 cudaError_t launch_one(const PropArgs& a, int jobs, cudaStream_t st) {
     const int pitch = a.W | 1;  // odd pitch: row and column lines spread over the banks
     const int threads = 32 * 4 * (a.phases == 4 ? 4 : a.phases == 2 ? 2 : 1);
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<unsigned long long> attr{0};
+    once_per_device(attr, [] {
         cudaFuncSetAttribute(k_propagate_smem<CONN, KIND, VPL, false, false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
         cudaFuncSetAttribute(k_propagate_smem<CONN, KIND, VPL, false, true>,
@@ -683,8 +683,7 @@ cudaError_t launch_one(const PropArgs& a, int jobs, cudaStream_t st) {
                              cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
         cudaFuncSetAttribute(k_propagate_glob<CONN, KIND, VPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              SMEM_LIMIT);
-        attr = true;
-    }
+    });
     const int C = strips_per_job(a);
     if (C > 0) {
         const size_t smem = smem_for_strips(a, C);

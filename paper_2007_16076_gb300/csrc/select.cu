@@ -896,12 +896,11 @@ __global__ void k_components(CompArgs a) {
 cudaError_t launch_select(const SelectArgs& a, cudaStream_t st) {
     if (a.order == 2 || a.order == 3) {
         if (a.N <= 16384) {
-            static bool attr = false;
-            if (!attr) {
+            static std::atomic<unsigned long long> attr{0};
+            once_per_device(attr, [] {
                 cudaFuncSetAttribute(k_select_small<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 8);
                 cudaFuncSetAttribute(k_select_small<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 8);
-                attr = true;
-            }
+            });
             if (a.order == 2) k_select_small<2, true><<<1, SEL_THREADS, (size_t)a.N * 8, st>>>(a);
             else k_select_small<3, true><<<1, SEL_THREADS, (size_t)a.N * 8, st>>>(a);
         } else {
@@ -940,11 +939,10 @@ cudaError_t launch_centroids(const ExtremaArgs& a, cudaStream_t st) {
 
 cudaError_t launch_rank(const ExtremaArgs& a, cudaStream_t st) {
     if (a.N <= 16384) {
-        static bool attr = false;
-        if (!attr) {
+        static std::atomic<unsigned long long> attr{0};
+        once_per_device(attr, [] {
             cudaFuncSetAttribute(k_rank_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 8);
-            attr = true;
-        }
+        });
         int n2 = 1;
         while (n2 < a.N) n2 <<= 1;
         k_rank_sort<<<1, RANK_THREADS, (size_t)n2 * 8, st>>>(a);

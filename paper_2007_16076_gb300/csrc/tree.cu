@@ -737,27 +737,24 @@ cudaError_t launch_tree(const TreeArgs& a, int B, cudaStream_t st, bool pdl) {
         // 16 rows or more, else two
         if (a.H >= 64) {
             const TreeCLayout L(a.H, a.W, 4);
-            static bool attr4 = false;
-            if (!attr4) {
+            static std::atomic<unsigned long long> attr4{0};
+            once_per_device(attr4, [] {
                 cudaFuncSetAttribute(k_treeC<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-                attr4 = true;
-            }
+            });
             return launch_ex(k_treeC<4>, 4 * B, 1024, L.bytes(), st, pdl, 4, a);
         }
         const TreeCLayout L(a.H, a.W, 2);
-        static bool attr2 = false;
-        if (!attr2) {
+        static std::atomic<unsigned long long> attr2{0};
+        once_per_device(attr2, [] {
             cudaFuncSetAttribute(k_treeC<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            attr2 = true;
-        }
+        });
         return launch_ex(k_treeC<2>, 2 * B, 1024, L.bytes(), st, pdl, 2, a);
     }
     if (a.N <= 16384) {
-        static bool attr = false;
-        if (!attr) {
+        static std::atomic<unsigned long long> attr{0};
+        once_per_device(attr, [] {
             cudaFuncSetAttribute(k_tree<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 11);
-            attr = true;
-        }
+        });
         // five 16-bit arrays and the image
         return launch_ex(k_tree<true>, B, 1024, (size_t)a.N * 11, st, pdl, 1, a);
     }
@@ -765,11 +762,10 @@ cudaError_t launch_tree(const TreeArgs& a, int B, cudaStream_t st, bool pdl) {
         // N > 16384 (so H > 64): eight strips of whole tiles, when a cluster
         // of eight such blocks can be resident at all
         const TreeWLayout L(a.H, a.W, 8);
-        static bool attr8 = false;
-        if (!attr8) {
+        static std::atomic<unsigned long long> attr8{0};
+        once_per_device(attr8, [] {
             cudaFuncSetAttribute(k_treeW<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            attr8 = true;
-        }
+        });
         if (L.bytes() <= 200 * 1024) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(8);
@@ -792,11 +788,10 @@ cudaError_t launch_tree(const TreeArgs& a, int B, cudaStream_t st, bool pdl) {
 }
 
 cudaError_t launch_depths(const TreeArgs& a, int B, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<unsigned long long> attr{0};
+    once_per_device(attr, [] {
         cudaFuncSetAttribute(k_depths, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 8);
-        attr = true;
-    }
+    });
     k_depths<<<B, 1024, (size_t)a.N * 8, st>>>(a);
     return cudaGetLastError();
 }
@@ -805,11 +800,10 @@ cudaError_t launch_fill(const TreeArgs& a, int B, cudaStream_t st, bool pdl) {
     (void)B;
     // mark rows, then one "changed" byte per row word
     const size_t smem = fill_smem_bytes(a.rows_per_block, a.words);
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<unsigned long long> attr_set{0};
+    once_per_device(attr_set, [] {
         cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
+    });
     const int grid = (a.N + a.rows_per_block - 1) / a.rows_per_block;
     return launch_ex(k_fill, grid, 256, smem, st, pdl, 1, a);
 }

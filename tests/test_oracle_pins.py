@@ -420,10 +420,42 @@ def test_extrema_one_row():
                          ids=lambda c: c["name"])
 def test_hand_counts(case):
     img = np.array(case["image"], dtype=np.uint8)
-    r = oracle.fill(img, case["order"], B=case["B"], conn=case["conn"], want_D=True)
+    seed = case.get("seed", 0)
+    if "sequence" in case:
+        # the frame sequence the derivation starts from (pinned on its own by
+        # the frame-structure and uniformity tests of the spiral order)
+        assert oracle.spiral_sequence(*img.shape, seed).tolist() == case["sequence"]
+    if "draws_raw" in case:
+        # the draws the derivation reduces: SplitMix64 from the handle's seed
+        assert [str(x) for x in _splitmix64(seed, len(case["draws_raw"]))] == case["draws_raw"]
+    r = oracle.fill(img, case["order"], B=case["B"], seed=seed, conn=case["conn"], want_D=True)
     for k in ("propagations", "prepass_propagations", "distance_ops", "new_pairs", "rounds"):
         assert getattr(r, k) == case[k], k
     assert r.sources.tolist() == case["sources"]
+    if "round_new" in case:
+        assert r.round_new.tolist() == case["round_new"]
+    assert np.array_equal(r.D, oracle.apsp(img, conn=case["conn"]))
+
+
+def _splitmix64(seed, n):
+    """SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) from its published
+    definition: state += 0x9E3779B97F4A7C15, then two xor-shift-multiply
+    steps and a final xor-shift."""
+    m = (1 << 64) - 1
+    s, out = seed & m, []
+    for _ in range(n):
+        s = (s + 0x9E3779B97F4A7C15) & m
+        z = s
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & m
+        out.append(z ^ (z >> 31))
+    return out
+
+
+def test_splitmix64_published_vector():
+    """The first outputs of SplitMix64 from state 0, as published with the
+    generator, so that the draws listed in the hand counts are its outputs."""
+    assert _splitmix64(0, 3) == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
 
 
 @pytest.mark.parametrize("W", [2, 5, 31])

@@ -35,6 +35,9 @@ def _cases():
         ("grey-8", synth.blobs(64, 64, 6, 4.0, 55.0, seed=11), None, 8),
         ("grey-4", synth.blobs(37, 50, 4, 3.0, 55.0, seed=12), None, 4),
         ("mask-8", None, synth.disk_mask(40, 45, 0.4, 2, 5, seed=13), 8),
+        ("l1-8", synth.blobs(33, 41, 4, 3.0, 55.0, seed=14), None, 8),
+        # a map too large for one block's shared memory: row strips on a cluster
+        ("grey-8-256", synth.blobs(256, 256, 64, 16.0, 40.0, seed=15), None, 8),
     ]
 
 
@@ -42,12 +45,12 @@ def _cases():
 def test_noalloc_matches_rows_twice(env, case):
     gp, torch = env
     name, img, mask, conn = case
-    kind = "grey" if mask is None else "mask"
+    kind = "mask" if mask is not None else ("l1" if name.startswith("l1") else "grey")
     plane = img if mask is None else mask
     H, W = plane.shape
     N = H * W
     dev_img = torch.from_numpy(np.ascontiguousarray(plane)).cuda()
-    with gp.Image(img, conn=conn, kind=kind, mask=mask) as im:
+    with gp.Image(img if mask is None else None, conn=conn, kind=kind, mask=mask) as im:
         for call, seed in enumerate((1, 2)):
             rng = np.random.default_rng(seed)
             src = rng.integers(0, N, size=40 + 9 * call).astype(np.int32)
@@ -79,3 +82,50 @@ def test_noalloc_rejects_beyond_limits(env):
         gp.rows_noalloc(dev_img, np.array([3, 256], dtype=np.int32), out)
     assert e.value.code == 1
     assert bool((out == 5).all())
+
+
+@pytest.mark.parametrize("K", [1, 305, 4096])
+def test_noalloc_source_counts(env, K):
+    """One source, the count past which the kernel runs one warp per sweep
+    direction (more than two sources per multiprocessor), and the maximum;
+    on a side stream."""
+    gp, torch = env
+    img = synth.blobs(20, 24, 3, 3.0, 55.0, seed=16)
+    N = img.size
+    src = (np.arange(K, dtype=np.int64) * 7 + 3) % N
+    dev_img = torch.from_numpy(img).cuda()
+    s = torch.cuda.Stream()
+    with gp.Image(img, conn=8) as im:
+        ref = gp.as_uint32(im.rows(src.astype(np.int32)))
+    for call in range(2):
+        out = torch.full((K, N), 9, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        # int64 host sources are converted, not read as pairs of int32 words
+        gp.rows_noalloc(dev_img, src, out, conn=8, stream=s)
+        s.synchronize()
+        assert np.array_equal(gp.as_uint32(out), ref), f"call {call}"
+
+
+def test_noalloc_rejects_bad_buffers(env):
+    gp, torch = env
+    img = synth.blobs(16, 16, 2, 2.0, 55.0, seed=3)
+    dev_img = torch.from_numpy(img).cuda()
+    src = np.array([1, 2, 3], dtype=np.int32)
+    # an output too small for K rows
+    with pytest.raises(ValueError):
+        gp.rows_noalloc(dev_img, src, torch.empty((2, 256), dtype=torch.int32, device="cuda"))
+    # a host image or output, and device sources of the wrong type
+    with pytest.raises(ValueError):
+        gp.rows_noalloc(torch.from_numpy(img), src, torch.empty((3, 256), dtype=torch.int32, device="cuda"))
+    with pytest.raises(ValueError):
+        gp.rows_noalloc(dev_img, src, torch.empty((3, 256), dtype=torch.int32))
+    with pytest.raises(ValueError):
+        gp.rows_noalloc(dev_img, torch.from_numpy(src.astype(np.int64)).cuda(),
+                        torch.empty((3, 256), dtype=torch.int32, device="cuda"))
+    # the C entry point itself refuses an output that is not device memory
+    host_out = np.zeros((3, 256), dtype=np.uint32)
+    rc = gp.load().gapsp_rows_noalloc(ctypes.c_void_p(dev_img.data_ptr()), 16, 16, 8, 0,
+                                      ctypes.c_void_p(src.ctypes.data), 3,
+                                      ctypes.c_void_p(host_out.ctypes.data), None)
+    assert rc == 1
+    assert not host_out.any()
