@@ -44,7 +44,7 @@ def _args():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="steps256",
                     help="the timed image (default: 256x256 blobs with step edges)")
     ap.add_argument("--no-extras", action="store_true", help="skip the side measurements")
-    ap.add_argument("--serve-seconds", type=float, default=4.0,
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the simulated serving run among the side measurements")
     ap.add_argument("--timed-only", action="store_true",
                     help="warm-up and timed steps only (for profiler runs); prints no JSON")
@@ -154,14 +154,13 @@ def job_throughput(entries_per_rank: float, steps: int, world: int, slowest_ms: 
     return entries_per_rank * steps * world / (slowest_ms / 1e3)
 
 
-def _serve(gp, torch, stream, seconds: float, rate: float = 50.0, seed: int = 0) -> dict:
-    """Serving: Poisson arrivals at `rate` requests/s for `seconds`. 70 % are
-    rows requests (K ~ U{1..512} sources on a square image whose side is
-    log-uniform in [64, 256]), 30 % all-pairs requests (minimum filling rate,
-    side log-uniform in [16, 160]); 8-connected blob images. Requests are
-    served one at a time in arrival order, each through its own handle
-    (gapsp_create, the call, gapsp_destroy); the result stays on the device.
-    Latency runs from arrival to the result being complete."""
+def _serve_stream(seconds: float, rate: float = 50.0, seed: int = 0):
+    """The serving workload: Poisson arrivals at `rate` requests/s for
+    `seconds`. 70 % are rows requests (K ~ U{1..512} sources on a square
+    image whose side is log-uniform in [64, 256]), 30 % all-pairs requests
+    (minimum filling rate, side log-uniform in [16, 160]); 8-connected blob
+    images drawn from a pool of 24 per kind (drawing one per request would
+    take longer than serving it). Returns [(t, kind, image, sources)]."""
     import math
 
     import numpy as np
@@ -172,11 +171,10 @@ def _serve(gp, torch, stream, seconds: float, rate: float = 50.0, seed: int = 0)
     def side(lo, hi):
         return int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
 
-    # a pool of images per kind (generating one per request would dominate)
     pool_rows = [synth.scaled_blobs(s, s, 8, seed=100 + i).img for i, s in
-                 enumerate(side(64, 256) for _ in range(12))]
+                 enumerate(side(64, 256) for _ in range(24))]
     pool_all = [synth.scaled_blobs(s, s, 8, seed=200 + i).img for i, s in
-                enumerate(side(16, 160) for _ in range(12))]
+                enumerate(side(16, 160) for _ in range(24))]
     reqs, t = [], 0.0
     while True:
         t += rng.exponential(1.0 / rate)
@@ -189,6 +187,97 @@ def _serve(gp, torch, stream, seconds: float, rate: float = 50.0, seed: int = 0)
             reqs.append((t, "rows", img, src))
         else:
             reqs.append((t, "all_pairs", pool_all[int(rng.integers(len(pool_all)))], None))
+    return reqs
+
+
+def _pct(v, q):
+    import numpy as np
+    return round(float(np.percentile(v, q)), 3) if len(v) else None
+
+
+def _serve(gp, torch, stream, seconds: float, budget: int = 120 << 30, slots: int = 16) -> dict:
+    """Continuous batching through gapsp_server: a client thread submits the
+    Poisson stream at its arrival times; the server admits requests by
+    footprint against `budget` as slots free up and runs them side by side;
+    a second thread releases each result as it completes. Latency (arrival
+    to result complete) and the times come from the server's clock."""
+    import threading
+
+    reqs = _serve_stream(seconds)
+    srv = gp.Server(mem_budget=budget, slots=slots, B=32)
+    # warm-up: one request of each kind
+    srv.release(srv.wait(srv.submit_rows(reqs[0][2], [0, 1, 2]))["id"])
+    srv.release(srv.wait(srv.submit_all_pairs(_serve_stream(5.0, seed=1)[0][2]))["id"])
+    done, lock = {}, threading.Lock()
+    kinds = {}
+    rejected = [0]
+    finished = threading.Event()
+
+    def reaper():
+        while True:
+            got = srv.poll(256)
+            for r in got:
+                srv.release(r["id"])
+                with lock:
+                    done[r["id"]] = r
+            if not got:
+                if finished.is_set() and len(done) >= len(kinds):
+                    return
+                time.sleep(0.0005)
+
+    th = threading.Thread(target=reaper)
+    th.start()
+    t0 = time.perf_counter()
+    entries = 0.0
+    for t_arr, kind, img, src in reqs:
+        now = time.perf_counter() - t0
+        if now < t_arr:
+            time.sleep(t_arr - now)
+        try:
+            if kind == "rows":
+                rid = srv.submit_rows(img, src)
+                entries_r = float(len(src)) * img.size
+            else:
+                rid = srv.submit_all_pairs(img)
+                entries_r = float(img.size) ** 2
+        except gp.GapspError:
+            rejected[0] += 1
+            continue
+        with lock:
+            kinds[rid] = (kind, entries_r)
+    finished.set()
+    th.join()
+    st = srv.stats()
+    srv.close()
+    t_first = min(r["t_submit_ms"] for r in done.values())
+    t_last = max(r["t_done_ms"] for r in done.values())
+    span = (t_last - t_first) / 1e3
+    lat = {"rows": [], "all_pairs": []}
+    ok = 0
+    for rid, r in done.items():
+        if r["status"] == 0:
+            ok += 1
+            lat[kinds[rid][0]].append(r["latency_ms"])
+            entries += kinds[rid][1]
+    both = lat["rows"] + lat["all_pairs"]
+    return {"requests": len(reqs), "offered_per_s": len(reqs) / reqs[-1][0], "seconds": seconds,
+            "served_per_s": ok / span, "completed_ok": ok, "rejected": rejected[0] + st["rejected"],
+            "failed": st["failed"], "admitted": st["admitted"],
+            "entries_per_s": entries / span, "p50_ms": _pct(both, 50), "p99_ms": _pct(both, 99),
+            "max_ms": round(max(both), 3), "rows_p50_ms": _pct(lat["rows"], 50),
+            "rows_p99_ms": _pct(lat["rows"], 99), "all_pairs_p50_ms": _pct(lat["all_pairs"], 50),
+            "all_pairs_p99_ms": _pct(lat["all_pairs"], 99), "budget_bytes": budget,
+            "peak_bytes": st["peak_bytes"], "slots": slots,
+            "note": "gapsp_server: continuous batching, admission by footprint (result + working "
+                    "state) against the budget; results released by the client as they complete"}
+
+
+def _serve_serial(gp, torch, stream, seconds: float) -> dict:
+    """The same kind of stream served one request at a time in arrival order,
+    each through its own handle (gapsp_create, the call, gapsp_destroy): the
+    plain one-image-at-a-time path the server is measured against."""
+    import numpy as np
+    reqs = _serve_stream(seconds)
 
     def serve_one(kind, img, src):
         with gp.Image(img, conn=8, B=32, stream=stream) as im:
@@ -198,28 +287,24 @@ def _serve(gp, torch, stream, seconds: float, rate: float = 50.0, seed: int = 0)
                 im.all_pairs("minfill")
             torch.cuda.synchronize()
 
-    serve_one("rows", pool_rows[0], np.arange(4, dtype=np.int32))  # warm-up
-    serve_one("all_pairs", pool_all[0], None)
+    serve_one("rows", reqs[0][2], np.arange(4, dtype=np.int32))
     lat = {"rows": [], "all_pairs": []}
+    entries = 0.0
     t0 = time.perf_counter()
     for t_arr, kind, img, src in reqs:
         now = time.perf_counter() - t0
         if now < t_arr:
             time.sleep(t_arr - now)
         serve_one(kind, img, src)
-        lat[kind].append(time.perf_counter() - t0 - t_arr)
+        lat[kind].append(1e3 * (time.perf_counter() - t0 - t_arr))
+        entries += float(len(src)) * img.size if kind == "rows" else float(img.size) ** 2
     span = time.perf_counter() - t0
-    both = sorted(lat["rows"] + lat["all_pairs"])
-
-    def pct(v, q):
-        return round(1e3 * float(np.percentile(v, q)), 3) if v else None
-
-    return {"requests": len(reqs), "offered_per_s": rate, "seconds": seconds,
-            "served_per_s": len(reqs) / span,
-            "p50_ms": pct(both, 50), "p99_ms": pct(both, 99), "max_ms": round(1e3 * max(both), 3),
-            "rows_p50_ms": pct(lat["rows"], 50), "rows_p99_ms": pct(lat["rows"], 99),
-            "all_pairs_p50_ms": pct(lat["all_pairs"], 50), "all_pairs_p99_ms": pct(lat["all_pairs"], 99),
-            "note": "one handle per request (create, call, destroy), result left on the device"}
+    both = lat["rows"] + lat["all_pairs"]
+    return {"requests": len(reqs), "seconds": seconds, "served_per_s": len(reqs) / span,
+            "entries_per_s": entries / span, "p50_ms": _pct(both, 50), "p99_ms": _pct(both, 99),
+            "rows_p50_ms": _pct(lat["rows"], 50), "rows_p99_ms": _pct(lat["rows"], 99),
+            "all_pairs_p50_ms": _pct(lat["all_pairs"], 50), "all_pairs_p99_ms": _pct(lat["all_pairs"], 99),
+            "note": "one request at a time, one handle per request"}
 
 
 def _peaks():
@@ -433,6 +518,7 @@ def _extras(a, gp, torch, w, im, D, flush, stream) -> dict:
         imb.close()
     del outs
     ex["serve"] = _serve(gp, torch, stream, seconds=a.serve_seconds)
+    ex["serve_serial"] = _serve_serial(gp, torch, stream, seconds=min(a.serve_seconds, 10.0))
     return ex
 
 

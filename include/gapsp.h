@@ -279,6 +279,119 @@ gapsp_status gapsp_rows_noalloc(const uint8_t *img, int H, int W, int conn, gaps
                                 const int32_t *sources, int K, uint32_t *out, void *stream);
 
 /*
+ * Autotuner for the launch parameters of one image's fill. The paper has no
+ * counterpart: its method is the same for every choice, and D is too; only
+ * the time and the counts of B > 1 change. Measures, on the image given, a
+ * fill in `order` for every candidate of B in {16, 32, 64}, lookahead on
+ * (0) or off (-1) and the tree fill with global marks (fill_rows 0) or rows
+ * of marks staged in shared memory (8), and returns in *best the options
+ * of *base (NULL: the defaults) with the fastest candidate's B, lookahead
+ * and fill_rows; *best_ms (may be NULL) receives its device time.
+ *   img, mask : as gapsp_create (host or device).
+ *   cache_path: NULL, or a text file of earlier results keyed by (H, W,
+ *               conn, kind, order, multiprocessor count): a key found there
+ *               is not measured again; a new result is appended.
+ * Allocates a scratch N x N array while measuring. Errors: GAPSP_E_INVALID,
+ * GAPSP_E_NOMEM, GAPSP_E_CUDA (no candidate could run).
+ */
+gapsp_status gapsp_tune(const uint8_t *img, const uint8_t *mask, int H, int W, const gapsp_opts *base,
+                        gapsp_order order, const char *cache_path, gapsp_opts *best, double *best_ms);
+
+/*
+ * Serving: a request loop with continuous batching. The paper has no
+ * serving layer; this runs its operations (Sec. 1: rows d(s, .); Sec. 2-3:
+ * the all-pairs fill in any order) for many callers at once.
+ *
+ * gapsp_server_submit queues a request (its inputs are copied, so the
+ * caller's arrays may be freed at once) and returns its id. A scheduler
+ * thread inside the library admits queued requests in arrival order as soon
+ * as one of opts.slots slots (one CUDA stream each) is free and the
+ * request's footprint fits in what the memory budget leaves: the footprint
+ * is its result, N*N*4 bytes for an all-pairs fill or K*N*4 bytes for K
+ * rows, plus the working state it holds while it runs (the image state, and
+ * the marks, trees and counts of a fill). Admitted requests run side by side
+ * on the GPU: a fill advances chunk by chunk of rounds and requests that
+ * arrive while others run start as soon as a slot and memory free up. A
+ * request whose footprint exceeds the whole budget is rejected at once
+ * (GAPSP_E_BUDGET). Each result equals that of gapsp_all_pairs / gapsp_rows
+ * on the same image alone (D does not depend on the order; the counts are
+ * the order's).
+ *
+ * Results stay resident in device memory, counted against the budget, until
+ * gapsp_server_release. A request with out == NULL gets a result array the
+ * server allocates (gapsp_result.result) and frees at release; with a
+ * caller-owned device out, the caller keeps that array alive until the
+ * request is done. The server uses the CUDA device current at its creation.
+ * All calls may come from any host thread.
+ */
+typedef struct gapsp_server gapsp_server;
+
+typedef enum { GAPSP_REQ_ALL_PAIRS = 0, GAPSP_REQ_ROWS = 1 } gapsp_request_kind;
+
+typedef struct {
+    gapsp_request_kind kind;
+    const uint8_t *img;     /* H*W host array: grey levels (GAPSP_GREY, GAPSP_L1) */
+    const uint8_t *mask;    /* H*W host array: 1 = free (GAPSP_MASK), else NULL */
+    int H, W, conn;         /* as gapsp_create */
+    gapsp_kind img_kind;
+    gapsp_order order;      /* GAPSP_REQ_ALL_PAIRS */
+    const int32_t *sources; /* GAPSP_REQ_ROWS: K host pixel indices in [0, N) */
+    int K;                  /* GAPSP_REQ_ROWS: 1 .. GAPSP_MAX_N */
+    uint32_t *out;          /* NULL, or a caller-owned 16-byte aligned device array of
+                               N*N (all-pairs) or K*N (rows) uint32 */
+} gapsp_request;
+
+typedef struct {
+    size_t mem_budget;  /* device bytes the admitted requests may hold at once (0 = 120 GiB) */
+    int slots;          /* requests running at once, one stream each: 1..256 (0 = 16) */
+    int B;              /* sources per round of the fills (0 = 32) */
+    int lookahead;      /* as gapsp_opts.lookahead, for the fills */
+} gapsp_server_opts;
+
+typedef struct {
+    uint64_t id;
+    int done;                  /* 1 once the request has finished (status is final) */
+    gapsp_status status;
+    uint32_t *result;          /* device array holding the result (valid until release) */
+    size_t result_bytes;
+    size_t footprint;          /* bytes the request was admitted with */
+    double t_submit_ms, t_admit_ms, t_done_ms; /* server clock, from its creation */
+    uint64_t propagations;     /* the fill's propagations (rows: K) */
+    uint64_t rounds;
+} gapsp_result;
+
+typedef struct {
+    uint64_t submitted, rejected, admitted, completed, failed, queued;
+    size_t bytes_in_use, peak_bytes, budget;
+} gapsp_server_counts;
+
+void gapsp_server_default_opts(gapsp_server_opts *opts);
+/* Starts a server (and its scheduler thread) on the current device. */
+gapsp_status gapsp_server_create(const gapsp_server_opts *opts, gapsp_server **out);
+/* Queues a request. Errors: GAPSP_E_INVALID (sizes, kinds, pointers, a source
+ * outside [0, N)), GAPSP_E_BUDGET (footprint above the whole budget). */
+gapsp_status gapsp_server_submit(gapsp_server *s, const gapsp_request *req, uint64_t *id);
+/* Waits up to timeout_ms (< 0: no limit) for request id to finish; fills *out.
+ * GAPSP_E_TIMEOUT if it has not finished in time, GAPSP_E_INVALID for an id
+ * unknown or released. */
+gapsp_status gapsp_server_wait(gapsp_server *s, uint64_t id, int timeout_ms, gapsp_result *out);
+/* Up to cap requests finished since the last poll, each reported once;
+ * returns how many. */
+int gapsp_server_poll(gapsp_server *s, gapsp_result *out, int cap);
+/* Copies a finished request's result (result_bytes) into dst, host or
+ * device memory; returns when the copy is complete. */
+gapsp_status gapsp_server_read(gapsp_server *s, uint64_t id, void *dst, size_t bytes);
+/* Frees a finished request's result and its share of the budget. */
+gapsp_status gapsp_server_release(gapsp_server *s, uint64_t id);
+gapsp_status gapsp_server_stats(gapsp_server *s, gapsp_server_counts *c);
+/* Stops the server: requests running finish, requests still queued are
+ * cancelled (GAPSP_E_CANCELLED), and every result not yet released is freed.
+ * Results held by the client count against the budget: a client that waits
+ * for a request while holding the results whose memory it needs waits
+ * forever, so release results as they complete (gapsp_server_poll). */
+void gapsp_server_destroy(gapsp_server *s);
+
+/*
  * Host-side fault injection, for tests of the error paths: after n more
  * successful device or pinned-host allocations made by the library, the
  * next one fails as if the device were out of memory (the call returns

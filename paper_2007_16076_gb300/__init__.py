@@ -54,6 +54,34 @@ class Stats(ctypes.Structure):
                 ("lookahead_propagations", ctypes.c_uint64), ("lookahead_hits", ctypes.c_uint64)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("img", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+                ("H", ctypes.c_int), ("W", ctypes.c_int), ("conn", ctypes.c_int),
+                ("img_kind", ctypes.c_int), ("order", ctypes.c_int), ("sources", ctypes.c_void_p),
+                ("K", ctypes.c_int), ("out", ctypes.c_void_p)]
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("mem_budget", ctypes.c_size_t), ("slots", ctypes.c_int), ("B", ctypes.c_int),
+                ("lookahead", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("done", ctypes.c_int), ("status", ctypes.c_int),
+                ("result", ctypes.c_void_p), ("result_bytes", ctypes.c_size_t),
+                ("footprint", ctypes.c_size_t), ("t_submit_ms", ctypes.c_double),
+                ("t_admit_ms", ctypes.c_double), ("t_done_ms", ctypes.c_double),
+                ("propagations", ctypes.c_uint64), ("rounds", ctypes.c_uint64)]
+
+
+class ServerCounts(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("queued", ctypes.c_uint64),
+                ("bytes_in_use", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t),
+                ("budget", ctypes.c_size_t)]
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -94,6 +122,27 @@ def load(build_if_missing: bool = True):
     lib.gapsp_rows_noalloc.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        P, ctypes.c_int, P, P]
     lib.gapsp_rows_noalloc.restype = ctypes.c_int
+    lib.gapsp_server_default_opts.argtypes = [ctypes.POINTER(ServerOpts)]
+    lib.gapsp_server_default_opts.restype = None
+    lib.gapsp_server_create.argtypes = [ctypes.POINTER(ServerOpts), ctypes.POINTER(P)]
+    lib.gapsp_server_create.restype = ctypes.c_int
+    lib.gapsp_server_submit.argtypes = [P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+    lib.gapsp_server_submit.restype = ctypes.c_int
+    lib.gapsp_server_wait.argtypes = [P, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(Result)]
+    lib.gapsp_server_wait.restype = ctypes.c_int
+    lib.gapsp_server_poll.argtypes = [P, ctypes.POINTER(Result), ctypes.c_int]
+    lib.gapsp_server_poll.restype = ctypes.c_int
+    lib.gapsp_server_read.argtypes = [P, ctypes.c_uint64, P, ctypes.c_size_t]
+    lib.gapsp_server_read.restype = ctypes.c_int
+    lib.gapsp_server_release.argtypes = [P, ctypes.c_uint64]
+    lib.gapsp_server_release.restype = ctypes.c_int
+    lib.gapsp_server_stats.argtypes = [P, ctypes.POINTER(ServerCounts)]
+    lib.gapsp_server_stats.restype = ctypes.c_int
+    lib.gapsp_server_destroy.argtypes = [P]
+    lib.gapsp_server_destroy.restype = None
+    lib.gapsp_tune.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Opts), ctypes.c_int,
+                               ctypes.c_char_p, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_double)]
+    lib.gapsp_tune.restype = ctypes.c_int
     lib.gapsp_cancel.argtypes = [P]
     lib.gapsp_cancel.restype = ctypes.c_int
     lib.gapsp_debug_fail_alloc.argtypes = [ctypes.c_int]
@@ -155,6 +204,26 @@ def all_pairs_batch(images, order: str = "minfill", outs=None):
 
 
 NOALLOC_MAX_SOURCES = 4096
+
+
+def tune(img, conn: int = 8, kind: str = "grey", mask=None, order: str = "minfill", cache=None) -> dict:
+    """gapsp_tune: the fastest B, lookahead and fill variant for this image's
+    fill, measured on the GPU (or read from the text cache `cache`).
+    Returns the keyword arguments for :class:`Image` and the time (ms)."""
+    lib = load()
+    a = None if kind == "mask" else np.ascontiguousarray(img, dtype=np.uint8)
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    H, W = (m if kind == "mask" else a).shape
+    o = Opts()
+    lib.gapsp_default_opts(ctypes.byref(o))
+    o.conn, o.kind = conn, KINDS[kind]
+    best = Opts()
+    ms = ctypes.c_double()
+    rc = lib.gapsp_tune(_ptr(a), _ptr(m), H, W, ctypes.byref(o), ORDERS[order],
+                        None if cache is None else str(cache).encode(), ctypes.byref(best), ctypes.byref(ms))
+    if rc != 0:
+        raise GapspError(rc, "gapsp_tune")
+    return {"B": best.B, "lookahead": best.lookahead, "fill_rows": best.fill_rows, "ms": ms.value}
 
 
 def debug_fail_alloc(n: int) -> int:
@@ -344,3 +413,125 @@ class Image:
         if rc != 0:
             raise GapspError(rc, "gapsp_rows")
         return out
+
+
+def _result_dict(r: Result) -> dict:
+    return {"id": int(r.id), "done": bool(r.done), "status": int(r.status), "ptr": r.result or 0,
+            "result_bytes": int(r.result_bytes), "footprint": int(r.footprint),
+            "t_submit_ms": r.t_submit_ms, "t_admit_ms": r.t_admit_ms, "t_done_ms": r.t_done_ms,
+            "latency_ms": r.t_done_ms - r.t_submit_ms, "propagations": int(r.propagations),
+            "rounds": int(r.rounds)}
+
+
+class Server:
+    """A request loop with continuous batching (gapsp_server_*).
+
+    Requests are queued by :meth:`submit_all_pairs` / :meth:`submit_rows`
+    (inputs are copied) and run side by side on the GPU as slots and memory
+    free up; :meth:`wait` / :meth:`poll` report them and :meth:`release`
+    frees a result. ``out`` may be a caller-owned CUDA tensor (int32, N x N
+    or K x N) that receives the result; otherwise the server owns it.
+    """
+
+    def __init__(self, mem_budget: int = 0, slots: int = 0, B: int = 0, lookahead: int = 0):
+        lib = load()
+        self._lib = lib
+        o = ServerOpts()
+        lib.gapsp_server_default_opts(ctypes.byref(o))
+        if mem_budget:
+            o.mem_budget = mem_budget
+        if slots:
+            o.slots = slots
+        if B:
+            o.B = B
+        o.lookahead = lookahead
+        self._s = ctypes.c_void_p()
+        rc = lib.gapsp_server_create(ctypes.byref(o), ctypes.byref(self._s))
+        if rc != 0:
+            raise GapspError(rc, "gapsp_server_create")
+
+    def _submit(self, kind, img, conn, img_kind, mask, order, sources, out):
+        q = Request()
+        q.kind = kind
+        q.conn = conn
+        q.img_kind = KINDS[img_kind]
+        q.order = ORDERS[order]
+        keep = []
+        if img_kind == "mask":
+            m = np.ascontiguousarray(mask, dtype=np.uint8)
+            keep.append(m)
+            q.mask = m.ctypes.data
+            q.H, q.W = m.shape
+        else:
+            a = np.ascontiguousarray(img, dtype=np.uint8)
+            keep.append(a)
+            q.img = a.ctypes.data
+            q.H, q.W = a.shape
+        if sources is not None:
+            src = np.ascontiguousarray(np.asarray(sources).reshape(-1)).astype(np.int32)
+            keep.append(src)
+            q.sources = src.ctypes.data
+            q.K = int(src.size)
+        if out is not None:
+            q.out = _ptr(out).value
+        rid = ctypes.c_uint64()
+        rc = self._lib.gapsp_server_submit(self._s, ctypes.byref(q), ctypes.byref(rid))
+        if rc != 0:
+            raise GapspError(rc, "gapsp_server_submit")
+        return int(rid.value)
+
+    def submit_all_pairs(self, img, conn: int = 8, order: str = "minfill", kind: str = "grey",
+                         mask=None, out=None) -> int:
+        return self._submit(0, img, conn, kind, mask, order, None, out)
+
+    def submit_rows(self, img, sources, conn: int = 8, kind: str = "grey", mask=None, out=None) -> int:
+        return self._submit(1, img, conn, kind, mask, "minfill", sources, out)
+
+    def wait(self, rid: int, timeout_ms: int = -1) -> dict:
+        r = Result()
+        rc = self._lib.gapsp_server_wait(self._s, rid, timeout_ms, ctypes.byref(r))
+        if rc != 0:
+            raise GapspError(rc, "gapsp_server_wait")
+        return _result_dict(r)
+
+    def poll(self, cap: int = 256) -> list:
+        buf = (Result * cap)()
+        n = self._lib.gapsp_server_poll(self._s, buf, cap)
+        return [_result_dict(buf[i]) for i in range(n)]
+
+    def read(self, rid: int, dst):
+        """Copies a finished request's result into dst (numpy array or tensor)."""
+        nbytes = dst.nbytes if isinstance(dst, np.ndarray) else dst.numel() * dst.element_size()
+        rc = self._lib.gapsp_server_read(self._s, rid, _ptr(dst), nbytes)
+        if rc != 0:
+            raise GapspError(rc, "gapsp_server_read")
+        return dst
+
+    def release(self, rid: int):
+        rc = self._lib.gapsp_server_release(self._s, rid)
+        if rc != 0:
+            raise GapspError(rc, "gapsp_server_release")
+
+    def stats(self) -> dict:
+        c = ServerCounts()
+        rc = self._lib.gapsp_server_stats(self._s, ctypes.byref(c))
+        if rc != 0:
+            raise GapspError(rc, "gapsp_server_stats")
+        return {k: int(getattr(c, k)) for k, _ in ServerCounts._fields_}
+
+    def close(self):
+        if self._s:
+            self._lib.gapsp_server_destroy(self._s)
+            self._s = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -13,95 +13,17 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
 #include "gapsp.h"
 #include "common.cuh"
 #include "internal.h"
+#include "runtime.h"
 
 using namespace gapsp;
 
-struct gapsp_handle {
-    int H = 0, W = 0, N = 0, conn = 8, kind = 0, B = 32;
-    uint64_t seed = 0;
-    size_t budget = 0;
-    cudaStream_t st = nullptr;
-    int tiles_w = 0, tiles_h = 0, words = 0;
-    int sweep_phases = 0;
-    int fill_rows = 0;
-    int prop_blocks = 0;
-    int lookahead = 0;  // option: 0 auto, -1 off, else candidates per round
-    bool warm = true;   // option: propagations start from complete neighbour rows
-    int max_sweep_rounds = 0;  // option: 0 = N + 2
-    int max_rounds = 0;        // option: 0 = N + 66
-    std::atomic<int> cancel{0};  // gapsp_cancel: stop the all-pairs call in progress
-    int sms = 0;        // multiprocessors of the device
-    uint64_t launches = 0;
-    // image
-    uint8_t* f = nullptr;
-    uint32_t* pgeo = nullptr;
-    int32_t* tbase = nullptr;
-    uint8_t* bound = nullptr;
-    int32_t* comp = nullptr;
-    int32_t* comp_size = nullptr;
-    int* status = nullptr;
-    int* changed = nullptr;
-    // fill state
-    bool fill_ready = false;
-    uint32_t* cnt = nullptr;
-    uint32_t* cnt_base = nullptr;
-    uint8_t* dirty = nullptr;
-    unsigned long long* marks = nullptr;
-    int32_t* parent = nullptr;
-    ulonglong2* seg = nullptr;
-    int32_t* jmp = nullptr;
-    int32_t* acc = nullptr;
-    int32_t* sel = nullptr;
-    int* nsel = nullptr;
-    int* cursor = nullptr;
-    int* done = nullptr;
-    int32_t* seq = nullptr;
-    int32_t* rank = nullptr;
-    int32_t* grank = nullptr;
-    uint8_t* row_done = nullptr;  // [N]: row already written by a propagation
-    uint8_t* row_claim = nullptr; // [N]: row handed to a lookahead launch (done or in flight)
-    int32_t* rp_ring = nullptr;   // spiral with repulsion: turns, S, draw state
-    int32_t* rp_fstart = nullptr;
-    uint8_t* rp_fcyc = nullptr;
-    unsigned* rp_inS = nullptr;
-    RepState* rp_state = nullptr;
-    uint8_t* rp_taken = nullptr;
-    int32_t* cand = nullptr;      // [2][1024]: lookahead candidates, by round parity
-    int* ncand = nullptr;         // [2]
-    uint16_t* dep_exit = nullptr; // [2][B][N] (N <= 16384): trees handed to k_depths, by round parity
-    uint16_t* dep_size = nullptr; // [2][B][N]
-    int* dep_count = nullptr;     // [2]
-    unsigned long long* stats = nullptr;
-    unsigned long long* round_new = nullptr;
-    unsigned long long* last_new = nullptr;
-    uint32_t* vfloor = nullptr;   // selection: least leading key field at the previous round
-    int32_t* sel_log = nullptr;
-    uint32_t* emap = nullptr;
-    uint32_t* gmap = nullptr;
-    unsigned long long* best = nullptr;
-    uint8_t* cen = nullptr;
-    int* h_done = nullptr;  // pinned, [4]: "done" flag, then the status word, after an even /
-                            // odd chunk of rounds
-    // scratch for host-side arrays
-    uint32_t* Dtmp = nullptr;
-    size_t Dtmp_bytes = 0;
-    int32_t* src_dev = nullptr;
-    int src_cap = 0;
-    uint32_t* out_tmp = nullptr;
-    size_t out_tmp_bytes = 0;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    // per-kernel timing (gapsp_profile_*)
-    bool prof = false;
-    struct Timed { int kind; cudaEvent_t a, b; };
-    std::vector<Timed> timed;
-    std::vector<cudaEvent_t> pool;
-};
 
 bool gapsp::is_device_ptr(const void* p) {
     cudaPointerAttributes at;
@@ -112,7 +34,8 @@ bool gapsp::is_device_ptr(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-namespace {
+namespace gapsp {
+namespace rt {
 
 // Host-side fault injection (gapsp_debug_fail_alloc): allocations left
 // before one fails; negative = never.
@@ -128,42 +51,60 @@ bool injected_failure() {
     return false;
 }
 
-template <class T>
-cudaError_t dalloc(T** p, size_t count) {
-    if (injected_failure()) {
-        *p = nullptr;
-        return cudaErrorMemoryAllocation;
-    }
-    const cudaError_t e = cudaMalloc((void**)p, count * sizeof(T) > 0 ? count * sizeof(T) : 1);
-    if (e == cudaSuccess) g_live.fetch_add(1);
-    return e;
-}
+// Pinned host words for the asynchronous copies of a fill's "done" flags
+// and status words: one process-wide pinned array handed out kWords at a
+// time, allocated once and never freed (allocating and freeing pinned
+// memory synchronises the device).
+struct PinnedSlots {
+    static constexpr int kSlots = 4096, kWords = 4;
+    std::mutex mu;
+    int* base = nullptr;
+    std::vector<int> free_list;
+};
+PinnedSlots g_pinned;
 
-cudaError_t halloc(int** p, size_t count) {
-    if (injected_failure()) {
-        *p = nullptr;
-        return cudaErrorMemoryAllocation;
+cudaError_t halloc(int** p) {
+    *p = nullptr;
+    if (injected_failure()) return cudaErrorMemoryAllocation;
+    std::lock_guard<std::mutex> lock(g_pinned.mu);
+    if (!g_pinned.base) {
+        const cudaError_t e = cudaMallocHost((void**)&g_pinned.base,
+                                             sizeof(int) * PinnedSlots::kSlots * PinnedSlots::kWords);
+        if (e != cudaSuccess) {
+            g_pinned.base = nullptr;
+            return e;
+        }
+        for (int i = PinnedSlots::kSlots - 1; i >= 0; --i) g_pinned.free_list.push_back(i);
     }
-    const cudaError_t e = cudaMallocHost((void**)p, count * sizeof(int));
-    if (e == cudaSuccess) g_live.fetch_add(1);
-    return e;
-}
-
-template <class T>
-void dfree(T*& p) {
-    if (p) {
-        cudaFree(p);
-        g_live.fetch_sub(1);
-    }
-    p = nullptr;
+    if (g_pinned.free_list.empty()) return cudaErrorMemoryAllocation;
+    *p = g_pinned.base + (size_t)g_pinned.free_list.back() * PinnedSlots::kWords;
+    g_pinned.free_list.pop_back();
+    g_live.fetch_add(1);
+    return cudaSuccess;
 }
 
 void hfree(int*& p) {
     if (p) {
-        cudaFreeHost(p);
+        std::lock_guard<std::mutex> lock(g_pinned.mu);
+        g_pinned.free_list.push_back((int)((p - g_pinned.base) / PinnedSlots::kWords));
         g_live.fetch_sub(1);
     }
     p = nullptr;
+}
+
+// Freed blocks up to this size stay in the device's pool for the next
+// handle instead of going back to the driver at every synchronisation.
+void keep_pool_warm() {
+    static std::atomic<unsigned long long> done{0};
+    once_per_device(done, [] {
+        int dev = 0;
+        cudaMemPool_t pool;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = 1ull << 30;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+    });
 }
 
 #define CK(x)                                                  \
@@ -270,13 +211,14 @@ size_t fill_state_bytes(const gapsp_handle* h) {
 
 void free_fill_state(gapsp_handle* h);
 
-gapsp_status alloc_fill_state(gapsp_handle* h);
+gapsp_status alloc_fill_state(gapsp_handle* h, cudaStream_t st);
 
-// The fill state is allocated on the first all-pairs call and kept; a
-// failed allocation frees whatever part of it was made.
-gapsp_status ensure_fill_state(gapsp_handle* h) {
+// The fill state is allocated on the first all-pairs call (on the stream
+// the fill runs on) and kept; a failed allocation frees whatever part of it
+// was made.
+gapsp_status ensure_fill_state(gapsp_handle* h, cudaStream_t st) {
     if (h->fill_ready) return GAPSP_OK;
-    const gapsp_status gs = alloc_fill_state(h);
+    const gapsp_status gs = alloc_fill_state(h, st);
     if (gs != GAPSP_OK) {
         free_fill_state(h);
         return gs;
@@ -285,69 +227,70 @@ gapsp_status ensure_fill_state(gapsp_handle* h) {
     return GAPSP_OK;
 }
 
-gapsp_status alloc_fill_state(gapsp_handle* h) {
+gapsp_status alloc_fill_state(gapsp_handle* h, cudaStream_t st) {
     const size_t N = h->N, B = h->B;
-    CK(dalloc(&h->cnt, N));
-    CK(dalloc(&h->cnt_base, N));
-    CK(dalloc(&h->dirty, N));
-    CK(dalloc(&h->marks, N * h->words));
-    CK(dalloc(&h->parent, B * N));
-    CK(dalloc(&h->seg, B * N));
-    CK(dalloc(&h->jmp, 2 * B * N));
-    CK(dalloc(&h->acc, 2 * B * N));
-    CK(dalloc(&h->sel, B));
-    CK(dalloc(&h->nsel, 1));
-    CK(dalloc(&h->cursor, 1));
-    CK(dalloc(&h->done, 1));
-    CK(dalloc(&h->seq, N));
-    CK(dalloc(&h->rank, N));
-    CK(dalloc(&h->grank, N));
-    CK(dalloc(&h->row_done, N));
-    CK(dalloc(&h->row_claim, N));
-    CK(dalloc(&h->rp_ring, N));
-    CK(dalloc(&h->rp_fstart, N + 2));
-    CK(dalloc(&h->rp_fcyc, N + 1));
-    CK(dalloc(&h->rp_inS, 32));
-    CK(dalloc(&h->rp_state, 1));
-    CK(dalloc(&h->rp_taken, N));
-    CK(dalloc(&h->cand, 2 * 1024));
-    CK(dalloc(&h->ncand, 2));
+    CK(dalloc(&h->cnt, N, st));
+    CK(dalloc(&h->cnt_base, N, st));
+    CK(dalloc(&h->dirty, N, st));
+    CK(dalloc(&h->marks, N * h->words, st));
+    CK(dalloc(&h->parent, B * N, st));
+    CK(dalloc(&h->seg, B * N, st));
+    CK(dalloc(&h->jmp, 2 * B * N, st));
+    CK(dalloc(&h->acc, 2 * B * N, st));
+    CK(dalloc(&h->sel, B, st));
+    CK(dalloc(&h->nsel, 1, st));
+    CK(dalloc(&h->cursor, 1, st));
+    CK(dalloc(&h->done, 1, st));
+    CK(dalloc(&h->seq, N, st));
+    CK(dalloc(&h->rank, N, st));
+    CK(dalloc(&h->grank, N, st));
+    CK(dalloc(&h->row_done, N, st));
+    CK(dalloc(&h->row_claim, N, st));
+    CK(dalloc(&h->rp_ring, N, st));
+    CK(dalloc(&h->rp_fstart, N + 2, st));
+    CK(dalloc(&h->rp_fcyc, N + 1, st));
+    CK(dalloc(&h->rp_inS, 32, st));
+    CK(dalloc(&h->rp_state, 1, st));
+    CK(dalloc(&h->rp_taken, N, st));
+    CK(dalloc(&h->cand, 2 * 1024, st));
+    CK(dalloc(&h->ncand, 2, st));
     if (N <= 16384) {
-        CK(dalloc(&h->dep_exit, 2 * B * N));
-        CK(dalloc(&h->dep_size, 2 * B * N));
-        CK(dalloc(&h->dep_count, 2));
+        CK(dalloc(&h->dep_exit, 2 * B * N, st));
+        CK(dalloc(&h->dep_size, 2 * B * N, st));
+        CK(dalloc(&h->dep_count, 2, st));
     }
-    CK(dalloc(&h->stats, S_SLOTS));
-    CK(dalloc(&h->round_new, N + 1));
-    CK(dalloc(&h->last_new, 1));
-    CK(dalloc(&h->vfloor, 1));
-    CK(dalloc(&h->sel_log, N + 1));
-    CK(dalloc(&h->emap, N));
-    CK(dalloc(&h->gmap, N));
-    CK(dalloc(&h->best, N));
-    CK(dalloc(&h->cen, N));
-    CK(halloc(&h->h_done, 4));
+    CK(dalloc(&h->stats, S_SLOTS, st));
+    CK(dalloc(&h->round_new, N + 1, st));
+    CK(dalloc(&h->last_new, 1, st));
+    CK(dalloc(&h->vfloor, 1, st));
+    CK(dalloc(&h->sel_log, N + 1, st));
+    CK(dalloc(&h->emap, N, st));
+    CK(dalloc(&h->gmap, N, st));
+    CK(dalloc(&h->best, N, st));
+    CK(dalloc(&h->cen, N, st));
+    CK(halloc(&h->h_done));
     return GAPSP_OK;
 }
 
 void free_fill_state(gapsp_handle* h) {
-    dfree(h->cnt); dfree(h->cnt_base); dfree(h->dirty); dfree(h->marks); dfree(h->parent); dfree(h->seg); dfree(h->jmp); dfree(h->acc);
-    dfree(h->sel); dfree(h->nsel); dfree(h->cursor); dfree(h->done); dfree(h->seq); dfree(h->rank); dfree(h->grank);
-    dfree(h->row_done); dfree(h->row_claim); dfree(h->cand); dfree(h->ncand);
-    dfree(h->rp_ring); dfree(h->rp_fstart); dfree(h->rp_fcyc); dfree(h->rp_inS); dfree(h->rp_state);
-    dfree(h->rp_taken);
-    dfree(h->dep_exit); dfree(h->dep_size); dfree(h->dep_count);
-    dfree(h->stats); dfree(h->round_new); dfree(h->last_new); dfree(h->vfloor); dfree(h->sel_log);
-    dfree(h->emap); dfree(h->gmap); dfree(h->best); dfree(h->cen);
+    dfree(h->cnt, h->st); dfree(h->cnt_base, h->st); dfree(h->dirty, h->st); dfree(h->marks, h->st); dfree(h->parent, h->st); dfree(h->seg, h->st); dfree(h->jmp, h->st); dfree(h->acc, h->st);
+    dfree(h->sel, h->st); dfree(h->nsel, h->st); dfree(h->cursor, h->st); dfree(h->done, h->st); dfree(h->seq, h->st); dfree(h->rank, h->st); dfree(h->grank, h->st);
+    dfree(h->row_done, h->st); dfree(h->row_claim, h->st); dfree(h->cand, h->st); dfree(h->ncand, h->st);
+    dfree(h->rp_ring, h->st); dfree(h->rp_fstart, h->st); dfree(h->rp_fcyc, h->st); dfree(h->rp_inS, h->st); dfree(h->rp_state, h->st);
+    dfree(h->rp_taken, h->st);
+    dfree(h->dep_exit, h->st); dfree(h->dep_size, h->st); dfree(h->dep_count, h->st);
+    dfree(h->stats, h->st); dfree(h->round_new, h->st); dfree(h->last_new, h->st); dfree(h->vfloor, h->st); dfree(h->sel_log, h->st);
+    dfree(h->emap, h->st); dfree(h->gmap, h->st); dfree(h->best, h->st); dfree(h->cen, h->st);
     hfree(h->h_done);
     h->fill_ready = false;
 }
 
 void free_all(gapsp_handle* h) {
-    dfree(h->f); dfree(h->pgeo); dfree(h->tbase); dfree(h->bound); dfree(h->comp);
-    dfree(h->comp_size); dfree(h->status); dfree(h->changed);
+    cudaStream_t st = h->st;
+    dfree(h->f, st); dfree(h->pgeo, st); dfree(h->tbase, st); dfree(h->bound, st); dfree(h->comp, st);
+    dfree(h->comp_size, st); dfree(h->status, st); dfree(h->changed, st);
     free_fill_state(h);
-    dfree(h->Dtmp); dfree(h->src_dev); dfree(h->out_tmp);
+    dfree(h->Dtmp, st); dfree(h->src_dev, st); dfree(h->out_tmp, st);
     for (auto& t : h->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
     h->timed.clear();
     for (auto e : h->pool) cudaEventDestroy(e);
@@ -388,7 +331,10 @@ struct ProfScope {
     cudaStream_t stream = nullptr;
 };
 
-}  // namespace
+}  // namespace rt
+}  // namespace gapsp
+
+using namespace gapsp::rt;
 
 extern "C" {
 
@@ -468,13 +414,14 @@ gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask,
         delete h;
         return e == cudaErrorMemoryAllocation ? GAPSP_E_NOMEM : GAPSP_E_CUDA;
     };
+    keep_pool_warm();
     cudaError_t e;
-    if ((e = dalloc(&h->f, N)) != cudaSuccess) return fail(e);
-    if ((e = dalloc(&h->pgeo, N)) != cudaSuccess) return fail(e);
-    if ((e = dalloc(&h->tbase, (size_t)h->words)) != cudaSuccess) return fail(e);
-    if ((e = dalloc(&h->bound, N)) != cudaSuccess) return fail(e);
-    if ((e = dalloc(&h->status, 1)) != cudaSuccess) return fail(e);
-    if ((e = dalloc(&h->changed, 1)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&h->f, N, h->st)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&h->pgeo, N, h->st)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&h->tbase, (size_t)h->words, h->st)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&h->bound, N, h->st)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&h->status, 1, h->st)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&h->changed, 1, h->st)) != cudaSuccess) return fail(e);
     if ((e = cudaEventCreate(&h->ev0)) != cudaSuccess) return fail(e);
     if ((e = cudaEventCreate(&h->ev1)) != cudaSuccess) return fail(e);
     // the kernels read grey levels (grey) or free flags (mask) from h->f
@@ -484,7 +431,9 @@ gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask,
     if (o.kind == GAPSP_MASK) {
         // normalise the flags to 0/1
         std::vector<uint8_t> m(N);
-        if ((e = cudaMemcpy(m.data(), mask, N, cudaMemcpyDefault)) != cudaSuccess) return fail(e);
+        if ((e = cudaMemcpyAsync(m.data(), mask, N, cudaMemcpyDefault, h->st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(h->st)) != cudaSuccess)
+            return fail(e);
         for (auto& v : m) v = v ? 1 : 0;
         if ((e = cudaMemcpyAsync(h->f, m.data(), N, cudaMemcpyHostToDevice, h->st)) != cudaSuccess) return fail(e);
         if ((e = cudaStreamSynchronize(h->st)) != cudaSuccess) return fail(e);
@@ -493,15 +442,16 @@ gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask,
     if ((e = launch_image_prep(ip, h->st)) != cudaSuccess) return fail(e);
     h->launches += 2;
     if (o.kind == GAPSP_MASK) {
-        if ((e = dalloc(&h->comp, N)) != cudaSuccess) return fail(e);
-        if ((e = dalloc(&h->comp_size, N)) != cudaSuccess) return fail(e);
+        if ((e = dalloc(&h->comp, N, h->st)) != cudaSuccess) return fail(e);
+        if ((e = dalloc(&h->comp_size, N, h->st)) != cudaSuccess) return fail(e);
         CompArgs ca{H, W, o.conn, h->f, h->comp, h->comp_size, h->changed, h->status};
         if ((e = launch_components(ca, h->st)) != cudaSuccess) return fail(e);
         h->launches += 1;
     }
-    if ((e = cudaStreamSynchronize(h->st)) != cudaSuccess) return fail(e);
     int sw = 0;
-    if ((e = cudaMemcpy(&sw, h->status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpyAsync(&sw, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(h->st)) != cudaSuccess)
+        return fail(e);
     if (sw) {
         free_all(h);
         delete h;
@@ -513,8 +463,7 @@ gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask,
 
 void gapsp_destroy(gapsp_handle* h) {
     if (!h) return;
-    cudaStreamSynchronize(h->st);
-    free_all(h);
+    free_all(h);  // stream-ordered: after the work queued on the handle's stream
     delete h;
 }
 
@@ -524,7 +473,8 @@ gapsp_status gapsp_rows(gapsp_handle* h, const int32_t* sources, int K, uint32_t
     if (!sources || !out) return GAPSP_E_INVALID;
     const size_t N = h->N;
     std::vector<int32_t> hs(K);
-    CK(cudaMemcpy(hs.data(), sources, K * sizeof(int32_t), cudaMemcpyDefault));
+    CK(cudaMemcpyAsync(hs.data(), sources, K * sizeof(int32_t), cudaMemcpyDefault, h->st));
+    CK(cudaStreamSynchronize(h->st));
     for (int k = 0; k < K; ++k)
         if (hs[k] < 0 || hs[k] >= h->N) return GAPSP_E_INVALID;
     const bool out_dev = is_device_ptr(out);
@@ -532,17 +482,17 @@ gapsp_status gapsp_rows(gapsp_handle* h, const int32_t* sources, int K, uint32_t
     const size_t out_bytes = (size_t)K * N * sizeof(uint32_t);
     if (h->budget && (out_dev ? 0 : out_bytes) + (size_t)K * 4 > h->budget) return GAPSP_E_BUDGET;
     if (K > h->src_cap) {
-        dfree(h->src_dev);
+        dfree(h->src_dev, h->st);
         h->src_cap = 0;
-        CK(dalloc(&h->src_dev, K));
+        CK(dalloc(&h->src_dev, K, h->st));
         h->src_cap = K;
     }
     uint32_t* dout = out;
     if (!out_dev) {
         if (h->out_tmp_bytes < out_bytes) {
-            dfree(h->out_tmp);
+            dfree(h->out_tmp, h->st);
             h->out_tmp_bytes = 0;
-            CK(dalloc(&h->out_tmp, (size_t)K * N));
+            CK(dalloc(&h->out_tmp, (size_t)K * N, h->st));
             h->out_tmp_bytes = out_bytes;
         }
         dout = h->out_tmp;
@@ -571,59 +521,9 @@ gapsp_status gapsp_rows(gapsp_handle* h, const int32_t* sources, int K, uint32_t
 
 }  // extern "C"
 
-namespace {
+namespace gapsp {
+namespace rt {
 
-// One fill in progress: the state of gapsp_all_pairs between its steps, so
-// that several fills (one per image) can advance side by side.
-struct FillRun {
-    gapsp_handle* h = nullptr;
-    gapsp_order order = GAPSP_MINFILL;
-    uint32_t* D = nullptr;   // caller's array
-    uint32_t* Dd = nullptr;  // device array the kernels fill
-    bool d_dev = true;
-    cudaStream_t s = nullptr;
-    int nseq = 0;
-    uint64_t prepass = 0;
-    SelectArgs sa{};
-    RepArgs ra{};
-    PropArgs pa{};
-    TreeArgs ta{};
-    int rounds = 0;
-    bool finished = false;
-    // lookahead: the next K candidates of each round are propagated on a
-    // second stream while the round's tree and fill run
-    int K = 0;
-    PropArgs pa_ahead{};
-    cudaStream_t side[2] = {nullptr, nullptr};  // lookahead launches of even / odd rounds
-    cudaEvent_t e_sel = nullptr;
-    cudaEvent_t e_ahead[2] = {nullptr, nullptr};  // lookahead launch of an even / odd round
-    // chunks of rounds: the host keeps one chunk queued beyond the one whose
-    // "done" flag it waits for, so that the device never waits for the host
-    cudaEvent_t chunk_ev[2] = {nullptr, nullptr};
-    int chunks = 0, polled = 0;
-    // depth sums (N <= 16384) on a third, low-priority stream: a round's
-    // trees are handed over in a buffer of the round's parity, which the
-    // tree launch two rounds later waits for
-    cudaStream_t stat = nullptr;
-    cudaEvent_t e_tree[2] = {nullptr, nullptr}, e_depth[2] = {nullptr, nullptr};
-    FillRun() = default;
-    FillRun(const FillRun&) = delete;
-    FillRun& operator=(const FillRun&) = delete;
-    ~FillRun() {
-        if (e_sel) cudaEventDestroy(e_sel);
-        for (cudaEvent_t e : e_ahead)
-            if (e) cudaEventDestroy(e);
-        for (cudaEvent_t e : chunk_ev)
-            if (e) cudaEventDestroy(e);
-        for (cudaEvent_t e : e_tree)
-            if (e) cudaEventDestroy(e);
-        for (cudaEvent_t e : e_depth)
-            if (e) cudaEventDestroy(e);
-        for (cudaStream_t x : side)
-            if (x) cudaStreamDestroy(x);
-        if (stat) cudaStreamDestroy(stat);
-    }
-};
 
 // Candidates propagated ahead per round: one block (cluster) for each
 // multiprocessor the round's own sources leave free, unless set by option.
@@ -649,14 +549,14 @@ gapsp_status fill_begin(FillRun& r) {
     const size_t dbytes = N * N * sizeof(uint32_t);
     const size_t need = fill_state_bytes(h) + (r.d_dev ? 0 : dbytes);
     if (h->budget && need > h->budget) return GAPSP_E_BUDGET;
-    gapsp_status gs = ensure_fill_state(h);
+    gapsp_status gs = ensure_fill_state(h, r.s);
     if (gs != GAPSP_OK) return gs;
     r.Dd = r.D;
     if (!r.d_dev) {
         if (h->Dtmp_bytes < dbytes) {
-            dfree(h->Dtmp);
+            dfree(h->Dtmp, r.s);
             h->Dtmp_bytes = 0;
-            CK(dalloc(&h->Dtmp, N * N));
+            CK(dalloc(&h->Dtmp, N * N, r.s));
             h->Dtmp_bytes = dbytes;
         }
         r.Dd = h->Dtmp;
@@ -670,7 +570,8 @@ gapsp_status fill_begin(FillRun& r) {
         std::vector<uint8_t> freef;
         if (h->kind == GAPSP_MASK) {
             freef.resize(N);
-            CK(cudaMemcpy(freef.data(), h->f, N, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpyAsync(freef.data(), h->f, N, cudaMemcpyDeviceToHost, r.s));
+            CK(cudaStreamSynchronize(r.s));
         }
         std::vector<int32_t> ring, fstart;
         std::vector<uint8_t> fcyc;
@@ -689,7 +590,8 @@ gapsp_status fill_begin(FillRun& r) {
         std::vector<uint8_t> freef;
         if (h->kind == GAPSP_MASK) {
             freef.resize(N);
-            CK(cudaMemcpy(freef.data(), h->f, N, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpyAsync(freef.data(), h->f, N, cudaMemcpyDeviceToHost, r.s));
+            CK(cudaStreamSynchronize(r.s));
         }
         std::vector<int32_t> seq;
         if (r.order == GAPSP_NAIVE) {
@@ -807,6 +709,7 @@ gapsp_status fill_begin(FillRun& r) {
         ta.rows_per_block = rpb < 1 ? 1 : (rpb > 8 ? 8 : rpb);
         if (h->fill_rows) ta.rows_per_block = h->fill_rows;
         if ((size_t)ta.rows_per_block * row_bytes > 200 * 1024) ta.rows_per_block = rpb < 1 ? 1 : rpb;
+        if (!h->fill_rows) ta.rows_per_block = 0;  // marks claimed in global memory
     }
     r.rounds = 0;
     r.finished = false;
@@ -825,14 +728,20 @@ gapsp_status fill_begin(FillRun& r) {
     return GAPSP_OK;
 }
 
-// Rounds per chunk: small enough that the rounds queued after the fill is
-// done cost little, large enough that the host stays ahead of the device.
-constexpr int kChunk = 8;
 
 // Enqueues `chunk` rounds and an asynchronous copy of the "done" flag.
-gapsp_status fill_enqueue(FillRun& r, int chunk) {
+gapsp_status fill_enqueue(FillRun& r, int chunk, bool graph) {
     gapsp_handle* h = r.h;
     cudaStream_t s = r.s;
+    // captured into a graph: no per-launch timing events, and the chunk is
+    // closed on itself (below)
+    const bool prof = h->prof;
+    if (graph) h->prof = false;
+    struct RestoreProf {
+        gapsp_handle* h;
+        bool v;
+        ~RestoreProf() { h->prof = v; }
+    } restore{h, prof};
     for (int i = 0; i < chunk; ++i) {
         // the candidate buffers alternate by round: a round's lookahead
         // launch reads one while the next selection writes the other
@@ -847,7 +756,9 @@ gapsp_status fill_enqueue(FillRun& r, int chunk) {
             r.ta.dep_exit = h->dep_exit + (size_t)par * h->B * h->N;
             r.ta.dep_size = h->dep_size + (size_t)par * h->B * h->N;
             r.ta.dep_count = h->dep_count + par;
-            CK(cudaStreamWaitEvent(s, r.e_depth[par], 0));
+            // (in a graph, the launch of two rounds ago belongs to the
+            // previous chunk, which ended before this one started)
+            if (!graph || i >= 2) CK(cudaStreamWaitEvent(s, r.e_depth[par], 0));
         }
         {
             ProfScope ps(h, K_SELECT, s);
@@ -871,7 +782,7 @@ gapsp_status fill_enqueue(FillRun& r, int chunk) {
             h->launches += 1;
             // ... and this round's own propagation waits for the previous
             // round's lookahead, which may have computed its sources
-            CK(cudaStreamWaitEvent(s, r.e_ahead[par ^ 1], 0));
+            if (!graph || i >= 1) CK(cudaStreamWaitEvent(s, r.e_ahead[par ^ 1], 0));
         }
         {
             ProfScope ps(h, K_PROP, s);
@@ -905,6 +816,21 @@ gapsp_status fill_enqueue(FillRun& r, int chunk) {
         h->launches += 5;
     }
     r.rounds += chunk;
+    if (graph) {
+        // a graph's chunk ends with every side stream joined, and its flags
+        // always go to the first slot (the host reads them after the launch)
+        if (r.K > 0) {
+            CK(cudaStreamWaitEvent(s, r.e_ahead[0], 0));
+            CK(cudaStreamWaitEvent(s, r.e_ahead[1], 0));
+        }
+        if (r.stat) {
+            CK(cudaStreamWaitEvent(s, r.e_depth[0], 0));
+            CK(cudaStreamWaitEvent(s, r.e_depth[1], 0));
+        }
+        CK(cudaMemcpyAsync(h->h_done, h->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h->h_done + 2, h->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        return GAPSP_OK;
+    }
     const int par = r.chunks & 1;
     CK(cudaMemcpyAsync(h->h_done + par, h->done, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(h->h_done + 2 + par, h->status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -929,6 +855,10 @@ gapsp_status fill_poll(FillRun& r) {
     const int cap = h->max_rounds ? h->max_rounds : h->N + 2 + 64;
     if (!r.finished && r.rounds - kChunk >= cap) return GAPSP_E_TIMEOUT;
     return GAPSP_OK;
+}
+
+bool fill_chunk_ready(const FillRun& r) {
+    return cudaEventQuery(r.chunk_ev[r.polled & 1]) != cudaErrorNotReady;
 }
 
 // After an error: waits for everything the fill queued on its streams, so
@@ -975,17 +905,18 @@ gapsp_status fill_finish(FillRun& r, gapsp_stats* st) {
         st->ms_total = ms;
         if (st->round_new && st->round_new_cap) {
             const size_t n = std::min<uint64_t>(st->round_new_cap, hs[S_ROUNDS]);
-            if (n) CK(cudaMemcpy(st->round_new, h->round_new, n * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+            if (n) CK(cudaMemcpyAsync(st->round_new, h->round_new, n * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
         }
         if (st->sources && st->sources_cap) {
             const size_t n = std::min<uint64_t>(st->sources_cap, hs[S_PROPAGATIONS]);
-            if (n) CK(cudaMemcpy(st->sources, h->sel_log, n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+            if (n) CK(cudaMemcpyAsync(st->sources, h->sel_log, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         }
         if (h->kind == GAPSP_MASK) {
             // pairs in different components or touching an obstacle
             std::vector<int32_t> comp(N), size(N);
-            CK(cudaMemcpy(comp.data(), h->comp, N * 4, cudaMemcpyDeviceToHost));
-            CK(cudaMemcpy(size.data(), h->comp_size, N * 4, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpyAsync(comp.data(), h->comp, N * 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(size.data(), h->comp_size, N * 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
             uint64_t same = 0;
             for (size_t p = 0; p < N; ++p)
                 if (comp[p] == (int32_t)p) same += (uint64_t)size[p] * (uint64_t)(size[p] - 1) / 2;
@@ -1002,7 +933,175 @@ bool valid_order(gapsp_order o) {
            o == GAPSP_REPULSION;
 }
 
-}  // namespace
+}  // namespace rt
+}  // namespace gapsp
+
+namespace gapsp {
+namespace rt {
+
+// The batched form as one CUDA graph. Each image's fill is set up on a
+// worker stream of its own, then one chunk of its rounds (the round
+// kernels, the lookahead branch, the depth-sum stream and the copies of its
+// flags) is captured once into a graph; the chunks of all images are child
+// graphs, side by side, of one graph, so that a single graph launch advances
+// every image by one chunk. The host launches it one launch ahead of the
+// one whose flags it reads, drops the images that are done (re-instantiating
+// the graph without them) and stops when all are done. Rounds queued after
+// an image is done find nothing to select and return at once, exactly as in
+// gapsp_all_pairs, so every result and count equals that of the image alone.
+struct BatchGraph {
+    int n;
+    std::vector<cudaStream_t> ws;
+    std::vector<FillRun> runs;
+    std::vector<cudaGraph_t> chunk;
+    std::vector<uint64_t> per_chunk;  // kernel launches in one chunk of image i
+    std::vector<int> replays;         // chunks image i has been launched with
+    cudaStream_t ls = nullptr;        // the graph launches
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int> in_exec;         // images of the instantiated graph
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    explicit BatchGraph(int n_) : n(n_), ws(n_, nullptr), runs(n_), chunk(n_, nullptr), per_chunk(n_, 0),
+                                  replays(n_, 0) {}
+    ~BatchGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        for (cudaGraph_t g : chunk)
+            if (g) cudaGraphDestroy(g);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        if (ls) cudaStreamDestroy(ls);
+        for (cudaStream_t x : ws)
+            if (x) cudaStreamDestroy(x);
+    }
+    // stream a waits for everything queued on stream b so far
+    static cudaError_t order_after(cudaStream_t a, cudaStream_t b) {
+        cudaEvent_t e = nullptr;
+        cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        if (r == cudaSuccess) r = cudaEventRecord(e, b);
+        if (r == cudaSuccess) r = cudaStreamWaitEvent(a, e, 0);
+        if (e) cudaEventDestroy(e);
+        return r;
+    }
+    gapsp_status instantiate(const std::vector<int>& imgs) {
+        if (exec) {
+            CK(cudaStreamSynchronize(ls));
+            CK(cudaGraphExecDestroy(exec));
+            exec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        CK(cudaGraphCreate(&g, 0));
+        for (int i : imgs) {
+            cudaGraphNode_t node;
+            const cudaError_t e = cudaGraphAddChildGraphNode(&node, g, nullptr, 0, chunk[i]);
+            if (e != cudaSuccess) {
+                cudaGraphDestroy(g);
+                CK(e);
+            }
+        }
+        const cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        CK(e);
+        in_exec = imgs;
+        return GAPSP_OK;
+    }
+    gapsp_status launch(int k) {
+        CK(cudaGraphLaunch(exec, ls));
+        CK(cudaEventRecord(ev[k & 1], ls));
+        for (int i : in_exec) ++replays[i];
+        return GAPSP_OK;
+    }
+    gapsp_status run(gapsp_handle* const* hs, gapsp_order order, uint32_t* const* Ds, gapsp_stats* st) {
+        for (int i = 0; i < n; ++i) {
+            CK(cudaStreamCreateWithFlags(&ws[i], cudaStreamNonBlocking));
+            CK(order_after(ws[i], hs[i]->st));  // after the handle's own stream
+            runs[i].h = hs[i];
+            runs[i].order = order;
+            runs[i].D = Ds[i];
+            runs[i].s = ws[i];
+        }
+        gapsp_status gs = GAPSP_OK;
+        for (int i = 0; i < n && gs == GAPSP_OK; ++i) gs = fill_begin(runs[i]);
+        for (int i = 0; i < n && gs == GAPSP_OK; ++i) {
+            const uint64_t l0 = hs[i]->launches;
+            cudaError_t e = cudaStreamBeginCapture(ws[i], cudaStreamCaptureModeRelaxed);
+            if (e == cudaSuccess) {
+                gs = fill_enqueue(runs[i], kChunk, true);
+                cudaGraph_t g = nullptr;
+                e = cudaStreamEndCapture(ws[i], &g);
+                chunk[i] = g;
+                if (gs == GAPSP_OK && e != cudaSuccess) gs = GAPSP_E_CUDA;
+            } else {
+                gs = GAPSP_E_CUDA;
+            }
+            cudaGetLastError();
+            per_chunk[i] = hs[i]->launches - l0;
+            hs[i]->launches = l0;
+        }
+        if (gs == GAPSP_OK) {
+            if (cudaStreamCreateWithFlags(&ls, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) != cudaSuccess)
+                gs = GAPSP_E_CUDA;
+            for (int i = 0; i < n && gs == GAPSP_OK; ++i)
+                if (order_after(ls, ws[i]) != cudaSuccess) gs = GAPSP_E_CUDA;
+        }
+        std::vector<int> running;
+        for (int i = 0; i < n; ++i) running.push_back(i);
+        if (gs == GAPSP_OK) gs = instantiate(running);
+        int launched = 0, waited = 0;
+        if (gs == GAPSP_OK) gs = launch(launched++);
+        while (gs == GAPSP_OK && !running.empty()) {
+            if ((gs = launch(launched++)) != GAPSP_OK) break;
+            // the flags of the launch before: every image of it has run
+            // that chunk (a newer launch may have updated the flags since,
+            // with values that only move towards "done")
+            if (cudaEventSynchronize(ev[waited++ & 1]) != cudaSuccess) {
+                gs = GAPSP_E_CUDA;
+                break;
+            }
+            std::vector<int> still;
+            for (int i : running) {
+                gapsp_handle* h = hs[i];
+                const gapsp_status dev = status_from_word(h->h_done[2]);
+                if (dev != GAPSP_OK) gs = dev;
+                else if (h->cancel.load()) gs = GAPSP_E_CANCELLED;
+                else if (!h->h_done[0]) {
+                    const int cap = h->max_rounds ? h->max_rounds : h->N + 2 + 64;
+                    if ((waited)*kChunk >= cap) gs = GAPSP_E_TIMEOUT;
+                    still.push_back(i);
+                }
+            }
+            if (gs != GAPSP_OK) break;
+            // re-instantiate without the images that are done once they
+            // make up an eighth of the graph (their chunks cost launches)
+            if (still.size() < running.size() && (running.size() - still.size()) * 8 >= in_exec.size()) {
+                running = still;
+                if (!running.empty()) gs = instantiate(running);
+            } else {
+                running = still;
+            }
+        }
+        // every worker stream waits for the graph launches, then the fills
+        // finish on them
+        for (int i = 0; i < n; ++i) {
+            if (!ws[i]) continue;
+            if (ls && order_after(ws[i], ls) != cudaSuccess && gs == GAPSP_OK) gs = GAPSP_E_CUDA;
+            hs[i]->launches += per_chunk[i] * (uint64_t)replays[i];
+        }
+        for (int i = 0; i < n && gs == GAPSP_OK; ++i) gs = fill_finish(runs[i], st ? st + i : nullptr);
+        if (gs != GAPSP_OK) {
+            if (ls) cudaStreamSynchronize(ls);
+            for (int i = 0; i < n; ++i) fill_drain(runs[i]);
+        }
+        // the handles' streams are ordered after the batch
+        for (int i = 0; i < n; ++i)
+            if (ws[i]) order_after(hs[i]->st, ws[i]);
+        cudaGetLastError();
+        return gs;
+    }
+};
+
+}  // namespace rt
+}  // namespace gapsp
 
 extern "C" {
 
@@ -1047,51 +1146,8 @@ gapsp_status gapsp_all_pairs_batch(gapsp_handle* const* hs, int n, gapsp_order o
     }
     if (n == 0) return GAPSP_OK;
     for (int i = 0; i < n; ++i) hs[i]->cancel.store(0);
-    // one worker stream per image, ordered after the handle's own stream
-    std::vector<cudaStream_t> ws(n, nullptr);
-    std::vector<FillRun> runs(n);
-    gapsp_status result = GAPSP_OK;
-    for (int i = 0; i < n && result == GAPSP_OK; ++i) {
-        cudaEvent_t e = nullptr;
-        if (cudaStreamCreateWithFlags(&ws[i], cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventRecord(e, hs[i]->st) != cudaSuccess || cudaStreamWaitEvent(ws[i], e, 0) != cudaSuccess) {
-            cudaGetLastError();
-            result = GAPSP_E_CUDA;
-        }
-        if (e) cudaEventDestroy(e);
-        runs[i].h = hs[i];
-        runs[i].order = order;
-        runs[i].D = Ds[i];
-        runs[i].s = ws[i];
-    }
-    for (int i = 0; i < n && result == GAPSP_OK; ++i) result = fill_begin(runs[i]);
-    for (int i = 0; i < n && result == GAPSP_OK; ++i) result = fill_enqueue(runs[i], kChunk);
-    bool all = false;
-    while (result == GAPSP_OK && !all) {
-        for (int i = 0; i < n && result == GAPSP_OK; ++i)
-            if (!runs[i].finished) result = fill_enqueue(runs[i], kChunk);
-        all = true;
-        for (int i = 0; i < n && result == GAPSP_OK; ++i)
-            if (!runs[i].finished) {
-                result = fill_poll(runs[i]);
-                all = all && runs[i].finished;
-            }
-    }
-    for (int i = 0; i < n && result == GAPSP_OK; ++i) result = fill_finish(runs[i], st ? st + i : nullptr);
-    if (result != GAPSP_OK)
-        for (int i = 0; i < n; ++i) fill_drain(runs[i]);
-    for (int i = 0; i < n; ++i) {
-        if (!ws[i]) continue;
-        cudaEvent_t e = nullptr;
-        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
-            cudaEventRecord(e, ws[i]);
-            cudaStreamWaitEvent(hs[i]->st, e, 0);
-            cudaEventDestroy(e);
-        }
-        cudaStreamDestroy(ws[i]);
-    }
-    cudaGetLastError();
+    BatchGraph bg(n);
+    gapsp_status result = bg.run(hs, order, Ds, st);
     return result;
 }
 

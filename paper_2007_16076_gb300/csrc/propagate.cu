@@ -48,13 +48,28 @@ constexpr int MAXWARPS = 16;              // 4 directions x up to 4 phases
 constexpr int BIGX = PINF;                // identity of the prefix-min of v - P
 constexpr int BIGY = PINF + (1 << 18);    // identity of the suffix-min of v + P
 
+// Where element x of a line sits in shared memory. Lane j holds elements
+// VPL*j .. VPL*j + VPL - 1 of a line, so element k of the 32 lanes would be
+// VPL words apart and fall into 32 / VPL banks only; rotating each lane's
+// group of VPL elements by x / 32 spreads them over all 32 banks. The map
+// stores pixel (r, c) at swz(r) * pitch + swz(c) (odd pitch): element k of
+// a row line (consecutive words) and of a column line (rows pitch apart)
+// then sits in a different bank for every lane. Lines are padded to a
+// multiple of VPL so that the rotation stays inside the storage.
+template <int VPL>
+__host__ __device__ __forceinline__ int swz(int x) {
+    return VPL == 1 ? x : ((x & ~(VPL - 1)) | ((x + (x >> 5)) & (VPL - 1)));
+}
+
+__host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+template <int VPL>
 struct SmemMap {
     int* base;
     int pitch;
-    __device__ __forceinline__ int ld(int r, int c) const {
-        return *((volatile const int*)(base + r * pitch + c));
-    }
-    __device__ __forceinline__ void lower(int r, int c, int v) const { atomicMin(base + r * pitch + c, v); }
+    __device__ __forceinline__ int* at(int r, int c) const { return base + swz<VPL>(r) * pitch + swz<VPL>(c); }
+    __device__ __forceinline__ int ld(int r, int c) const { return *((volatile const int*)at(r, c)); }
+    __device__ __forceinline__ void lower(int r, int c, int v) const { atomicMin(at(r, c), v); }
 };
 
 struct GlobMap {
@@ -73,6 +88,7 @@ struct Shared {
     uint8_t* chR;       // [3][hs]: row line lowered during round t (slot t % 3)
     uint8_t* chC;       // [3][W]: column line lowered during round t
     int r0, hs;
+    int pitch;                // map pitch of every strip of the cluster (shared memory)
     // rows next to the strip, owned by the neighbour blocks of the cluster
     // (distributed shared memory), or NULL at the image border
     const int* up_map;        // neighbour above: its map; its last row is row r0 - 1
@@ -150,11 +166,12 @@ __device__ bool sweep(const PropArgs& a, const Map& map, const Shared& sh, int d
                     has_pred = true;
                     pred_changed = rch[((round + 2) % 3) * rhs + rrow] != 0 ||
                                    *((volatile const uint8_t*)(rch + (round % 3) * rhs + rrow)) != 0;
-                    const int rpitch = a.W | 1;
 #pragma unroll
                     for (int k = 0; k < VPL; ++k) {
                         const int pos = VPL * lane + k;
-                        const int dv = pos < len ? *((volatile const int*)(rmap + rrow * rpitch + pos)) : PINF;
+                        const int dv =
+                            pos < len ? *((volatile const int*)(rmap + swz<VPL>(rrow) * sh.pitch + swz<VPL>(pos)))
+                                      : PINF;
                         const int fg = pos < len ? (int)__ldg(a.f + grow * a.W + pos) : 0;
                         gp[k] = KIND == 0 ? (pos < len ? dv + fg : dv) : KIND == 2 ? dv : (fg ? dv : PINF);
                         gf[k] = fg;
@@ -473,15 +490,16 @@ __device__ __forceinline__ int warm_bound(uint32_t dx, int dq) {
 // (obstacles stay unreached). Warm, a line is flagged for the first round
 // when it holds a finite value (flag slot 2 is the one round 0 reads as
 // "previous round"); returns whether the map is warm.
-template <int KIND>
+template <int KIND, int VPL>
 __device__ bool init_map(const PropArgs& a, int* smap, int pitch, uint8_t* flags, int r0, int hs, int src,
                          const Helpers& h, int nh) {
+    const SmemMap<VPL> map{smap, pitch};
     const int n = hs * a.W, g0 = r0 * a.W;
     const bool warm = a.warm_rows && src >= 0;
     if (!warm) {
         for (int p = threadIdx.x; p < n; p += blockDim.x) {
             const int r = p / a.W, c = p - r * a.W;
-            smap[r * pitch + c] = is_seed(a, src, g0 + p) ? 0 : PINF;
+            *map.at(r, c) = is_seed(a, src, g0 + p) ? 0 : PINF;
         }
         return false;
     }
@@ -507,7 +525,7 @@ __device__ bool init_map(const PropArgs& a, int* smap, int pitch, uint8_t* flags
                 int x = v[k];
                 if (KIND == 1 && !a.f[g0 + p + k]) x = PINF;
                 if (is_seed(a, src, g0 + p + k)) x = 0;
-                smap[r * pitch + c + k] = x;
+                *map.at(r, c + k) = x;
                 if (x < PINF) {
                     any = true;
                     fc[c + k] = 1;
@@ -522,7 +540,7 @@ __device__ bool init_map(const PropArgs& a, int* smap, int pitch, uint8_t* flags
             if (KIND == 1 && !a.f[g0 + p]) x = PINF;
             if (is_seed(a, src, g0 + p)) x = 0;
             const int r = p / a.W, c = p - r * a.W;
-            smap[r * pitch + c] = x;
+            *map.at(r, c) = x;
             if (x < PINF) {
                 fr[r] = 1;
                 fc[c] = 1;
@@ -557,29 +575,33 @@ __global__ void __launch_bounds__(32 * MAXWARPS) k_propagate_smem(PropArgs a, in
     __shared__ Helpers s_help;
     const int nh = pick_helpers(a, src, s_help);
     // the flags are cleared by setup_shared: it comes first, then the map
-    Shared sh = setup_shared<KIND, VPL>(a, reinterpret_cast<char*>(smap + hs * pitch), r0, hs);
+    // every strip's map has the same padded height, so the state after it
+    // sits at the same offset in every block of the cluster
+    const int rows = round_up(hs0, VPL);
+    Shared sh = setup_shared<KIND, VPL>(a, reinterpret_cast<char*>(smap + rows * pitch), r0, hs);
+    sh.pitch = pitch;
     if (threadIdx.x == 0) { s_flag[0] = 0; s_flag[1] = 0; }
     __syncthreads();
-    const bool warm = init_map<KIND>(a, smap, pitch, sh.chR, r0, hs, src, s_help, nh);
+    const bool warm = init_map<KIND, VPL>(a, smap, pitch, sh.chR, r0, hs, src, s_help, nh);
     if (!warm) flag_seed_lines(a, sh, src);
     if (CL) {
         cg::cluster_group cl = cg::this_cluster();
         if (rank > 0) {
             sh.up_map = cl.map_shared_rank(smap, rank - 1);
             sh.up_hs = hs0;
-            sh.up_chR = reinterpret_cast<const uint8_t*>(sh.up_map + sh.up_hs * pitch);
+            sh.up_chR = reinterpret_cast<const uint8_t*>(sh.up_map + rows * pitch);
         }
         if (rank + 1 < C) {
             sh.dn_map = cl.map_shared_rank(smap, rank + 1);
             sh.dn_hs = min(hs0, a.H - (rank + 1) * hs0);
-            sh.dn_chR = reinterpret_cast<const uint8_t*>(sh.dn_map + sh.dn_hs * pitch);
+            sh.dn_chR = reinterpret_cast<const uint8_t*>(sh.dn_map + rows * pitch);
         }
         cl.sync();  // every strip is initialised before any remote access
     } else {
         __syncthreads();
     }
-    const SmemMap map{smap, pitch};
-    run_block<CONN, KIND, VPL, SmemMap, CL, EX>(a, map, sh, s_flag, &s_rounds);
+    const SmemMap<VPL> map{smap, pitch};
+    run_block<CONN, KIND, VPL, SmemMap<VPL>, CL, EX>(a, map, sh, s_flag, &s_rounds);
     if (CL) cg::this_cluster().sync();  // no block leaves while others may read it
     __syncthreads();
     if (threadIdx.x == 0 && a.sweeps) atomicAdd(a.sweeps, (unsigned long long)s_rounds * (blockDim.x >> 5));
@@ -590,13 +612,13 @@ __global__ void __launch_bounds__(32 * MAXWARPS) k_propagate_smem(PropArgs a, in
         int4* o4 = reinterpret_cast<int4*>(o);
         for (int q = threadIdx.x; q < n / 4; q += blockDim.x) {
             const int p = 4 * q, r = p / a.W, c = p - r * a.W;
-            const int* m = smap + r * pitch + c;
-            o4[q] = make_int4(finish(a, m[0]), finish(a, m[1]), finish(a, m[2]), finish(a, m[3]));
+            o4[q] = make_int4(finish(a, *map.at(r, c)), finish(a, *map.at(r, c + 1)), finish(a, *map.at(r, c + 2)),
+                              finish(a, *map.at(r, c + 3)));
         }
     } else {
         for (int p = threadIdx.x; p < n; p += blockDim.x) {
             const int r = p / a.W, c = p - r * a.W;
-            o[p] = finish(a, smap[r * pitch + c]);
+            o[p] = finish(a, *map.at(r, c));
         }
     }
     __syncthreads();
@@ -652,10 +674,13 @@ __global__ void __launch_bounds__(32 * MAXWARPS) k_propagate_glob(PropArgs a) {
 
 constexpr int SMEM_LIMIT = 220 * 1024;
 
+// Map pitch: the width padded to a multiple of the values per lane, odd.
+int map_pitch(const PropArgs& a) { return round_up(a.W, prop_vpl(a.H > a.W ? a.H : a.W)) | 1; }
+
 size_t smem_for_strips(const PropArgs& a, int c) {
-    const int pitch = a.W | 1;
     const int hs = (a.H + c - 1) / c;
-    return (size_t)hs * pitch * sizeof(int) + shared_state_bytes(hs, a.W);
+    const int rows = round_up(hs, prop_vpl(a.H > a.W ? a.H : a.W));
+    return (size_t)rows * map_pitch(a) * sizeof(int) + shared_state_bytes(hs, a.W);
 }
 
 // Row strips (blocks of one cluster) per source: the requested cluster size,
@@ -671,7 +696,7 @@ int strips_per_job(const PropArgs& a) {
 
 template <int CONN, int KIND, int VPL>
 cudaError_t launch_one(const PropArgs& a, int jobs, cudaStream_t st) {
-    const int pitch = a.W | 1;  // odd pitch: row and column lines spread over the banks
+    const int pitch = map_pitch(a);
     const int threads = 32 * 4 * (a.phases == 4 ? 4 : a.phases == 2 ? 2 : 1);
     static std::atomic<unsigned long long> attr{0};
     once_per_device(attr, [] {

@@ -669,6 +669,104 @@ __global__ void __launch_bounds__(256, 4) k_fill(TreeArgs a) {
     if (threadIdx.x < nu && ((s_gain >> threadIdx.x) & 1u)) a.dirty[s_rows[threadIdx.x]] = 1;
 }
 
+#ifndef FILL_G_MINB
+#define FILL_G_MINB 8
+#endif
+
+// The same fill with the marks claimed in global memory, through L2: no
+// staging, so a block needs no shared memory and no barrier, and every warp
+// leaves as soon as its own walks end. A warp owns 8 consecutive rows
+// (lanes 0-7, 8-15, ...: the same rows) for 4 trees, so the 8 walks of one
+// tree, whose paths soon merge, fetch mostly the same records. Each step of
+// a walk fetches together the next two segment masks, the record two
+// segments ahead and row b's mark words for the two tiles of those
+// segments; a segment's bits not yet in the word are claimed with one 64-bit
+// atomic OR (the word read ahead may be stale, the OR's old value decides).
+// A claimed bit is a new pair {a, b}: D[a][b] = D[b][a] = d(s,b) - d(s,a)
+// (Property 1) and the mirror bit (row a, column b) as in k_fill.
+__global__ void __launch_bounds__(128, FILL_G_MINB) k_fill_g(TreeArgs a, int quads) {
+    pdl_wait();
+    pdl_trigger();
+    const int nsel = *a.nsel;
+    if (nsel == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int grp = warp / quads, quad = warp - grp * quads;
+    const int b = grp * 8 + (lane & 7), j = quad * 4 + (lane >> 3);
+    if (b >= a.N || j >= nsel) return;
+    if (__ldcg(a.cnt + b) >= (uint32_t)a.N) return;  // row b holds every pair already
+    const int s = a.sel[j];
+    // 32-bit offsets (N^2 < 2^32): fewer registers, more warps in flight
+    const uint32_t srow = (uint32_t)s * (uint32_t)a.N, brow = (uint32_t)b * (uint32_t)a.N;
+    const uint32_t db = __ldg(a.D + srow + b);
+    if (b == s || db == UNREACH) return;
+    const ulonglong2* seg = a.seg + (size_t)j * a.N;
+    const uint32_t mrow = (uint32_t)b * (uint32_t)a.words;
+    const uint32_t gb = __ldg(a.pgeo + b);
+    const int tb = (int)(gb >> 8);
+    const unsigned long long bbit = 1ull << (gb & 63);
+    bool gained = false;
+    auto take = [&](int t, unsigned long long m, unsigned long long w) {
+        unsigned long long nb = m & ~w;
+        if (!nb) return;
+        nb &= ~atomicOr(a.marks + mrow + t, nb);
+        if (!nb) return;
+        gained = true;
+        const int base = __ldg(a.tbase + t);
+        while (nb) {
+            int ap[4];
+            uint32_t dv[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                ap[k] = -1;
+                if (nb) {
+                    const int bit = __ffsll((long long)nb) - 1;
+                    nb &= nb - 1;
+                    ap[k] = base + (bit >> 3) * a.W + (bit & 7);
+                    dv[k] = __ldg(a.D + srow + ap[k]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (ap[k] < 0) continue;
+                const uint32_t val = db - dv[k];
+                atomicOr(a.marks + (uint32_t)ap[k] * (uint32_t)a.words + tb, bbit);
+                a.dirty[ap[k]] = 1;
+                __stcs(a.Dw + (uint32_t)ap[k] * (uint32_t)a.N + b, val);
+                __stcs(a.Dw + brow + ap[k], val);
+            }
+        }
+    };
+    ulonglong2 g = __ldg(seg + b);
+    unsigned long long m = g.x & ~bbit;  // b's ancestors inside b's tile
+    int t = tb;
+    unsigned long long w = ld_cg64(a.marks + mrow + t);
+    for (int guard = 0; guard <= a.N; ++guard) {
+        const unsigned long long y = g.y;
+        const int e1 = (int)(y & 0x1FFFFu) - 1, t1 = (int)((y >> 17) & 0x3FFu);
+        const int e2 = (int)((y >> 27) & 0x1FFFFu) - 1, t2 = (int)((y >> 44) & 0x3FFu);
+        unsigned long long m1 = 0, w1 = ~0ull, w2 = ~0ull;
+        ulonglong2 g2 = make_ulonglong2(0ull, 0ull);
+        if (e1 >= 0) {
+            m1 = __ldg(reinterpret_cast<const unsigned long long*>(seg + e1));
+            w1 = ld_cg64(a.marks + mrow + t1);
+        }
+        if (e2 >= 0) {
+            g2 = __ldg(seg + e2);
+            w2 = ld_cg64(a.marks + mrow + t2);
+        }
+        take(t, m, w);
+        if (e1 < 0) break;
+        take(t1, m1, w1);
+        if (e2 < 0) break;
+        g = g2;
+        t = t2;
+        m = g.x;
+        w = w2;
+    }
+    if (gained) a.dirty[b] = 1;
+}
+
 // Fill counts of the rows that gained marks: cnt(x) = cnt at the start +
 // the number of marked pairs of row x (both bits of a pair are set, so row
 // x holds every filled pair {x, y}). One warp per row. The increments are
@@ -700,9 +798,9 @@ __global__ void k_recount(TreeArgs a) {
 
 // cudaLaunchKernelEx with an optional cluster size and the programmatic
 // dependent launch attribute.
-template <typename... KArgs>
+template <typename... KArgs, typename... Args>
 cudaError_t launch_ex(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t st, bool pdl,
-                      int cluster, const TreeArgs& a) {
+                      int cluster, Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);
@@ -724,7 +822,7 @@ cudaError_t launch_ex(void (*kern)(KArgs...), int grid, int block, size_t smem, 
     }
     cfg.attrs = at;
     cfg.numAttrs = n;
-    return cudaLaunchKernelEx(&cfg, kern, a);
+    return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 cudaError_t launch_recount(const TreeArgs& a, cudaStream_t st, bool pdl) {
@@ -797,7 +895,12 @@ cudaError_t launch_depths(const TreeArgs& a, int B, cudaStream_t st) {
 }
 
 cudaError_t launch_fill(const TreeArgs& a, int B, cudaStream_t st, bool pdl) {
-    (void)B;
+    if (a.rows_per_block == 0) {
+        // marks claimed in global memory: one warp per 8 rows x 4 trees
+        const int quads = (B + 3) / 4;
+        const long long warps = (long long)((a.N + 7) / 8) * quads;
+        return launch_ex(k_fill_g, (int)((warps + 3) / 4), 128, 0, st, pdl, 1, a, quads);
+    }
     // mark rows, then one "changed" byte per row word
     const size_t smem = fill_smem_bytes(a.rows_per_block, a.words);
     static std::atomic<unsigned long long> attr_set{0};

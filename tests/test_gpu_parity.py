@@ -347,6 +347,29 @@ def test_full_size_blobs128(gp, order):
 # one value per lane where the width is not a multiple of 4)
 # --------------------------------------------------------------------------
 
+@pytest.mark.parametrize("fill_rows", [0, 1, 8])
+@pytest.mark.parametrize("shape,conn,kind", [((29, 31), 8, "grey"), ((40, 24), 4, "mask"), ((136, 121), 8, "grey")])
+def test_fill_variants(gp, shape, conn, kind, fill_rows):
+    """The tree fill with the marks claimed in global memory (fill_rows 0,
+    the default) and staged in shared memory (1 or 8 rows per block): the
+    whole array against Dijkstra and the counts against the oracle."""
+    H, W = shape
+    if kind == "mask":
+        mask = synth.disk_mask(H, W, 0.4, 2, 4, seed=H)
+        img = np.zeros((H, W), dtype=np.uint8)
+    else:
+        mask = None
+        img = synth.scaled_blobs(H, W, conn, seed=W).img
+    with gp.Image(None if mask is not None else img, conn=conn, kind=kind, mask=mask, B=32,
+                  fill_rows=fill_rows) as im:
+        D, st = im.all_pairs("minfill")
+    assert np.array_equal(_u32(D), oracle.apsp(img, conn=conn, kind=kind, mask=mask))
+    if H * W <= 4096:
+        ref = oracle.fill(img, "minfill", B=32, conn=conn, kind=kind, mask=mask)
+        for k in ("propagations", "distance_ops", "new_pairs", "rounds"):
+            assert st[k] == getattr(ref, k), k
+
+
 @pytest.mark.parametrize("order", ["minfill", "extrema"])
 def test_counts_blobs136x121(gp, order):
     """136x121 (N = 16456), 8-connected, B = 32: counts, per-round new pairs
@@ -433,3 +456,51 @@ def test_all_pairs_batch_equals_alone(gp):
     finally:
         for im in ims:
             im.close()
+
+
+@pytest.mark.parametrize("order", ["minfill", "naive", "spiral", "extrema", "repulsion"])
+def test_batch_graph_every_order(gp, order):
+    """The batch runs as one CUDA graph over all images: twelve images of
+    uneven sizes (one 136 x 121, above the small-image paths), each equal to
+    its fill alone; the handles work normally afterwards."""
+    rng = np.random.default_rng(7)
+    specs = [(int(rng.integers(6, 48)), int(rng.integers(6, 48)), 4 if k % 3 == 0 else 8) for k in range(11)]
+    specs.append((136, 121, 8))
+    imgs = [synth.scaled_blobs(H, W, c, seed=k).img for k, (H, W, c) in enumerate(specs)]
+    ims = [gp.Image(img, conn=c, B=16 if k % 2 else 32, seed=k) for k, (img, (H, W, c)) in
+           enumerate(zip(imgs, specs))]
+    try:
+        outs, stats = gp.all_pairs_batch(ims, order)
+        for im, img, (H, W, c), D, st in zip(ims, imgs, specs, outs, stats):
+            alone, sa = im.all_pairs(order)
+            assert np.array_equal(_u32(D), _u32(alone))
+            for key in ("propagations", "distance_ops", "new_pairs", "rounds"):
+                assert st[key] == sa[key], key
+            if H * W <= 1024:
+                assert np.array_equal(_u32(D), oracle.apsp(img, conn=c))
+        # a second batch on the same handles gives the same again
+        outs2, stats2 = gp.all_pairs_batch(ims, order)
+        for D, D2, st, st2 in zip(outs, outs2, stats, stats2):
+            assert np.array_equal(_u32(D), _u32(D2))
+            assert st["propagations"] == st2["propagations"]
+    finally:
+        for im in ims:
+            im.close()
+
+
+def test_tune_picks_a_candidate_and_caches(gp, tmp_path):
+    """The autotuner returns one of its candidates, and the result of a fill
+    with the tuned options is the same array; a second call reads the
+    cache instead of measuring again."""
+    img = synth.scaled_blobs(40, 44, 8, seed=3).img
+    cache = tmp_path / "tune.txt"
+    t = gp.tune(img, conn=8, cache=cache)
+    assert t["B"] in (16, 32, 64) and t["lookahead"] in (0, -1) and t["fill_rows"] in (0, 8)
+    assert t["ms"] > 0
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and lines[0].startswith("gapsp-tune-1 40 44 8 0 2 ")
+    t2 = gp.tune(img, conn=8, cache=cache)
+    assert t2 == t and len(cache.read_text().splitlines()) == 1
+    with gp.Image(img, conn=8, B=t["B"], lookahead=t["lookahead"], fill_rows=t["fill_rows"]) as im:
+        D, _ = im.all_pairs("minfill")
+    assert np.array_equal(_u32(D), oracle.apsp(img, conn=8))
