@@ -41,7 +41,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="steps256",
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(PROFILE_WORKLOADS), default="steps256",
                     help="the timed image (default: 256x256 blobs with step edges)")
     ap.add_argument("--no-extras", action="store_true", help="skip the side measurements")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
@@ -53,11 +53,13 @@ def _args():
 
 # name -> synth factory (every one 8-connected, B = 32)
 WORKLOADS = {"steps256": "steps_256", "mask256": "mask_256", "blobs128": "batched_128"}
+# smaller cases for profiling only (not measured among the side workloads)
+PROFILE_WORKLOADS = {"steps160": "steps_160"}
 
 
 def _workload(name: str, rank: int):
     from paper_2007_16076_gb300 import synth
-    return getattr(synth, WORKLOADS[name])(seed=rank)
+    return getattr(synth, {**WORKLOADS, **PROFILE_WORKLOADS}[name])(seed=rank)
 
 
 def _image(gp, w, stream, **kw):

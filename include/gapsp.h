@@ -82,7 +82,10 @@ typedef enum {
 typedef enum {
     GAPSP_GREY = 0, /* w(p,q) = f(p) + f(q) + 1: sum of grey levels (Sec. 2, eq. "distance somme") */
     GAPSP_MASK = 1, /* w = 2 between free pixels; obstacles have no edges */
-    GAPSP_L1 = 2    /* w(p,q) = |f(p) - f(q)| + 1: pseudo-metric L1 (Sec. 2, eq. "distance abs difference") */
+    GAPSP_L1 = 2,   /* w(p,q) = |f(p) - f(q)| + 1: pseudo-metric L1 (Sec. 2, eq. "distance abs difference") */
+    GAPSP_SUM = 3   /* multichannel image of L channels (Sec. 2: values in T^L): the sum pseudo-metric
+                       over the channels, w(p,q) = sum_l (f_l(p) + f_l(q)) + 1 = F(p) + F(q) + 1 with
+                       F = sum_l f_l; handles of this kind come from gapsp_create_channels */
 } gapsp_kind;
 
 typedef struct {
@@ -162,6 +165,22 @@ gapsp_status gapsp_create(const uint8_t *img, int H, int W, const uint8_t *mask,
                           const gapsp_opts *opts, gapsp_handle **out);
 
 /*
+ * Creates a handle for a multichannel image with the sum pseudo-metric over
+ * its channels (GAPSP_SUM; Sec. 2 extends the pseudo-metrics to images with
+ * values in T^L): w(p,q) = sum_l (f_l(p) + f_l(q)) + 1.
+ *   planes : L*H*W uint8, channel after channel, each H*W row-major; host or
+ *            device pointer, read during the call only.
+ *   L      : 1..GAPSP_MAX_CHANNELS; with N = H*W, (N - 1) * (510 * L + 1) must
+ *            stay below 2^30 - 2^18 (every distance fits the kernels' int32
+ *            sweeps; always true up to 32 channels).
+ * opts.kind is ignored (GAPSP_SUM). The handle then serves gapsp_all_pairs,
+ * gapsp_all_pairs_batch and gapsp_rows like any other. Errors as gapsp_create.
+ */
+#define GAPSP_MAX_CHANNELS 32
+gapsp_status gapsp_create_channels(const uint8_t *planes, int L, int H, int W, const gapsp_opts *opts,
+                                   gapsp_handle **out);
+
+/*
  * Fills the whole N x N array D (Sec. 2, eq. "A": all (N^2 - N)/2 pairs) by
  * propagations from sources chosen in `order`, B per round, plus the
  * geodesic-tree fill of Property 1.
@@ -221,6 +240,11 @@ gapsp_status gapsp_cancel(gapsp_handle *h);
 
 /* Static text for a status code. */
 const char *gapsp_strerror(gapsp_status s);
+
+/* The CUDA runtime call behind this host thread's last GAPSP_E_CUDA or
+ * GAPSP_E_NOMEM from a handle call: source line, the call and the runtime's
+ * error text ("" if none). Valid until this thread's next failing call. */
+const char *gapsp_last_error_detail(void);
 
 /* Number of kernels the library launched on this handle since its creation
  * (for launch accounting). */

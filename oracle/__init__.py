@@ -64,13 +64,21 @@ def _ptr(a):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 
 
-KINDS = {"grey": 0, "mask": 1, "l1": 2}
+KINDS = {"grey": 0, "mask": 1, "l1": 2, "sum": 3}
 
 
 def _prep(img, mask, kind):
-    img = np.ascontiguousarray(img, dtype=np.uint8)
-    H, W = img.shape
+    """Image, mask, sizes and the oracle's kind code. For kind "sum" the
+    image is L x H x W (a multichannel image, Sec. 2: values in T^L) and the
+    code carries L: 3 | (L << 8)."""
     k = KINDS[kind] if isinstance(kind, str) else int(kind)
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    if k == 3:
+        if img.ndim != 3:
+            raise ValueError("the sum kind takes an L x H x W image")
+        L, H, W = img.shape
+        return img, None, H, W, 3 | (L << 8)
+    H, W = img.shape
     m = None
     if k == 1:
         if mask is None:

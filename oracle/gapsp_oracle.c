@@ -43,10 +43,22 @@
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
-    const uint8_t *f;    /* grey values, H*W, row-major */
+    const uint8_t *f;    /* grey values, H*W, row-major; for kind 3, nch planes of H*W */
     const uint8_t *mask; /* 1 = free pixel; NULL means every pixel is free */
-    int H, W, conn, kind; /* kind 0 = sum of grey levels, 1 = mask (w = 2), 2 = L1 */
+    int H, W, conn, kind; /* kind 0 = sum of grey levels, 1 = mask (w = 2), 2 = L1,
+                             3 = sum over the channels of a multichannel image */
+    int nch;              /* channels (kind 3) */
 } or_graph;
+
+/* The exported functions take the kind as a code: 0, 1, 2, or 3 | (L << 8)
+ * for a multichannel image of L channels (Sec. 2: values in T^L), whose f
+ * then holds the L planes one after the other. */
+static or_graph or_make(const uint8_t *f, const uint8_t *mask, int H, int W, int conn, int code) {
+    or_graph g = {f, mask, H, W, conn, code & 0xFF, code >> 8};
+    return g;
+}
+
+static int or_code(const or_graph *g) { return g->kind | (g->nch << 8); }
 
 static int or_free(const or_graph *g, int p) {
     return g->kind != 1 || g->mask == NULL || g->mask[p] != 0;
@@ -74,11 +86,22 @@ static int or_neighbours(const or_graph *g, int p, int *out) {
 }
 
 /* Edge weight: sum of grey levels plus one (Sec. 2, eq. "distance somme",
- * with +1), 2 between free pixels of a mask, or the absolute difference of
+ * with +1), 2 between free pixels of a mask, the absolute difference of
  * grey levels plus one (Sec. 2, pseudo-metric L1, eq. "distance abs
- * difference", with +1 so that every edge costs at least 1). */
+ * difference", with +1 so that every edge costs at least 1), or, for a
+ * multichannel image (Sec. 2, values in T^L), the sum pseudo-metric added
+ * over its channels plus one. Parity status of the channel sum: pinned by
+ * brute force, Floyd-Warshall, the one-channel case, constant channels and
+ * the 1 x W closed form. */
 static uint32_t or_weight(const or_graph *g, int p, int q) {
     if (g->kind == 1) return 2u;
+    if (g->kind == 3) {
+        /* the sum pseudo-metric summed over the channels, plus one */
+        size_t N = (size_t)g->H * g->W;
+        uint32_t w = 1u;
+        for (int l = 0; l < g->nch; l++) w += (uint32_t)g->f[l * N + p] + (uint32_t)g->f[l * N + q];
+        return w;
+    }
     if (g->kind == 2) return (uint32_t)(g->f[p] > g->f[q] ? g->f[p] - g->f[q] : g->f[q] - g->f[p]) + 1u;
     return (uint32_t)g->f[p] + (uint32_t)g->f[q] + 1u;
 }
@@ -155,7 +178,7 @@ static void or_dijkstra(const or_graph *g, const int *src, int nsrc, uint32_t *d
  * enumeration, the 1-D closed form and the constant-image closed forms. */
 void or_sssp(const uint8_t *f, const uint8_t *mask, int H, int W, int conn, int kind,
              int s, uint32_t *row) {
-    or_graph g = {f, mask, H, W, conn, kind};
+    or_graph g = or_make(f, mask, H, W, conn, kind);
     if (!or_free(&g, s)) {
         for (int p = 0; p < H * W; p++) row[p] = OR_UNREACH;
         row[s] = 0;
@@ -167,7 +190,7 @@ void or_sssp(const uint8_t *f, const uint8_t *mask, int H, int W, int conn, int 
 /* Multi-source distance (used by the geodesic-extrema pre-pass). */
 void or_msssp(const uint8_t *f, const uint8_t *mask, int H, int W, int conn, int kind,
               const int32_t *src, int nsrc, uint32_t *row) {
-    or_graph g = {f, mask, H, W, conn, kind};
+    or_graph g = or_make(f, mask, H, W, conn, kind);
     or_dijkstra(&g, (const int *)src, nsrc, row);
 }
 
@@ -183,7 +206,7 @@ static void *or_apsp_worker(void *arg) {
     int N = j->g->H * j->g->W;
     for (int i = j->t; i < j->nrows; i += j->T) {
         int s = j->rows ? j->rows[i] : i;
-        or_sssp(j->g->f, j->g->mask, j->g->H, j->g->W, j->g->conn, j->g->kind, s,
+        or_sssp(j->g->f, j->g->mask, j->g->H, j->g->W, j->g->conn, or_code(j->g), s,
                 j->D + (size_t)i * N);
     }
     return NULL;
@@ -194,7 +217,7 @@ static void *or_apsp_worker(void *arg) {
  * method of Sec. 1: one propagation per source. */
 void or_rows(const uint8_t *f, const uint8_t *mask, int H, int W, int conn, int kind,
              const int32_t *src, int nsrc, uint32_t *out, int nthreads) {
-    or_graph g = {f, mask, H, W, conn, kind};
+    or_graph g = or_make(f, mask, H, W, conn, kind);
     if (nthreads < 1) nthreads = 1;
     if (nthreads > 256) nthreads = 256;
     pthread_t th[256];
@@ -212,7 +235,7 @@ void or_rows(const uint8_t *f, const uint8_t *mask, int H, int W, int conn, int 
  * independent route to the same array. */
 void or_floyd(const uint8_t *f, const uint8_t *mask, int H, int W, int conn, int kind,
               uint32_t *D) {
-    or_graph g = {f, mask, H, W, conn, kind};
+    or_graph g = or_make(f, mask, H, W, conn, kind);
     int N = H * W, nb[8];
     uint64_t *M = (uint64_t *)malloc((size_t)N * N * sizeof(uint64_t));
     const uint64_t INF = (uint64_t)1 << 62;
@@ -241,7 +264,7 @@ void or_floyd(const uint8_t *f, const uint8_t *mask, int H, int W, int conn, int
 
 void or_parents(const uint8_t *f, const uint8_t *mask, int H, int W, int conn, int kind,
                 const uint32_t *drow, int s, int32_t *parent) {
-    or_graph g = {f, mask, H, W, conn, kind};
+    or_graph g = or_make(f, mask, H, W, conn, kind);
     int N = H * W, nb[8];
     for (int b = 0; b < N; b++) {
         parent[b] = -1;
@@ -352,7 +375,7 @@ static int or_rank_cmp(const void *a, const void *b) {
  * number of components. */
 int or_extrema(const uint8_t *f, const uint8_t *mask, int H, int W, int conn, int kind,
                uint32_t *e, uint32_t *gdist, int32_t *centroids, int32_t *rank) {
-    or_graph g = {f, mask, H, W, conn, kind};
+    or_graph g = or_make(f, mask, H, W, conn, kind);
     int N = H * W, nb[8];
     int *comp = (int *)malloc((size_t)N * sizeof(int));
     int *csize = (int *)malloc((size_t)N * sizeof(int));
@@ -437,7 +460,7 @@ int or_rings(const uint8_t *mask, int kind, int H, int W, int32_t *ring, int32_t
 int or_fill(const uint8_t *f, const uint8_t *mask, int H, int W, int conn, int kind,
             int order, int B, uint64_t seed, uint64_t *stats, int32_t *seq_out,
             uint64_t *round_new, uint32_t *D_out) {
-    or_graph g = {f, mask, H, W, conn, kind};
+    or_graph g = or_make(f, mask, H, W, conn, kind);
     int N = H * W;
     size_t words = ((size_t)N * N + 63) / 64;
     uint64_t *mrk = (uint64_t *)calloc(words, sizeof(uint64_t));

@@ -19,7 +19,7 @@ from . import _build
 
 UNREACH = 0xFFFFFFFF
 ORDERS = {"naive": 0, "spiral": 1, "minfill": 2, "extrema": 3, "repulsion": 4}
-KINDS = {"grey": 0, "mask": 1, "l1": 2}
+KINDS = {"grey": 0, "mask": 1, "l1": 2, "sum": 3}
 KERNELS = ("select", "propagate", "tree", "lookahead", "fill", "init", "prepass", "depths", "recount")
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "memory budget exceeded",
           4: "CUDA runtime error", 5: "propagation did not converge", 6: "round limit exceeded",
@@ -31,7 +31,11 @@ _lib = None
 class GapspError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
-        super().__init__(f"{where}: {STATUS.get(code, code)} (status {code})")
+        detail = ""
+        if code in (2, 4) and _lib is not None:
+            d = _lib.gapsp_last_error_detail()
+            detail = f" [{d.decode(errors='replace')}]" if d else ""
+        super().__init__(f"{where}: {STATUS.get(code, code)} (status {code}){detail}")
 
 
 class Opts(ctypes.Structure):
@@ -101,6 +105,9 @@ def load(build_if_missing: bool = True):
     lib.gapsp_create.argtypes = [P, ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(Opts),
                                  ctypes.POINTER(P)]
     lib.gapsp_create.restype = ctypes.c_int
+    lib.gapsp_create_channels.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Opts),
+                                          ctypes.POINTER(P)]
+    lib.gapsp_create_channels.restype = ctypes.c_int
     lib.gapsp_all_pairs.argtypes = [P, ctypes.c_int, P, ctypes.POINTER(Stats)]
     lib.gapsp_all_pairs.restype = ctypes.c_int
     lib.gapsp_rows.argtypes = [P, P, ctypes.c_int, P]
@@ -143,6 +150,8 @@ def load(build_if_missing: bool = True):
     lib.gapsp_tune.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Opts), ctypes.c_int,
                                ctypes.c_char_p, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_double)]
     lib.gapsp_tune.restype = ctypes.c_int
+    lib.gapsp_last_error_detail.argtypes = []
+    lib.gapsp_last_error_detail.restype = ctypes.c_char_p
     lib.gapsp_cancel.argtypes = [P]
     lib.gapsp_cancel.restype = ctypes.c_int
     lib.gapsp_debug_fail_alloc.argtypes = [ctypes.c_int]
@@ -271,7 +280,11 @@ def rows_noalloc(img, sources, out, conn: int = 8, kind: str = "grey", stream=No
 
 
 class Image:
-    """A handle on one image (gapsp_create / gapsp_destroy)."""
+    """A handle on one image (gapsp_create / gapsp_destroy).
+
+    kind "grey", "l1": img is H x W grey levels; "mask": mask is H x W free
+    flags; "sum": img is L x H x W, a multichannel image whose channels' sum
+    pseudo-metric weighs the edges (gapsp_create_channels)."""
 
     def __init__(self, img, conn: int = 8, kind: str = "grey", mask=None, B: int = 32,
                  seed: int = 0, mem_budget: int = 0, stream=None, sweep_phases: int = 0,
@@ -280,7 +293,12 @@ class Image:
         lib = load()
         self._lib = lib
         self._h = ctypes.c_void_p()
-        if kind != "mask":
+        if kind == "sum":
+            img_a = img if hasattr(img, "data_ptr") else np.ascontiguousarray(img, dtype=np.uint8)
+            if len(img_a.shape) != 3:
+                raise ValueError("the sum kind takes an L x H x W image")
+            L, H, W = (int(x) for x in img_a.shape)
+        elif kind != "mask":
             img_a = img if hasattr(img, "data_ptr") else np.ascontiguousarray(img, dtype=np.uint8)
             H, W = int(img_a.shape[0]), int(img_a.shape[1])
         else:
@@ -305,7 +323,10 @@ class Image:
         o.max_rounds = max_rounds
         o.stream = _torch_stream(stream)
         self.H, self.W, self.N, self.conn, self.kind, self.B = H, W, H * W, conn, kind, B
-        rc = lib.gapsp_create(_ptr(img_a), H, W, _ptr(mask_a), ctypes.byref(o), ctypes.byref(self._h))
+        if kind == "sum":
+            rc = lib.gapsp_create_channels(_ptr(img_a), L, H, W, ctypes.byref(o), ctypes.byref(self._h))
+        else:
+            rc = lib.gapsp_create(_ptr(img_a), H, W, _ptr(mask_a), ctypes.byref(o), ctypes.byref(self._h))
         if rc != 0:
             self._h = ctypes.c_void_p()
             raise GapspError(rc, "gapsp_create")

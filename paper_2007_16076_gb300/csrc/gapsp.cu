@@ -107,11 +107,20 @@ void keep_pool_warm() {
     });
 }
 
+// The last failing CUDA runtime call of this host thread, for
+// gapsp_last_error_detail.
+thread_local char t_detail[256] = "";
+
+void note_cuda_error(cudaError_t e, const char* call, int line) {
+    std::snprintf(t_detail, sizeof t_detail, "gapsp.cu:%d: %s: %s", line, call, cudaGetErrorString(e));
+}
+
 #define CK(x)                                                  \
     do {                                                       \
         cudaError_t e_ = (x);                                  \
         if (e_ != cudaSuccess) {                               \
             cudaGetLastError();                                \
+            note_cuda_error(e_, #x, __LINE__);                 \
             return e_ == cudaErrorMemoryAllocation ? GAPSP_E_NOMEM : GAPSP_E_CUDA; \
         }                                                      \
     } while (0)
@@ -188,6 +197,7 @@ PropArgs base_prop(const gapsp_handle* h) {
     a.N = h->N;
     a.conn = h->conn;
     a.kind_mask = h->kind == GAPSP_MASK;
+    a.level_bytes = h->kind == GAPSP_SUM ? 2 : 1;
     a.f = h->f;
     a.status = h->status;
     a.max_sweeps = 4 * (h->max_sweep_rounds ? h->max_sweep_rounds : h->N + 2);
@@ -362,18 +372,31 @@ const char* gapsp_strerror(gapsp_status s) {
 
 uint64_t gapsp_kernel_launches(const gapsp_handle* h) { return h ? h->launches : 0; }
 
-gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask, const gapsp_opts* opts,
-                          gapsp_handle** out) {
+}  // extern "C"
+
+// gapsp_create and gapsp_create_channels: `img` holds L channel planes when
+// L > 0 (the GAPSP_SUM kind), else one plane of grey levels or free flags.
+static gapsp_status create_handle(const uint8_t* img, int L, int H, int W, const uint8_t* mask,
+                                  const gapsp_opts* opts, gapsp_handle** out) {
     if (!out) return GAPSP_E_INVALID;
     *out = nullptr;
     gapsp_opts o;
     gapsp_default_opts(&o);
     if (opts) o = *opts;
+    if (L > 0) {
+        o.kind = GAPSP_SUM;
+        if (L > GAPSP_MAX_CHANNELS) return GAPSP_E_INVALID;
+        // every distance must stay below the sweeps' "unreached" sentinel
+        if ((long long)(H * W - 1) * (510LL * L + 1) >= (1LL << 30) - (1LL << 18)) return GAPSP_E_INVALID;
+    } else if (o.kind == GAPSP_SUM) {
+        return GAPSP_E_INVALID;  // needs the channels (gapsp_create_channels)
+    }
     if (o.conn == 0) o.conn = 8;
     if (o.B == 0) o.B = 32;
     if (H < 1 || W < 1 || H > GAPSP_MAX_SIDE || W > GAPSP_MAX_SIDE || H * W > GAPSP_MAX_N) return GAPSP_E_INVALID;
     if (o.conn != 4 && o.conn != 8) return GAPSP_E_INVALID;
-    if (o.kind != GAPSP_GREY && o.kind != GAPSP_MASK && o.kind != GAPSP_L1) return GAPSP_E_INVALID;
+    if (o.kind != GAPSP_GREY && o.kind != GAPSP_MASK && o.kind != GAPSP_L1 && o.kind != GAPSP_SUM)
+        return GAPSP_E_INVALID;
     if (o.B < 1 || o.B > 1024) return GAPSP_E_INVALID;
     if (o.sweep_phases < 0 || o.sweep_phases > 4 || o.sweep_phases == 3) return GAPSP_E_INVALID;
     if (o.fill_rows < 0 || o.fill_rows > 32) return GAPSP_E_INVALID;
@@ -416,7 +439,8 @@ gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask,
     };
     keep_pool_warm();
     cudaError_t e;
-    if ((e = dalloc(&h->f, N, h->st)) != cudaSuccess) return fail(e);
+    // levels: one byte per pixel, two for the channel sum
+    if ((e = dalloc(&h->f, L > 0 ? 2 * N : N, h->st)) != cudaSuccess) return fail(e);
     if ((e = dalloc(&h->pgeo, N, h->st)) != cudaSuccess) return fail(e);
     if ((e = dalloc(&h->tbase, (size_t)h->words, h->st)) != cudaSuccess) return fail(e);
     if ((e = dalloc(&h->bound, N, h->st)) != cudaSuccess) return fail(e);
@@ -426,7 +450,18 @@ gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask,
     if ((e = cudaEventCreate(&h->ev1)) != cudaSuccess) return fail(e);
     // the kernels read grey levels (grey) or free flags (mask) from h->f
     const uint8_t* srcimg = o.kind == GAPSP_MASK ? mask : img;
-    if ((e = cudaMemcpyAsync(h->f, srcimg, N, cudaMemcpyDefault, h->st)) != cudaSuccess) return fail(e);
+    if (L > 0) {
+        // F = sum of the channels, in 16-bit levels
+        uint8_t* planes = nullptr;
+        if ((e = dalloc(&planes, (size_t)L * N, h->st)) != cudaSuccess) return fail(e);
+        e = cudaMemcpyAsync(planes, img, (size_t)L * N, cudaMemcpyDefault, h->st);
+        if (e == cudaSuccess) e = launch_channel_sum(planes, L, (int)N, reinterpret_cast<uint16_t*>(h->f), h->st);
+        dfree(planes, h->st);
+        if (e != cudaSuccess) return fail(e);
+        h->launches += 1;
+    } else if ((e = cudaMemcpyAsync(h->f, srcimg, N, cudaMemcpyDefault, h->st)) != cudaSuccess) {
+        return fail(e);
+    }
     if ((e = cudaMemsetAsync(h->status, 0, sizeof(int), h->st)) != cudaSuccess) return fail(e);
     if (o.kind == GAPSP_MASK) {
         // normalise the flags to 0/1
@@ -459,6 +494,20 @@ gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask,
     }
     *out = h;
     return GAPSP_OK;
+}
+
+extern "C" {
+
+gapsp_status gapsp_create(const uint8_t* img, int H, int W, const uint8_t* mask, const gapsp_opts* opts,
+                          gapsp_handle** out) {
+    return create_handle(img, 0, H, W, mask, opts, out);
+}
+
+gapsp_status gapsp_create_channels(const uint8_t* planes, int L, int H, int W, const gapsp_opts* opts,
+                                   gapsp_handle** out) {
+    if (out) *out = nullptr;
+    if (L < 1 || !planes) return GAPSP_E_INVALID;
+    return create_handle(planes, L, H, W, nullptr, opts, out);
 }
 
 void gapsp_destroy(gapsp_handle* h) {
@@ -875,11 +924,13 @@ gapsp_status fill_finish(FillRun& r, gapsp_stats* st) {
     gapsp_handle* h = r.h;
     cudaStream_t s = r.s;
     const size_t N = h->N;
-    if (r.K > 0) {
+    // (a fill that ran as a graph joined its side streams inside every
+    // chunk; its events were recorded in the capture only)
+    if (r.K > 0 && !r.graphed) {
         CK(cudaStreamWaitEvent(s, r.e_ahead[0], 0));
         CK(cudaStreamWaitEvent(s, r.e_ahead[1], 0));
     }
-    if (r.stat) {
+    if (r.stat && !r.graphed) {
         CK(cudaStreamWaitEvent(s, r.e_depth[0], 0));
         CK(cudaStreamWaitEvent(s, r.e_depth[1], 0));
     }
@@ -1022,6 +1073,7 @@ struct BatchGraph {
         for (int i = 0; i < n && gs == GAPSP_OK; ++i) gs = fill_begin(runs[i]);
         for (int i = 0; i < n && gs == GAPSP_OK; ++i) {
             const uint64_t l0 = hs[i]->launches;
+            runs[i].graphed = true;
             cudaError_t e = cudaStreamBeginCapture(ws[i], cudaStreamCaptureModeRelaxed);
             if (e == cudaSuccess) {
                 gs = fill_enqueue(runs[i], kChunk, true);
@@ -1123,6 +1175,8 @@ gapsp_status gapsp_all_pairs(gapsp_handle* h, gapsp_order order, uint32_t* D, ga
     if (gs != GAPSP_OK) fill_drain(r);
     return gs;
 }
+
+const char* gapsp_last_error_detail(void) { return t_detail; }
 
 gapsp_status gapsp_cancel(gapsp_handle* h) {
     if (!h) return GAPSP_E_INVALID;

@@ -48,7 +48,8 @@ struct PropArgs {
     const int* njobs_dev;       // device-side job count (NULL: use njobs)
     int njobs;
     int H, W, N, conn, kind_mask;
-    const uint8_t* f;           // grey levels (grey) or free flags (mask)
+    int level_bytes;            // bytes per level: 1, or 2 for the channel sum (GAPSP_SUM)
+    const uint8_t* f;           // levels (uint8, or uint16 for GAPSP_SUM) or free flags (mask)
     int* status;                // device status word (ST_* bits)
     unsigned long long* sweeps; // optional: total sweeps run
     int max_sweeps;
@@ -209,5 +210,7 @@ struct CompArgs {
 cudaError_t launch_components(const CompArgs& a, cudaStream_t st);
 
 cudaError_t launch_unreach_convert(uint32_t* rows, size_t n, cudaStream_t st);
+// F(p) = sum over the L channels (planes of N bytes) of the levels of p.
+cudaError_t launch_channel_sum(const uint8_t* planes, int L, int N, uint16_t* F, cudaStream_t st);
 
 }  // namespace gapsp

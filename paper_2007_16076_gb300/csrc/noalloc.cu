@@ -103,6 +103,7 @@ extern "C" gapsp_status gapsp_rows_noalloc(const uint8_t* img, int H, int W, int
     a.N = N;
     a.conn = conn;
     a.kind_mask = kind == GAPSP_MASK;
+    a.level_bytes = 1;
     a.f = img;
     a.status = dstatus;
     a.max_sweeps = 4 * (N + 2);

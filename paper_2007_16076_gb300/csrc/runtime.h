@@ -149,6 +149,7 @@ struct FillRun {
     TreeArgs ta{};
     int rounds = 0;
     bool finished = false;
+    bool graphed = false;  // its chunks run as a captured graph (gapsp_all_pairs_batch)
     // lookahead: the next K candidates of each round are propagated on a
     // second stream while the round's tree and fill run
     int K = 0;

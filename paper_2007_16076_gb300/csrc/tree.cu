@@ -46,19 +46,22 @@ __device__ __forceinline__ uint32_t tile_bit(const TreeArgs& a, int p) {
 // Canonical parent of b in the tree of s (-1 for the root and unreached):
 // the first neighbour q in increasing index with d(s,q) + w(q,b) = d(s,b).
 // fs: the grey levels (grey) or free flags (mask), in shared or global memory.
-__device__ __forceinline__ int canonical_parent(const TreeArgs& a, const uint32_t* drow, const uint8_t* fs, int s,
+template <class Lv>
+__device__ __forceinline__ int canonical_parent(const TreeArgs& a, const uint32_t* drow, const Lv* fs, int s,
                                                 int b) {
     const uint32_t db = drow[b];
     if (b == s || db == UNREACH) return -1;
     const int W = a.W;
     const int r = row_of(a, b), c = b - r * W;
     const int f_b = fs[b];
-    // w(q,b): f(q) + f(b) + 1 (sum), |f(q) - f(b)| + 1 (L1), 2 (mask)
+    // w(q,b): f(q) + f(b) + 1 (sum, of grey levels or of channels), |f(q) - f(b)| + 1 (L1), 2 (mask)
     auto tight = [&](int q) {
         if (a.kind == 1 && !fs[q]) return false;
         const uint32_t dq = drow[q];
         const int fq = fs[q];
-        const uint32_t w = a.kind == 0 ? (uint32_t)(fq + f_b + 1) : a.kind == 2 ? (uint32_t)(abs(fq - f_b) + 1) : 2u;
+        const uint32_t w = (a.kind == 0 || a.kind == 3) ? (uint32_t)(fq + f_b + 1)
+                           : a.kind == 2                 ? (uint32_t)(abs(fq - f_b) + 1)
+                                                         : 2u;
         return dq != UNREACH && dq + w == db;
     };
     if (r > 0 && r + 1 < a.H && c > 0 && c + 1 < W) {
@@ -100,6 +103,25 @@ __device__ __forceinline__ int canonical_parent(const TreeArgs& a, const uint32_
 //     summed along the segment chain by pointer jumping. When N <= 16384
 //     (SMALL) the parents and the jumping arrays are 16-bit shared arrays;
 //     otherwise they live in global scratch.
+// Canonical parent with the staged levels `sf` (8-bit, or 16-bit for the
+// channel sum): sf points at pixel 0 of the staged range's coordinates.
+__device__ __forceinline__ int parent_of(const TreeArgs& a, const uint32_t* drow, const void* sf, int s, int b) {
+    return a.kind == 3 ? canonical_parent(a, drow, static_cast<const uint16_t*>(sf), s, b)
+                       : canonical_parent(a, drow, static_cast<const uint8_t*>(sf), s, b);
+}
+
+// Stages levels [base, base + S) of the image into sf (same width).
+__device__ __forceinline__ void stage_levels(const TreeArgs& a, void* sf, int base, int S) {
+    if (a.kind == 3) {
+        const uint16_t* f = reinterpret_cast<const uint16_t*>(a.f);
+        for (int v = threadIdx.x; v < S; v += blockDim.x) static_cast<uint16_t*>(sf)[v] = f[base + v];
+    } else {
+        for (int v = threadIdx.x; v < S; v += blockDim.x) static_cast<uint8_t*>(sf)[v] = a.f[base + v];
+    }
+}
+
+__host__ __device__ inline int level_bytes(int kind) { return kind == 3 ? 2 : 1; }
+
 template <bool SMALL>
 __global__ void __launch_bounds__(1024) k_tree(TreeArgs a) {
     extern __shared__ uint16_t sdep[];
@@ -121,25 +143,23 @@ __global__ void __launch_bounds__(1024) k_tree(TreeArgs a) {
     if (SMALL) {
         uint32_t* srow = reinterpret_cast<uint32_t*>(sdep);
         uint8_t* sf = reinterpret_cast<uint8_t*>(sdep + 5 * N);
-        if ((N & 15) == 0) {
+        if ((N & 15) == 0 && a.kind != 3) {
             // 16-byte loads: the row starts at s * N * 4 bytes, the image at 0
             for (int v = 4 * threadIdx.x; v < N; v += 4 * blockDim.x)
                 *reinterpret_cast<uint4*>(srow + v) = __ldcg(reinterpret_cast<const uint4*>(drow + v));
             for (int v = 16 * threadIdx.x; v < N; v += 16 * blockDim.x)
                 *reinterpret_cast<uint4*>(sf + v) = __ldg(reinterpret_cast<const uint4*>(a.f + v));
         } else {
-            for (int v = threadIdx.x; v < N; v += blockDim.x) {
-                srow[v] = __ldcg(drow + v);
-                sf[v] = a.f[v];
-            }
+            for (int v = threadIdx.x; v < N; v += blockDim.x) srow[v] = __ldcg(drow + v);
+            stage_levels(a, sf, 0, N);
         }
         __syncthreads();
         for (int b = threadIdx.x; b < N; b += blockDim.x) {
-            const int pb = canonical_parent(a, srow, sf, s, b);
+            const int pb = parent_of(a, srow, sf, s, b);
             spar[b] = srow[b] == UNREACH ? (uint16_t)0xFFFF : (uint16_t)(pb + 1);
         }
     } else {
-        for (int b = threadIdx.x; b < N; b += blockDim.x) par[b] = canonical_parent(a, drow, a.f, s, b);
+        for (int b = threadIdx.x; b < N; b += blockDim.x) par[b] = parent_of(a, drow, a.f, s, b);
     }
     __syncthreads();
     for (int v = threadIdx.x; v < N; v += blockDim.x) {
@@ -248,12 +268,14 @@ __global__ void __launch_bounds__(1024) k_tree(TreeArgs a) {
 // as k_tree.
 struct TreeCLayout {
     int hs, smax, pmax;  // rows per strip (the last may be shorter or empty); staged, owned pixels
-    __host__ __device__ TreeCLayout(int H, int W, int C) {
+    size_t o_par;        // byte offset of the parents (after the staged row and levels)
+    __host__ __device__ TreeCLayout(int H, int W, int C, int lvb) {
         hs = (((H + C - 1) / C + 7) / 8) * 8;
         smax = (hs + 2) * W;
         pmax = hs * W;
+        o_par = ((size_t)smax * (4 + lvb) + 15) & ~(size_t)15;
     }
-    __host__ __device__ size_t bytes() const { return (size_t)smax * 5 + (size_t)pmax * 6 + 16; }
+    __host__ __device__ size_t bytes() const { return o_par + (size_t)pmax * 6 + 16; }
 };
 
 template <int C>
@@ -267,29 +289,27 @@ __global__ void __launch_bounds__(1024) k_treeC(TreeArgs a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *a.dep_count = *a.nsel;
     if (j >= *a.nsel) return;  // all blocks of the cluster leave together
     const int N = a.N, W = a.W, H = a.H, s = a.sel[j];
-    const TreeCLayout L(H, W, C);
+    const TreeCLayout L(H, W, C, level_bytes(a.kind));
     const int r0 = min(rank * L.hs, H), r1 = min(r0 + L.hs, H);
     const int hr0 = r0 > 0 ? r0 - 1 : 0, hr1 = r1 < H ? r1 + 1 : H;
     const int base = hr0 * W, S = r1 > r0 ? (hr1 - hr0) * W : 0;  // staged pixels [base, base + S)
     const int p0 = r0 * W, P = (r1 - r0) * W;                     // owned pixels [p0, p0 + P)
     uint32_t* srow = reinterpret_cast<uint32_t*>(smc);
     uint8_t* sf = smc + (size_t)L.smax * 4;
-    uint16_t* spar = reinterpret_cast<uint16_t*>(smc + (((size_t)L.smax * 5 + 15) & ~(size_t)15));
+    uint16_t* spar = reinterpret_cast<uint16_t*>(smc + L.o_par);
     uint16_t* acc = spar + L.pmax;
     uint16_t* jx = acc + L.pmax;
     const uint32_t* drow = a.D + (size_t)s * N;
     ulonglong2* seg = a.seg + (size_t)j * N;
-    for (int v = threadIdx.x; v < S; v += blockDim.x) {
-        srow[v] = __ldcg(drow + base + v);
-        sf[v] = a.f[base + v];
-    }
+    for (int v = threadIdx.x; v < S; v += blockDim.x) srow[v] = __ldcg(drow + base + v);
+    stage_levels(a, sf, base, S);
     __syncthreads();
     // parents of the owned pixels (neighbours within the staged rows)
     const uint32_t* drow_l = srow - base;
-    const uint8_t* sf_l = sf - base;
+    const void* sf_l = sf - (size_t)base * level_bytes(a.kind);
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         const int b = p0 + i;
-        const int pb = canonical_parent(a, drow_l, sf_l, s, b);
+        const int pb = parent_of(a, drow_l, sf_l, s, b);
         spar[i] = drow_l[b] == UNREACH ? (uint16_t)0xFFFF : (uint16_t)(pb + 1);
     }
     __syncthreads();
@@ -345,11 +365,11 @@ __global__ void __launch_bounds__(1024) k_treeC(TreeArgs a) {
 struct TreeWLayout {
     int hs, smax, pmax;
     size_t o_par;  // byte offset of the parents
-    __host__ __device__ TreeWLayout(int H, int W, int C) {
+    __host__ __device__ TreeWLayout(int H, int W, int C, int lvb) {
         hs = (((H + C - 1) / C + 7) / 8) * 8;
         smax = (hs + 2) * W;
         pmax = hs * W;
-        o_par = ((size_t)smax * 5 + 15) & ~(size_t)15;
+        o_par = ((size_t)smax * (4 + lvb) + 15) & ~(size_t)15;
     }
     __host__ __device__ size_t bytes() const { return o_par + (size_t)pmax * 12 + 16; }
 };
@@ -365,7 +385,7 @@ __global__ void __launch_bounds__(1024) k_treeW(TreeArgs a) {
     const int j = blockIdx.x / C;
     if (j >= *a.nsel) return;  // all blocks of the cluster leave together
     const int N = a.N, W = a.W, H = a.H, s = a.sel[j];
-    const TreeWLayout L(H, W, C);
+    const TreeWLayout L(H, W, C, level_bytes(a.kind));
     const int r0 = min(rank * L.hs, H), r1 = min(r0 + L.hs, H);
     const int hr0 = r0 > 0 ? r0 - 1 : 0, hr1 = r1 < H ? r1 + 1 : H;
     const int base = hr0 * W, S = r1 > r0 ? (hr1 - hr0) * W : 0;  // staged pixels [base, base + S)
@@ -381,18 +401,16 @@ __global__ void __launch_bounds__(1024) k_treeW(TreeArgs a) {
     const uint32_t* drow = a.D + (size_t)s * N;
     ulonglong2* seg = a.seg + (size_t)j * N;
     if (threadIdx.x == 0) { s_more[0] = 0; s_more[1] = 0; }
-    for (int v = threadIdx.x; v < S; v += blockDim.x) {
-        srow[v] = __ldcg(drow + base + v);
-        sf[v] = a.f[base + v];
-    }
+    for (int v = threadIdx.x; v < S; v += blockDim.x) srow[v] = __ldcg(drow + base + v);
+    stage_levels(a, sf, base, S);
     __syncthreads();
     // parents of the owned pixels (neighbours within the staged rows); parent
     // + 1, 0 for the root, all ones for unreached pixels
     const uint32_t* drow_l = srow - base;
-    const uint8_t* sf_l = sf - base;
+    const void* sf_l = sf - (size_t)base * level_bytes(a.kind);
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         const int b = p0 + i;
-        const int pb = canonical_parent(a, drow_l, sf_l, s, b);
+        const int pb = parent_of(a, drow_l, sf_l, s, b);
         spar[i] = drow_l[b] == UNREACH ? 0xFFFFFFFFu : (uint32_t)(pb + 1);
     }
     __syncthreads();
@@ -731,7 +749,10 @@ __global__ void __launch_bounds__(128, FILL_G_MINB) k_fill_g(TreeArgs a, int qua
                 if (ap[k] < 0) continue;
                 const uint32_t val = db - dv[k];
                 atomicOr(a.marks + (uint32_t)ap[k] * (uint32_t)a.words + tb, bbit);
-                a.dirty[ap[k]] = 1;
+                // most rows are flagged already: a read (which may be stale,
+                // costing one redundant store) spares the flag array, 1 byte
+                // per row, millions of stores to the same few lines
+                if (!a.dirty[ap[k]]) a.dirty[ap[k]] = 1;
                 __stcs(a.Dw + (uint32_t)ap[k] * (uint32_t)a.N + b, val);
                 __stcs(a.Dw + brow + ap[k], val);
             }
@@ -834,14 +855,14 @@ cudaError_t launch_tree(const TreeArgs& a, int B, cudaStream_t st, bool pdl) {
         // several blocks (one cluster) per tree: four strips when they are
         // 16 rows or more, else two
         if (a.H >= 64) {
-            const TreeCLayout L(a.H, a.W, 4);
+            const TreeCLayout L(a.H, a.W, 4, level_bytes(a.kind));
             static std::atomic<unsigned long long> attr4{0};
             once_per_device(attr4, [] {
                 cudaFuncSetAttribute(k_treeC<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
             });
             return launch_ex(k_treeC<4>, 4 * B, 1024, L.bytes(), st, pdl, 4, a);
         }
-        const TreeCLayout L(a.H, a.W, 2);
+        const TreeCLayout L(a.H, a.W, 2, level_bytes(a.kind));
         static std::atomic<unsigned long long> attr2{0};
         once_per_device(attr2, [] {
             cudaFuncSetAttribute(k_treeC<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -851,15 +872,15 @@ cudaError_t launch_tree(const TreeArgs& a, int B, cudaStream_t st, bool pdl) {
     if (a.N <= 16384) {
         static std::atomic<unsigned long long> attr{0};
         once_per_device(attr, [] {
-            cudaFuncSetAttribute(k_tree<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 11);
+            cudaFuncSetAttribute(k_tree<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 12);
         });
         // five 16-bit arrays and the image
-        return launch_ex(k_tree<true>, B, 1024, (size_t)a.N * 11, st, pdl, 1, a);
+        return launch_ex(k_tree<true>, B, 1024, (size_t)a.N * (10 + level_bytes(a.kind)), st, pdl, 1, a);
     }
     if (a.H >= 64) {
         // N > 16384 (so H > 64): eight strips of whole tiles, when a cluster
         // of eight such blocks can be resident at all
-        const TreeWLayout L(a.H, a.W, 8);
+        const TreeWLayout L(a.H, a.W, 8, level_bytes(a.kind));
         static std::atomic<unsigned long long> attr8{0};
         once_per_device(attr8, [] {
             cudaFuncSetAttribute(k_treeW<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

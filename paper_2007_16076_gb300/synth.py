@@ -169,6 +169,14 @@ def steps_256(seed: int = 0) -> Workload:
     return Workload("steps-256x256-8conn-B32", img, 8, B=32, meta={"seed": seed})
 
 
+def steps_160(seed: int = 0) -> Workload:
+    """The 256x256 step-edge image's generator at 160x160 (blob count and
+    sigma scaled with the area and the side, 20 step edges): a smaller case
+    of the same structure, for profiling."""
+    img = blobs_with_steps(160, 160, 25, 10.0, 20, 100.0, 40.0, seed)
+    return Workload("steps-160x160-8conn-B32", img, 8, B=32, meta={"seed": seed})
+
+
 def mask_256(seed: int = 0) -> Workload:
     """256x256 obstacle disks (radius 3-12, 40% coverage), w=2, 8-connected."""
     m = disk_mask(256, 256, 0.40, 3, 12, seed)

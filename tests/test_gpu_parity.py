@@ -500,7 +500,71 @@ def test_tune_picks_a_candidate_and_caches(gp, tmp_path):
     lines = cache.read_text().splitlines()
     assert len(lines) == 1 and lines[0].startswith("gapsp-tune-1 40 44 8 0 2 ")
     t2 = gp.tune(img, conn=8, cache=cache)
-    assert t2 == t and len(cache.read_text().splitlines()) == 1
+    keys = ("B", "lookahead", "fill_rows")
+    assert {k: t2[k] for k in keys} == {k: t[k] for k in keys} and abs(t2["ms"] - t["ms"]) < 1e-3
+    assert len(cache.read_text().splitlines()) == 1
     with gp.Image(img, conn=8, B=t["B"], lookahead=t["lookahead"], fill_rows=t["fill_rows"]) as im:
         D, _ = im.all_pairs("minfill")
     assert np.array_equal(_u32(D), oracle.apsp(img, conn=8))
+
+
+# --------------------------------------------------------------------------
+# Multichannel images: the sum pseudo-metric over L channels (16-bit levels)
+# --------------------------------------------------------------------------
+
+def _channels(L, H, W, seed):
+    return np.stack([synth.blobs(H, W, max(1, H * W // 300), max(1.5, (H + W) / 16), 55.0, seed=seed + l)
+                     for l in range(L)])
+
+
+@pytest.mark.parametrize("shape,L", [((7, 13), 2), ((64, 64), 3), ((129, 130), 8), ((256, 256), 5)],
+                         ids=lambda x: str(x))
+@pytest.mark.parametrize("conn", [4, 8])
+def test_rows_channels(gp, shape, L, conn):
+    H, W = shape
+    ch = _channels(L, H, W, seed=H + W)
+    N = H * W
+    rng = np.random.default_rng(N)
+    src = np.unique(np.concatenate([[0, N - 1], rng.integers(0, N, size=12)])).astype(np.int32)
+    with gp.Image(ch, conn=conn, kind="sum") as im:
+        out = _u32(im.rows(src))
+    assert np.array_equal(out, oracle.rows(ch, src, conn=conn, kind="sum"))
+
+
+@pytest.mark.parametrize("order", ["naive", "spiral", "repulsion", "extrema", "minfill"])
+@pytest.mark.parametrize("conn", [4, 8])
+def test_all_pairs_channels(gp, order, conn):
+    ch = _channels(3, 19, 23, seed=conn)
+    with gp.Image(ch, conn=conn, kind="sum", B=5, seed=3) as im:
+        D, st = im.all_pairs(order, want_log=True)
+    assert np.array_equal(_u32(D), oracle.apsp(ch, conn=conn, kind="sum"))
+    ref = oracle.fill(ch, order, B=5, seed=3, conn=conn, kind="sum")
+    for k in ("propagations", "prepass_propagations", "distance_ops", "new_pairs", "rounds"):
+        assert st[k] == getattr(ref, k), k
+    assert st["sources"].tolist() == ref.sources.tolist()
+
+
+def test_channels_whole_array_136x121(gp):
+    """Above 16384 pixels (eight-strip trees, 16-bit levels staged there too)."""
+    ch = _channels(4, 136, 121, seed=9)
+    with gp.Image(ch, conn=8, kind="sum", B=32) as im:
+        D, _ = im.all_pairs("minfill")
+    assert np.array_equal(_u32(D), oracle.apsp(ch, conn=8, kind="sum"))
+
+
+def test_channels_largest_levels(gp):
+    """32 channels at 255 (F = 8160, the largest distances the kernels take):
+    constant image, so d = (2 * 8160 + 1) x chessboard steps; and 33
+    channels are refused."""
+    H, W = 64, 256
+    ch = np.full((32, H, W), 255, dtype=np.uint8)
+    src = np.array([0, W - 1, H * W - 1, (H // 2) * W + 7], dtype=np.int32)
+    with gp.Image(ch, conn=8, kind="sum") as im:
+        out = _u32(im.rows(src))
+    r, c = np.divmod(np.arange(H * W), W)
+    for k, s in enumerate(src):
+        steps = np.maximum(np.abs(r - s // W), np.abs(c - s % W))
+        assert np.array_equal(out[k], (2 * 8160 + 1) * steps)
+    with pytest.raises(gp.GapspError) as e:
+        gp.Image(np.zeros((33, 8, 8), np.uint8), conn=8, kind="sum")
+    assert e.value.code == 1

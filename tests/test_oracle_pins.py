@@ -134,6 +134,90 @@ def test_l1_brute_force_paths(shape, conn):
         assert np.array_equal(oracle.apsp(img, conn=conn, kind="l1"), _brute_force_l1(img, conn))
 
 
+# --------------------------------------------------------------------------
+# Multichannel images (Sec. 2: values in T^L), sum pseudo-metric over the
+# channels: w(p,q) = sum_l (f_l(p) + f_l(q)) + 1
+# --------------------------------------------------------------------------
+
+def _brute_force_channels(ch, conn):
+    """Minimum over all simple paths of the channel-summed weights, each
+    weight added up channel by channel."""
+    L, H, W = ch.shape
+    N = H * W
+    f = ch.reshape(L, -1).astype(np.int64)
+    D = np.full((N, N), U, dtype=np.uint64)
+    for s in range(N):
+        D[s, s] = 0
+        stack = [(s, 0, 1 << s)]
+        while stack:
+            v, cost, seen = stack.pop()
+            for q in _nbrs(H, W, conn, v):
+                if seen >> q & 1:
+                    continue
+                c2 = cost + 1 + sum(int(f[l, v] + f[l, q]) for l in range(L))
+                if c2 < D[s, q]:
+                    D[s, q] = c2
+                stack.append((q, c2, seen | (1 << q)))
+    return D.astype(np.uint32)
+
+
+@pytest.mark.parametrize("shape", [(2, 3), (3, 3)])
+@pytest.mark.parametrize("conn", [4, 8])
+@pytest.mark.parametrize("L", [2, 3])
+def test_channels_brute_force_paths(shape, conn, L):
+    rng = np.random.default_rng(17 + shape[0] * 10 + shape[1] + conn + L)
+    for _ in range(2):
+        ch = rng.integers(0, 256, size=(L,) + shape).astype(np.uint8)
+        assert np.array_equal(oracle.apsp(ch, conn=conn, kind="sum"), _brute_force_channels(ch, conn))
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_channels_one_channel_is_grey(conn):
+    """With one channel the channel sum is the grey sum pseudo-metric."""
+    img = synth.blobs(13, 17, 3, 3.0, 55.0, seed=conn)
+    assert np.array_equal(oracle.apsp(img[None], conn=conn, kind="sum"), oracle.apsp(img, conn=conn))
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_channels_constant_closed_form(conn):
+    """Constant channels c_l: every edge costs 2 sum(c) + 1, so d is that
+    times the chessboard (8) or city-block (4) step count."""
+    c = np.array([3, 0, 250, 17], dtype=np.uint8)
+    H, W = 6, 9
+    ch = np.broadcast_to(c[:, None, None], (4, H, W)).copy()
+    D = oracle.apsp(ch, conn=conn, kind="sum")
+    r, col = np.divmod(np.arange(H * W), W)
+    dr = np.abs(r[:, None] - r[None, :])
+    dc = np.abs(col[:, None] - col[None, :])
+    steps = np.maximum(dr, dc) if conn == 8 else dr + dc
+    assert np.array_equal(D, (2 * int(c.sum()) + 1) * steps)
+
+
+@pytest.mark.parametrize("W", [2, 9, 31])
+def test_channels_one_row_closed_form(W):
+    """1 x W (eq. 'distance geo somme' over the channel sums F): d(i,j) =
+    F(i) + F(j) + 2 sum_{i<k<j} F(k) + |j - i|."""
+    rng = np.random.default_rng(W)
+    ch = rng.integers(0, 256, size=(3, 1, W)).astype(np.uint8)
+    F = ch.astype(np.int64).sum(axis=0)[0]
+    D = oracle.apsp(ch, conn=8, kind="sum")
+    for i in range(W):
+        for j in range(W):
+            lo, hi = min(i, j), max(i, j)
+            want = 0 if i == j else F[i] + F[j] + 2 * F[lo + 1:hi].sum() + (hi - lo)
+            assert D[i, j] == want
+
+
+def test_channels_floyd_warshall_and_fill():
+    rng = np.random.default_rng(5)
+    ch = rng.integers(0, 256, size=(5, 7, 8)).astype(np.uint8)
+    D = oracle.apsp(ch, conn=8, kind="sum")
+    assert np.array_equal(D, oracle.floyd(ch, conn=8, kind="sum"))
+    r = oracle.fill(ch, "minfill", B=3, conn=8, kind="sum", want_D=True)
+    assert np.array_equal(r.D, D)
+    assert r.new_pairs == 56 * 55 // 2
+
+
 @pytest.mark.parametrize("W", [1, 2, 9, 40])
 def test_l1_one_row_closed_form(W):
     """L1 on a 1xW image: the path is unique, so d(i,j) is the total variation
