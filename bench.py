@@ -123,7 +123,13 @@ class Clocks:
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the dominant kernel per workload, from an ncu capture, with the launch it
 # came from; None when no capture of the kernel as it stands exists.
-DRAM_BYTES = {}
+DRAM_BYTES = {
+    # k_fill_g at 256x256 step edges, launch of round 20 (ncu, one pass,
+    # cold caches, commit 664029f): 473.2 MB read + 533.2 MB written, for
+    # 32,666,831 new pairs (8 B each: 261.3 MB) in that round
+    "steps256": {"kernel": "k_fill", "bytes": 1006.4e6, "launch": "round 20",
+                 "launch_algorithmic_bytes": 261.3e6},
+}
 
 
 THROTTLE = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
@@ -432,6 +438,8 @@ def roofline(w, st, prof, ms_per_step, peaks, dram=None) -> dict:
         tgt = fill if dram["kernel"] == "k_fill" else prop
         tgt["traffic"] = dram["bytes"]
         tgt["traffic_launch"] = dram["launch"]
+        if "launch_algorithmic_bytes" in dram:
+            tgt["traffic_launch_algorithmic_bytes"] = dram["launch_algorithmic_bytes"]
     tot = sum(v[0] for v in prof.values())
     dom = fill if fill_ms >= prop_ms else prop
     out = dict(dom)

@@ -224,8 +224,10 @@ gapsp_status gapsp_all_pairs_batch(gapsp_handle *const *h, int n, gapsp_order or
  */
 gapsp_status gapsp_rows(gapsp_handle *h, const int32_t *sources, int K, uint32_t *out);
 
-/* Releases the handle and its device memory. NULL is accepted. Waits for
- * the handle's work in flight first. */
+/* Releases the handle and its device memory. NULL is accepted. The memory
+ * is released in stream order, after the work queued on the handle's
+ * stream, without waiting for it; a handle that staged a host array (a
+ * host D or host rows) first waits for its stream. */
 void gapsp_destroy(gapsp_handle *h);
 
 /*

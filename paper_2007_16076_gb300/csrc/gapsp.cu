@@ -92,6 +92,30 @@ void hfree(int*& p) {
     p = nullptr;
 }
 
+// Staging buffers for arrays in host memory (up to 17 GB at 256 x 256):
+// plain allocations, kept by the handle, so that repeated calls do not grow
+// and trim the stream-ordered pool by that much each time.
+template <class T>
+cudaError_t salloc(T** p, size_t count) {
+    if (injected_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    const cudaError_t e = cudaMalloc((void**)p, count * sizeof(T) > 0 ? count * sizeof(T) : 1);
+    if (e == cudaSuccess) g_live.fetch_add(1);
+    else *p = nullptr;
+    return e;
+}
+
+template <class T>
+void sfree(T*& p) {
+    if (p) {
+        cudaFree(p);
+        g_live.fetch_sub(1);
+    }
+    p = nullptr;
+}
+
 // Freed blocks up to this size stay in the device's pool for the next
 // handle instead of going back to the driver at every synchronisation.
 void keep_pool_warm() {
@@ -300,7 +324,13 @@ void free_all(gapsp_handle* h) {
     dfree(h->f, st); dfree(h->pgeo, st); dfree(h->tbase, st); dfree(h->bound, st); dfree(h->comp, st);
     dfree(h->comp_size, st); dfree(h->status, st); dfree(h->changed, st);
     free_fill_state(h);
-    dfree(h->Dtmp, st); dfree(h->src_dev, st); dfree(h->out_tmp, st);
+    dfree(h->src_dev, st);
+    if (h->Dtmp || h->out_tmp) {
+        // the staging buffers of host arrays: after the handle's work
+        cudaStreamSynchronize(st);
+        sfree(h->Dtmp);
+        sfree(h->out_tmp);
+    }
     for (auto& t : h->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
     h->timed.clear();
     for (auto e : h->pool) cudaEventDestroy(e);
@@ -539,9 +569,9 @@ gapsp_status gapsp_rows(gapsp_handle* h, const int32_t* sources, int K, uint32_t
     uint32_t* dout = out;
     if (!out_dev) {
         if (h->out_tmp_bytes < out_bytes) {
-            dfree(h->out_tmp, h->st);
+            sfree(h->out_tmp);
             h->out_tmp_bytes = 0;
-            CK(dalloc(&h->out_tmp, (size_t)K * N, h->st));
+            CK(salloc(&h->out_tmp, (size_t)K * N));
             h->out_tmp_bytes = out_bytes;
         }
         dout = h->out_tmp;
@@ -576,14 +606,17 @@ namespace rt {
 
 // Candidates propagated ahead per round: one block (cluster) for each
 // multiprocessor the round's own sources leave free, unless set by option.
-int lookahead_count(const gapsp_handle* h, const PropArgs& pa) {
+int lookahead_count(const gapsp_handle* h, const PropArgs& pa, int sm_share) {
     // a map in global memory is the output row itself, which the round's
     // fill may write while a lookahead launch sweeps it: no lookahead then
     if (h->lookahead < 0 || !prop_map_in_smem(pa)) return 0;
     int K = h->lookahead;
     if (K == 0) {
+        // the multiprocessors this fill may count on: the whole device, or
+        // its share when fills run side by side (batch, server)
         const int per = prop_blocks_per_job(pa);
-        K = h->sms / per - h->B;
+        const int sms = sm_share > 0 ? std::min(sm_share, h->sms) : h->sms;
+        K = sms / per - h->B;
     }
     K = std::min(K, 1024 - h->B);
     return K > 0 ? K : 0;
@@ -603,9 +636,9 @@ gapsp_status fill_begin(FillRun& r) {
     r.Dd = r.D;
     if (!r.d_dev) {
         if (h->Dtmp_bytes < dbytes) {
-            dfree(h->Dtmp, r.s);
+            sfree(h->Dtmp);
             h->Dtmp_bytes = 0;
-            CK(dalloc(&h->Dtmp, N * N, r.s));
+            CK(salloc(&h->Dtmp, N * N));
             h->Dtmp_bytes = dbytes;
         }
         r.Dd = h->Dtmp;
@@ -723,7 +756,7 @@ gapsp_status fill_begin(FillRun& r) {
     pa.row_done = h->row_done;
     if (h->warm) pa.warm_rows = Dd;
     // the repulsion order's draws cannot be foreseen: no lookahead
-    r.K = r.order == GAPSP_REPULSION ? 0 : lookahead_count(h, pa);
+    r.K = r.order == GAPSP_REPULSION ? 0 : lookahead_count(h, pa, r.sm_share);
     if (r.K > 0) {
         r.sa.K = r.K;
         r.sa.KL = 1024 - h->B;
@@ -1068,6 +1101,7 @@ struct BatchGraph {
             runs[i].order = order;
             runs[i].D = Ds[i];
             runs[i].s = ws[i];
+            runs[i].sm_share = std::max(1, hs[i]->sms / n);  // the fills share the device
         }
         gapsp_status gs = GAPSP_OK;
         for (int i = 0; i < n && gs == GAPSP_OK; ++i) gs = fill_begin(runs[i]);

@@ -150,6 +150,7 @@ struct FillRun {
     int rounds = 0;
     bool finished = false;
     bool graphed = false;  // its chunks run as a captured graph (gapsp_all_pairs_batch)
+    int sm_share = 0;      // multiprocessors the fill plans its lookahead for (0: all)
     // lookahead: the next K candidates of each round are propagated on a
     // second stream while the round's tree and fill run
     int K = 0;

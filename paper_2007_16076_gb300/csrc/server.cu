@@ -16,6 +16,7 @@
 // Nothing here waits for the whole device: handles and results come from
 // the stream-ordered allocator. A result stays resident in device memory,
 // counted against the budget, until the client releases it.
+#include <algorithm>
 #include <chrono>
 #include <cstring>
 #include <condition_variable>
@@ -160,6 +161,10 @@ void gapsp_server::begin(Request* r) {
     f.order = q.order;
     f.D = r->out;
     f.s = s;
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+        f.sm_share = std::max(1, sms / (int)busy.size());  // the slots share the device
+    cudaGetLastError();
     if ((gs = fill_begin(f)) == GAPSP_OK && (gs = fill_enqueue(f, kChunk)) == GAPSP_OK)
         gs = fill_enqueue(f, kChunk);
     if (gs != GAPSP_OK) {
