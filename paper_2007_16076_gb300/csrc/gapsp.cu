@@ -240,7 +240,7 @@ size_t fill_state_bytes(const gapsp_handle* h) {
     // point; the lookahead candidate buffers
     return N * h->words * 8 + B * N * (4 + 16 + 8 + 8) +
            N * (4 + 4 + 1 + 4 + 4 + 4 + 8 + 4 + 4 + 4 + 8 + 1 + 1 + 1 + 4 + 4 + 1 + 1) + 2 * 1024 * 4 + 4096 +
-           (N <= 16384 ? 8 * B * N : 0);  // trees handed to k_depths
+           (N <= 16384 ? 4 * kDepRing * B * N : 0);  // trees handed to k_depths
 }
 
 void free_fill_state(gapsp_handle* h);
@@ -289,9 +289,9 @@ gapsp_status alloc_fill_state(gapsp_handle* h, cudaStream_t st) {
     CK(dalloc(&h->cand, 2 * 1024, st));
     CK(dalloc(&h->ncand, 2, st));
     if (N <= 16384) {
-        CK(dalloc(&h->dep_exit, 2 * B * N, st));
-        CK(dalloc(&h->dep_size, 2 * B * N, st));
-        CK(dalloc(&h->dep_count, 2, st));
+        CK(dalloc(&h->dep_exit, kDepRing * B * N, st));
+        CK(dalloc(&h->dep_size, kDepRing * B * N, st));
+        CK(dalloc(&h->dep_count, kDepRing, st));
     }
     CK(dalloc(&h->stats, S_SLOTS, st));
     CK(dalloc(&h->round_new, N + 1, st));
@@ -802,7 +802,7 @@ gapsp_status fill_begin(FillRun& r) {
         int least = 0, greatest = 0;
         CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
         CK(cudaStreamCreateWithPriority(&r.stat, cudaStreamNonBlocking, least));
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < kDepRing; ++i) {
             CK(cudaEventCreateWithFlags(&r.e_tree[i], cudaEventDisableTiming));
             CK(cudaEventCreateWithFlags(&r.e_depth[i], cudaEventDisableTiming));
         }
@@ -832,15 +832,18 @@ gapsp_status fill_enqueue(FillRun& r, int chunk, bool graph) {
             r.sa.cand = h->cand + par * 1024;
             r.sa.ncand = h->ncand + par;
         }
+        const int slot = (r.rounds + i) % kDepRing;
         if (r.stat) {
-            // this round hands its trees to k_depths through the buffer of
-            // its parity, once the launch that read it two rounds ago is done
-            r.ta.dep_exit = h->dep_exit + (size_t)par * h->B * h->N;
-            r.ta.dep_size = h->dep_size + (size_t)par * h->B * h->N;
-            r.ta.dep_count = h->dep_count + par;
-            // (in a graph, the launch of two rounds ago belongs to the
+            // this round hands its trees to the depth sums through the
+            // buffer of its slot in a ring of kDepRing, once the launch that
+            // read it kDepRing rounds ago is done: the depth sums, on a
+            // low-priority stream, have the gaps of several rounds to run in
+            r.ta.dep_exit = h->dep_exit + (size_t)slot * h->B * h->N;
+            r.ta.dep_size = h->dep_size + (size_t)slot * h->B * h->N;
+            r.ta.dep_count = h->dep_count + slot;
+            // (in a graph, the launch kDepRing rounds ago belongs to the
             // previous chunk, which ended before this one started)
-            if (!graph || i >= 2) CK(cudaStreamWaitEvent(s, r.e_depth[par], 0));
+            if (!graph || i >= kDepRing) CK(cudaStreamWaitEvent(s, r.e_depth[slot], 0));
         }
         {
             ProfScope ps(h, K_SELECT, s);
@@ -886,13 +889,13 @@ gapsp_status fill_enqueue(FillRun& r, int chunk, bool graph) {
             CK(launch_recount(r.ta, s, true));
         }
         if (r.stat) {
-            CK(cudaEventRecord(r.e_tree[par], s));
-            CK(cudaStreamWaitEvent(r.stat, r.e_tree[par], 0));
+            CK(cudaEventRecord(r.e_tree[slot], s));
+            CK(cudaStreamWaitEvent(r.stat, r.e_tree[slot], 0));
             {
                 ProfScope ps(h, K_DEPTH, r.stat);
                 CK(launch_depths(r.ta, h->B, r.stat));
             }
-            CK(cudaEventRecord(r.e_depth[par], r.stat));
+            CK(cudaEventRecord(r.e_depth[slot], r.stat));
             h->launches += 1;
         }
         h->launches += 5;
@@ -905,10 +908,8 @@ gapsp_status fill_enqueue(FillRun& r, int chunk, bool graph) {
             CK(cudaStreamWaitEvent(s, r.e_ahead[0], 0));
             CK(cudaStreamWaitEvent(s, r.e_ahead[1], 0));
         }
-        if (r.stat) {
-            CK(cudaStreamWaitEvent(s, r.e_depth[0], 0));
-            CK(cudaStreamWaitEvent(s, r.e_depth[1], 0));
-        }
+        if (r.stat)
+            for (int k = 0; k < kDepRing; ++k) CK(cudaStreamWaitEvent(s, r.e_depth[k], 0));
         CK(cudaMemcpyAsync(h->h_done, h->done, sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(h->h_done + 2, h->status, sizeof(int), cudaMemcpyDeviceToHost, s));
         return GAPSP_OK;
@@ -964,8 +965,7 @@ gapsp_status fill_finish(FillRun& r, gapsp_stats* st) {
         CK(cudaStreamWaitEvent(s, r.e_ahead[1], 0));
     }
     if (r.stat && !r.graphed) {
-        CK(cudaStreamWaitEvent(s, r.e_depth[0], 0));
-        CK(cudaStreamWaitEvent(s, r.e_depth[1], 0));
+        for (int k = 0; k < kDepRing; ++k) CK(cudaStreamWaitEvent(s, r.e_depth[k], 0));
     }
     CK(cudaEventRecord(h->ev1, s));
     unsigned long long hs[S_SLOTS];

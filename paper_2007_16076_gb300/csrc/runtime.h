@@ -60,9 +60,9 @@ struct gapsp_handle {
     uint8_t* rp_taken = nullptr;
     int32_t* cand = nullptr;      // [2][1024]: lookahead candidates, by round parity
     int* ncand = nullptr;         // [2]
-    uint16_t* dep_exit = nullptr; // [2][B][N] (N <= 16384): trees handed to k_depths, by round parity
-    uint16_t* dep_size = nullptr; // [2][B][N]
-    int* dep_count = nullptr;     // [2]
+    uint16_t* dep_exit = nullptr; // [ring][B][N] (N <= 16384): trees handed to k_depths, by round
+    uint16_t* dep_size = nullptr; // [ring][B][N]
+    int* dep_count = nullptr;     // [ring]
     unsigned long long* stats = nullptr;
     unsigned long long* round_new = nullptr;
     unsigned long long* last_new = nullptr;
@@ -91,6 +91,10 @@ struct gapsp_handle {
 
 namespace gapsp {
 namespace rt {
+
+// Depth-sum hand-over buffers per handle: a ring of this many rounds (a
+// chunk of rounds is a whole number of turns of the ring).
+constexpr int kDepRing = 4;
 
 // Host-side fault injection and the count of live allocations
 // (gapsp_debug_fail_alloc).
@@ -166,7 +170,7 @@ struct FillRun {
     // trees are handed over in a buffer of the round's parity, which the
     // tree launch two rounds later waits for
     cudaStream_t stat = nullptr;
-    cudaEvent_t e_tree[2] = {nullptr, nullptr}, e_depth[2] = {nullptr, nullptr};
+    cudaEvent_t e_tree[kDepRing] = {}, e_depth[kDepRing] = {};
     FillRun() = default;
     FillRun(const FillRun&) = delete;
     FillRun& operator=(const FillRun&) = delete;
@@ -189,6 +193,7 @@ struct FillRun {
 // Rounds per chunk: small enough that the rounds queued after the fill is
 // done cost little, large enough that the host stays ahead of the device.
 constexpr int kChunk = 8;
+static_assert(kChunk % kDepRing == 0, "a chunk of rounds is a whole number of turns of the depth ring");
 
 // Set-up of a fill: checks D, allocates what is missing, initialises the
 // state on r.s, runs the extrema pre-pass of the ranked orders.
