@@ -235,11 +235,11 @@ PropArgs base_prop(const gapsp_handle* h) {
 
 size_t fill_state_bytes(const gapsp_handle* h) {
     const size_t N = h->N, B = h->B;
-    // marks; parent, seg, jmp, acc per source; cnt, cnt_base, dirty, seq,
+    // marks; parent, seg, jmp, acc per source; cnt, cnt_base, seq,
     // rank, grank, round_new, sel_log, emap, gmap, best, cen, row_done per
     // point; the lookahead candidate buffers
     return N * h->words * 8 + B * N * (4 + 16 + 8 + 8) +
-           N * (4 + 4 + 1 + 4 + 4 + 4 + 8 + 4 + 4 + 4 + 8 + 1 + 1 + 1 + 4 + 4 + 1 + 1) + 2 * 1024 * 4 + 4096 +
+           N * (4 + 4 + 4 + 4 + 4 + 8 + 4 + 4 + 4 + 8 + 1 + 1 + 1 + 4 + 4 + 1 + 1) + 2 * 1024 * 4 + 4096 +
            (N <= 16384 ? 4 * kDepRing * B * N : 0);  // trees handed to k_depths
 }
 
@@ -265,7 +265,6 @@ gapsp_status alloc_fill_state(gapsp_handle* h, cudaStream_t st) {
     const size_t N = h->N, B = h->B;
     CK(dalloc(&h->cnt, N, st));
     CK(dalloc(&h->cnt_base, N, st));
-    CK(dalloc(&h->dirty, N, st));
     CK(dalloc(&h->marks, N * h->words, st));
     CK(dalloc(&h->parent, B * N, st));
     CK(dalloc(&h->seg, B * N, st));
@@ -307,7 +306,7 @@ gapsp_status alloc_fill_state(gapsp_handle* h, cudaStream_t st) {
 }
 
 void free_fill_state(gapsp_handle* h) {
-    dfree(h->cnt, h->st); dfree(h->cnt_base, h->st); dfree(h->dirty, h->st); dfree(h->marks, h->st); dfree(h->parent, h->st); dfree(h->seg, h->st); dfree(h->jmp, h->st); dfree(h->acc, h->st);
+    dfree(h->cnt, h->st); dfree(h->cnt_base, h->st); dfree(h->marks, h->st); dfree(h->parent, h->st); dfree(h->seg, h->st); dfree(h->jmp, h->st); dfree(h->acc, h->st);
     dfree(h->sel, h->st); dfree(h->nsel, h->st); dfree(h->cursor, h->st); dfree(h->done, h->st); dfree(h->seq, h->st); dfree(h->rank, h->st); dfree(h->grank, h->st);
     dfree(h->row_done, h->st); dfree(h->row_claim, h->st); dfree(h->cand, h->st); dfree(h->ncand, h->st);
     dfree(h->rp_ring, h->st); dfree(h->rp_fstart, h->st); dfree(h->rp_fcyc, h->st); dfree(h->rp_inS, h->st); dfree(h->rp_state, h->st);
@@ -704,7 +703,6 @@ gapsp_status fill_begin(FillRun& r) {
         CK(launch_init(ia, s));
     }
     CK(cudaMemcpyAsync(h->cnt_base, h->cnt, N * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemsetAsync(h->dirty, 0, N, s));
     h->launches += 1;
 
     r.prepass = 0;
@@ -782,7 +780,7 @@ gapsp_status fill_begin(FillRun& r) {
     ta.pgeo = h->pgeo; ta.tbase = h->tbase;
     ta.parent = h->parent; ta.seg = h->seg; ta.jmp = h->jmp; ta.acc = h->acc;
     ta.marks = h->marks; ta.cnt = h->cnt; ta.Dw = Dd; ta.stats = h->stats;
-    ta.cnt_base = h->cnt_base; ta.dirty = h->dirty;
+    ta.cnt_base = h->cnt_base;
     {
         const size_t row_bytes = fill_smem_bytes(1, h->words);  // marks + changed flags
         int rpb = (int)((96 * 1024) / row_bytes);

@@ -106,7 +106,6 @@ struct TreeArgs {
     unsigned long long* marks;  // [N][words]
     uint32_t* cnt;              // [N]
     const uint32_t* cnt_base;   // [N] fill count at the start (1 + pairs no path joins)
-    uint8_t* dirty;             // [N] rows that gained marks this round
     uint32_t* Dw;               // writable array for new pairs
     unsigned long long* stats;  // StatSlot counters
     int rows_per_block;

@@ -37,7 +37,6 @@ struct gapsp_handle {
     bool fill_ready = false;
     uint32_t* cnt = nullptr;
     uint32_t* cnt_base = nullptr;
-    uint8_t* dirty = nullptr;
     unsigned long long* marks = nullptr;
     int32_t* parent = nullptr;
     ulonglong2* seg = nullptr;

@@ -560,7 +560,6 @@ __global__ void __launch_bounds__(256, 4) k_fill(TreeArgs a) {
     pdl_trigger();
     __shared__ int s_rows[32], s_tile[32], s_bit[32];
     __shared__ int s_nu;
-    __shared__ unsigned s_gain;  // bit i: row s_rows[i] gained marks
     const int nsel = *a.nsel;
     if (nsel == 0) return;
     const int b0 = blockIdx.x * a.rows_per_block;
@@ -578,7 +577,6 @@ __global__ void __launch_bounds__(256, 4) k_fill(TreeArgs a) {
         }
         if (lane == 0) {
             s_nu = __popc(m);
-            s_gain = 0;
         }
     }
     __syncthreads();
@@ -607,7 +605,6 @@ __global__ void __launch_bounds__(256, 4) k_fill(TreeArgs a) {
         uint8_t* mychg = chg + (size_t)bl * cs;
         const int tb = s_tile[bl];
         const unsigned long long bbit = 1ull << s_bit[bl];
-        bool gained = false;
         // one tile segment: the bits of m not yet in row b are new pairs
         auto take = [&](int t, unsigned long long m) {
             // a plain read first: most segments bring nothing new, and the
@@ -623,7 +620,6 @@ __global__ void __launch_bounds__(256, 4) k_fill(TreeArgs a) {
             const unsigned ohi = hi ? atomicOr(w32 + 1, hi) : 0xFFFFFFFFu;
             unsigned long long nb = (((unsigned long long)hi << 32) | lo) & ~(((unsigned long long)ohi << 32) | olo);
             if (!nb) return;
-            gained = true;
             mychg[t] = 1;
             const int base = __ldg(a.tbase + t);
             // up to 8 new pairs at a time: the distance loads first, so that
@@ -648,7 +644,6 @@ __global__ void __launch_bounds__(256, 4) k_fill(TreeArgs a) {
                     if (ap[k] < 0) continue;
                     const uint32_t val = db - dv[k];
                     atomicOr(a.marks + (size_t)ap[k] * words + tb, bbit);
-                    a.dirty[ap[k]] = 1;
                     // streaming stores: D is far larger than L2, keep the
                     // trees and marks resident instead
                     __stcs(a.Dw + (size_t)ap[k] * a.N + b, val);
@@ -677,14 +672,12 @@ __global__ void __launch_bounds__(256, 4) k_fill(TreeArgs a) {
             t = t2;
             m = g.x;
         }
-        if (gained) atomicOr(&s_gain, 1u << bl);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nu * words; i += blockDim.x) {
         const int r = i / words, w = i - r * words;
         if (chg[r * cs + w]) atomicOr(a.marks + (size_t)s_rows[r] * words + w, srow[r * rs + w]);
     }
-    if (threadIdx.x < nu && ((s_gain >> threadIdx.x) & 1u)) a.dirty[s_rows[threadIdx.x]] = 1;
 }
 
 #ifndef FILL_G_MINB
@@ -723,13 +716,11 @@ __global__ void __launch_bounds__(128, FILL_G_MINB) k_fill_g(TreeArgs a, int qua
     const uint32_t gb = __ldg(a.pgeo + b);
     const int tb = (int)(gb >> 8);
     const unsigned long long bbit = 1ull << (gb & 63);
-    bool gained = false;
     auto take = [&](int t, unsigned long long m, unsigned long long w) {
         unsigned long long nb = m & ~w;
         if (!nb) return;
         nb &= ~atomicOr(a.marks + mrow + t, nb);
         if (!nb) return;
-        gained = true;
         const int base = __ldg(a.tbase + t);
         while (nb) {
             int ap[4];
@@ -749,10 +740,6 @@ __global__ void __launch_bounds__(128, FILL_G_MINB) k_fill_g(TreeArgs a, int qua
                 if (ap[k] < 0) continue;
                 const uint32_t val = db - dv[k];
                 atomicOr(a.marks + (uint32_t)ap[k] * (uint32_t)a.words + tb, bbit);
-                // most rows are flagged already: a read (which may be stale,
-                // costing one redundant store) spares the flag array, 1 byte
-                // per row, millions of stores to the same few lines
-                if (!a.dirty[ap[k]]) a.dirty[ap[k]] = 1;
                 __stcs(a.Dw + (uint32_t)ap[k] * (uint32_t)a.N + b, val);
                 __stcs(a.Dw + brow + ap[k], val);
             }
@@ -785,13 +772,15 @@ __global__ void __launch_bounds__(128, FILL_G_MINB) k_fill_g(TreeArgs a, int qua
         m = g.x;
         w = w2;
     }
-    if (gained) a.dirty[b] = 1;
 }
 
-// Fill counts of the rows that gained marks: cnt(x) = cnt at the start +
-// the number of marked pairs of row x (both bits of a pair are set, so row
-// x holds every filled pair {x, y}). One warp per row. The increments are
-// summed into S_NEW, which thus counts every new pair twice.
+// Fill counts of the rows still open: cnt(x) = cnt at the start + the
+// number of marked pairs of row x (both bits of a pair are set, so row x
+// holds every filled pair {x, y}). One warp per row; rows already filled
+// (cnt = N) cannot change. Recounting every open row costs one streaming
+// read of its marks, where flagging the rows that changed cost the fill a
+// store per new pair. The increments are summed into S_NEW, which thus
+// counts every new pair twice.
 __global__ void k_recount(TreeArgs a) {
     __shared__ unsigned long long s_sum;
     pdl_wait();
@@ -799,7 +788,7 @@ __global__ void k_recount(TreeArgs a) {
     __syncthreads();
     const int x = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (x < a.N && a.dirty[x]) {
+    if (x < a.N && __ldcg(a.cnt + x) < (uint32_t)a.N) {
         const unsigned long long* row = a.marks + (size_t)x * a.words;
         unsigned c = 0;
         for (int w = lane; w < a.words; w += 32) c += __popcll(__ldcg(row + w));
@@ -808,7 +797,6 @@ __global__ void k_recount(TreeArgs a) {
             const uint32_t nc = a.cnt_base[x] + c;
             atomicAdd(&s_sum, (unsigned long long)(nc - a.cnt[x]));
             a.cnt[x] = nc;
-            a.dirty[x] = 0;
         }
     }
     __syncthreads();
