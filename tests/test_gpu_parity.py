@@ -396,25 +396,28 @@ def test_counts_blobs136x121(gp, order):
 # Full-size 256x256 workloads (17.2 GB array on the device)
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("name,factory", [("steps256", synth.steps_256), ("mask256", synth.mask_256)])
-def test_full_size_256(gp, name, factory):
-    """256x256, 8-connected, B = 32, minimum filling rate: the counts against
-    the oracle's stored simulation, sampled rows and columns of D against
-    Dijkstra, and symmetry of the sampled entries."""
+@pytest.mark.parametrize("name,factory,order", [("steps256", synth.steps_256, o) for o in
+                                               ("minfill", "naive", "spiral", "extrema", "repulsion")] +
+                         [("mask256", synth.mask_256, "minfill")])
+def test_full_size_256(gp, name, factory, order):
+    """256x256, 8-connected, B = 32 (the benchmark's workload, every order;
+    and the obstacle mask): the counts against the oracle's stored
+    simulation, sampled rows and columns of D against Dijkstra, and symmetry
+    of the sampled entries."""
     import torch
     path = os.path.join(GOLDEN, f"counts_{name}.json")
     if not os.path.exists(path):
         pytest.skip("counts fixture not generated")
     gold_all = json.load(open(path))["orders"]
-    if "minfill" not in gold_all:
-        pytest.skip("minfill counts not generated")
-    gold = gold_all["minfill"]
+    if order not in gold_all:
+        pytest.skip(f"{order} counts not generated")
+    gold = gold_all[order]
     w = factory(0)
     N = w.N
     img = w.img if w.kind == "grey" else None
     D = torch.empty((N, N), dtype=torch.int32, device="cuda")
     with gp.Image(img, conn=w.conn, kind=w.kind, mask=w.mask, B=w.B, seed=0) as im:
-        _, st = im.all_pairs("minfill", out=D, want_log=True)
+        _, st = im.all_pairs(order, out=D, want_log=True)
     for k in ("propagations", "prepass_propagations", "distance_ops", "new_pairs", "rounds"):
         assert st[k] == gold[k], k
     assert [int(x) for x in st["round_new"]] == gold["round_new"]
