@@ -299,7 +299,7 @@ gapsp_status alloc_fill_state(gapsp_handle* h, cudaStream_t st) {
     CK(dalloc(&h->sel_log, N + 1, st));
     CK(dalloc(&h->emap, N, st));
     CK(dalloc(&h->gmap, N, st));
-    CK(dalloc(&h->best, N, st));
+    CK(dalloc(&h->best, (N + 16383) / 16384 * 16384, st));  // also the rank sort's scratch
     CK(dalloc(&h->cen, N, st));
     CK(halloc(&h->h_done));
     return GAPSP_OK;
@@ -718,8 +718,9 @@ gapsp_status fill_begin(FillRun& r) {
             ProfScope ps(h, K_PROP, s);
             CK(launch_propagate(a, h->conn, h->kind, 1, 1, s));
         }
+        // (the centroids' scratch is free again when the ranks are sorted)
         ExtremaArgs ea{h->N, h->kind == GAPSP_MASK ? h->f : nullptr, h->comp, h->emap, h->best, h->cen,
-                       h->gmap, h->rank, h->grank};
+                       h->gmap, h->rank, h->grank, h->N > 16384 ? h->best : nullptr};
         {
             ProfScope ps(h, K_PRE, s);
             CK(launch_centroids(ea, s));
@@ -734,7 +735,7 @@ gapsp_status fill_begin(FillRun& r) {
             ProfScope ps(h, K_PRE, s);
             CK(launch_rank(ea, s));
         }
-        h->launches += 6;
+        h->launches += h->N > 16384 ? 7 : 6;  // the larger images rank in two launches
         r.prepass = 2;
     }
 

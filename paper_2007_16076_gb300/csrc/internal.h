@@ -194,6 +194,7 @@ struct ExtremaArgs {
     const uint32_t* g;          // distance from the centroids
     int32_t* rank;              // [N]
     int32_t* grank;             // [N]
+    unsigned long long* keys;   // N > 16384: sort scratch, N rounded up to 16384 keys, or NULL
 };
 cudaError_t launch_centroids(const ExtremaArgs& a, cudaStream_t st);
 cudaError_t launch_rank(const ExtremaArgs& a, cudaStream_t st);

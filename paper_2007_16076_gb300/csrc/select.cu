@@ -820,6 +820,72 @@ __global__ void __launch_bounds__(RANK_THREADS) k_rank_sort(ExtremaArgs a) {
 // Position in the extrema list Ext: free pixels by decreasing distance from
 // the centroid, ties by increasing index; and the number of free pixels
 // strictly farther from the centroid. Counted directly.
+// Larger images (N > 16384): ranks from sorted chunks. Each block sorts
+// 16384 keys (not g, p), padding and obstacles as all ones, in shared memory
+// (bitonic) and writes them to a.keys; the rank of p is then the number of
+// keys below its own over all chunks, and its count of points strictly
+// farther from the centroids the number of keys below (not g, 0), each
+// found by a binary search in every chunk.
+constexpr int RANK_CHUNK = 16384;
+
+__global__ void __launch_bounds__(RANK_THREADS) k_rank_chunks(ExtremaArgs a) {
+    extern __shared__ unsigned long long ck[];
+    const int tid = threadIdx.x, c0 = blockIdx.x * RANK_CHUNK;
+    for (int i = tid; i < RANK_CHUNK; i += RANK_THREADS) {
+        const int p = c0 + i;
+        unsigned long long k = ~0ull;
+        if (p < a.N && (!a.freef || a.freef[p])) k = ((unsigned long long)(~a.g[p]) << 32) | (unsigned)p;
+        ck[i] = k;
+    }
+    __syncthreads();
+    for (int k = 2; k <= RANK_CHUNK; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < RANK_CHUNK; i += RANK_THREADS) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const unsigned long long x = ck[i], y = ck[ixj];
+                    if ((x > y) == ((i & k) == 0)) {
+                        ck[i] = y;
+                        ck[ixj] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = tid; i < RANK_CHUNK; i += RANK_THREADS) a.keys[c0 + i] = ck[i];
+}
+
+// Number of keys of the sorted chunk below x.
+__device__ __forceinline__ int below(const unsigned long long* chunk, unsigned long long x) {
+    int lo = 0, hi = RANK_CHUNK;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (chunk[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_rank_merge(ExtremaArgs a, int chunks) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.N) return;
+    if (a.freef && !a.freef[p]) {
+        a.rank[p] = -1;
+        a.grank[p] = -1;
+        return;
+    }
+    const unsigned long long hi = (unsigned long long)(~a.g[p]) << 32;
+    const unsigned long long key = hi | (unsigned)p;
+    int r = 0, gr = 0;
+    for (int c = 0; c < chunks; ++c) {
+        const unsigned long long* chunk = a.keys + (size_t)c * RANK_CHUNK;
+        r += below(chunk, key);
+        gr += below(chunk, hi);
+    }
+    a.rank[p] = r;
+    a.grank[p] = gr;
+}
+
 __global__ void k_rank(ExtremaArgs a) {
     __shared__ uint32_t sg[1024];
     __shared__ uint8_t sf[1024];
@@ -946,6 +1012,14 @@ cudaError_t launch_rank(const ExtremaArgs& a, cudaStream_t st) {
         int n2 = 1;
         while (n2 < a.N) n2 <<= 1;
         k_rank_sort<<<1, RANK_THREADS, (size_t)n2 * 8, st>>>(a);
+    } else if (a.keys) {
+        static std::atomic<unsigned long long> attr2{0};
+        once_per_device(attr2, [] {
+            cudaFuncSetAttribute(k_rank_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize, RANK_CHUNK * 8);
+        });
+        const int chunks = (a.N + RANK_CHUNK - 1) / RANK_CHUNK;
+        k_rank_chunks<<<chunks, RANK_THREADS, (size_t)RANK_CHUNK * 8, st>>>(a);
+        k_rank_merge<<<(a.N + 255) / 256, 256, 0, st>>>(a, chunks);
     } else {
         k_rank<<<(a.N + 255) / 256, 256, 0, st>>>(a);
     }
