@@ -2,7 +2,9 @@
 // them (declared in include/gapsp.h).
 //
 // The candidates are the parameters that shape the work on the GPU without
-// changing D: sources per round B (how many trees a round builds and fills),
+// changing D: sources per round B in {16, 32, 64, 128, 256} (how many trees a
+// round builds and fills: wider rounds make the chain of rounds shorter and
+// cost more propagations),
 // whether rows are computed ahead (the lookahead launches), and how the tree
 // fill claims its pairs (marks in global memory, or rows of marks staged in
 // shared memory). Each candidate fills the caller's image once after a
@@ -47,7 +49,7 @@ bool cache_lookup(const char* path, const Key& k, Choice& c) {
     while (std::fgets(line, sizeof line, f)) {
         Key x{};
         Choice y{};
-        if (std::sscanf(line, "gapsp-tune-1 %d %d %d %d %d %d %d %d %d %lf", &x.H, &x.W, &x.conn, &x.kind, &x.order,
+        if (std::sscanf(line, "gapsp-tune-2 %d %d %d %d %d %d %d %d %d %lf", &x.H, &x.W, &x.conn, &x.kind, &x.order,
                         &x.sms, &y.B, &y.lookahead, &y.fill_rows, &y.ms) == 10 &&
             x == k) {
             c = y;  // the last line for a key wins
@@ -62,7 +64,7 @@ void cache_store(const char* path, const Key& k, const Choice& c) {
     if (!path) return;
     FILE* f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "gapsp-tune-1 %d %d %d %d %d %d %d %d %d %.4f\n", k.H, k.W, k.conn, k.kind, k.order, k.sms, c.B,
+    std::fprintf(f, "gapsp-tune-2 %d %d %d %d %d %d %d %d %d %.4f\n", k.H, k.W, k.conn, k.kind, k.order, k.sms, c.B,
                  c.lookahead, c.fill_rows, c.ms);
     std::fclose(f);
 }
@@ -115,7 +117,7 @@ extern "C" gapsp_status gapsp_tune(const uint8_t* img, const uint8_t* mask, int 
             cudaStreamDestroy(st);
             return GAPSP_E_NOMEM;
         }
-        const int Bs[] = {16, 32, 64};
+        const int Bs[] = {16, 32, 64, 128, 256};
         const int looks[] = {0, -1};
         const int fills[] = {0, 8};
         c.ms = -1.0;
