@@ -226,7 +226,7 @@ def _serve(gp, torch, stream, seconds: float, budget: int = 120 << 30, slots: in
     import threading
 
     reqs = _serve_stream(seconds)
-    srv = gp.Server(mem_budget=budget, slots=slots, B=32)
+    srv = gp.Server(mem_budget=budget, slots=slots)  # the server's defaults (B = 256)
     # warm-up: one request of each kind
     srv.release(srv.wait(srv.submit_rows(reqs[0][2], [0, 1, 2]))["id"])
     srv.release(srv.wait(srv.submit_all_pairs(_serve_stream(5.0, seed=1)[0][2]))["id"])

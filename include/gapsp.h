@@ -370,7 +370,7 @@ typedef struct {
 typedef struct {
     size_t mem_budget;  /* device bytes the admitted requests may hold at once (0 = 120 GiB) */
     int slots;          /* requests running at once, one stream each: 1..256 (0 = 16) */
-    int B;              /* sources per round of the fills (0 = 32) */
+    int B;              /* sources per round of the fills (0 = 256: fewer rounds, lower latency) */
     int lookahead;      /* as gapsp_opts.lookahead, for the fills */
 } gapsp_server_opts;
 
