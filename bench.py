@@ -138,13 +138,12 @@ class Clocks:
 # the dominant kernel per workload, from an ncu capture, with the launch it
 # came from; None when no capture of the kernel as it stands exists.
 DRAM_BYTES = {
-    # k_fill_g at 256x256 step edges, launch of round 20 (ncu, one pass,
-    # cold caches, commit 664029f): 473.2 MB read + 533.2 MB written, for
-    # 32,666,831 new pairs (8 B each: 261.3 MB) in that round
-    "steps256": {"kernel": "k_fill", "bytes": 1006.4e6, "launch": "round 20",
-                 "launch_algorithmic_bytes": 261.3e6},
+    # k_fill_g at 256x256 step edges with the tuned options (B = 256), the
+    # launch of round 8 (ncu, one pass, cold caches, commit f232e2c): 2.54 GB
+    # read + 0.589 GB written, for 41422102 new pairs (8 B each) in that round
+    "steps256": {"kernel": "k_fill", "bytes": 3129.18e6, "launch": "round 8",
+                 "launch_algorithmic_bytes": 331.4e6},
 }
-
 
 THROTTLE = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
 

@@ -396,9 +396,15 @@ def test_counts_blobs136x121(gp, order):
 # Full-size 256x256 workloads (17.2 GB array on the device)
 # --------------------------------------------------------------------------
 
+def _with_B(w, B):
+    w.B = B
+    return w
+
+
 @pytest.mark.parametrize("name,factory,order", [("steps256", synth.steps_256, o) for o in
                                                ("minfill", "naive", "spiral", "extrema", "repulsion")] +
-                         [("mask256", synth.mask_256, "minfill")])
+                         [("mask256", synth.mask_256, "minfill"),
+                          ("steps256_B256", lambda seed: _with_B(synth.steps_256(seed), 256), "minfill")])
 def test_full_size_256(gp, name, factory, order):
     """256x256, 8-connected, B = 32 (the benchmark's workload, every order;
     and the obstacle mask): the counts against the oracle's stored
