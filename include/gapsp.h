@@ -68,7 +68,8 @@ typedef enum {
     GAPSP_E_CUDA = 4,           /* a CUDA runtime call failed */
     GAPSP_E_NOT_CONVERGED = 5,  /* a propagation hit its sweep limit */
     GAPSP_E_TIMEOUT = 6,        /* a round loop hit its round limit */
-    GAPSP_E_CANCELLED = 7       /* gapsp_cancel stopped the call */
+    GAPSP_E_CANCELLED = 7,      /* gapsp_cancel stopped the call */
+    GAPSP_E_CHECK = 8           /* the result failed its certificate (opts.checked) */
 } gapsp_status;
 
 typedef enum {
@@ -96,7 +97,9 @@ typedef struct {
     size_t mem_budget; /* bytes of device memory a call may use (0 = no limit) */
     int sweep_phases;  /* warps per sweep direction in a propagation: 0 = auto, 1, 2 or 4 */
     int fill_rows;     /* rows of marks per tree-fill block: 0 = auto, else 1..32 */
-    int checked;       /* reserved (0) */
+    int checked;       /* 1: certify every result before returning it (gapsp_certify on the
+                          whole D or on the rows; about one more read of the array);
+                          a result that fails returns GAPSP_E_CHECK. 0: off */
     void *stream;      /* cudaStream_t the calls run on (NULL = default stream) */
     int prop_blocks;   /* blocks (row strips, one thread-block cluster) per propagation:
                           0 = auto, 1, 2 or 4 */
@@ -223,6 +226,23 @@ gapsp_status gapsp_all_pairs_batch(gapsp_handle *const *h, int n, gapsp_order or
  * an invalid source nothing is written.
  */
 gapsp_status gapsp_rows(gapsp_handle *h, const int32_t *sources, int K, uint32_t *out);
+
+/*
+ * Certificate of a result, independent of how it was computed. With positive
+ * integer edge weights the distances from p are the unique solution of
+ * d(p,p) = 0 and d(p,r) = min over the neighbours q of r of d(p,q) + w(q,r)
+ * for r != p (Sec. 2, eqs. "temps" and "distance": a shortest path ends
+ * with an edge), UNREACH when no neighbour is reachable. The call checks
+ * every entry of the K rows given against that equation, on the device, and
+ * so proves the rows exact when it counts no violation.
+ *   D       : K*N uint32, device pointer, row k = d(sources[k], .).
+ *   sources : K int32 host or device, or NULL for rows 0..K-1 (the whole
+ *             array when K = N).
+ *   bad     : receives the number of entries that break the equation.
+ * Returns GAPSP_OK (whatever *bad is), GAPSP_E_INVALID, GAPSP_E_CUDA.
+ */
+gapsp_status gapsp_certify(gapsp_handle *h, const uint32_t *D, const int32_t *sources, int K,
+                           uint64_t *bad);
 
 /* Releases the handle and its device memory. NULL is accepted. The memory
  * is released in stream order, after the work queued on the handle's

@@ -23,7 +23,7 @@ KINDS = {"grey": 0, "mask": 1, "l1": 2, "sum": 3}
 KERNELS = ("select", "propagate", "tree", "lookahead", "fill", "init", "prepass", "depths", "recount")
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "memory budget exceeded",
           4: "CUDA runtime error", 5: "propagation did not converge", 6: "round limit exceeded",
-          7: "cancelled"}
+          7: "cancelled", 8: "result failed its certificate"}
 
 _lib = None
 
@@ -152,6 +152,8 @@ def load(build_if_missing: bool = True):
     lib.gapsp_tune.restype = ctypes.c_int
     lib.gapsp_last_error_detail.argtypes = []
     lib.gapsp_last_error_detail.restype = ctypes.c_char_p
+    lib.gapsp_certify.argtypes = [P, P, P, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]
+    lib.gapsp_certify.restype = ctypes.c_int
     lib.gapsp_cancel.argtypes = [P]
     lib.gapsp_cancel.restype = ctypes.c_int
     lib.gapsp_debug_fail_alloc.argtypes = [ctypes.c_int]
@@ -289,7 +291,8 @@ class Image:
     def __init__(self, img, conn: int = 8, kind: str = "grey", mask=None, B: int = 32,
                  seed: int = 0, mem_budget: int = 0, stream=None, sweep_phases: int = 0,
                  fill_rows: int = 0, prop_blocks: int = 0, lookahead: int = 0,
-                 warm_start: int = 0, max_sweep_rounds: int = 0, max_rounds: int = 0):
+                 warm_start: int = 0, max_sweep_rounds: int = 0, max_rounds: int = 0,
+                 checked: int = 0):
         lib = load()
         self._lib = lib
         self._h = ctypes.c_void_p()
@@ -321,6 +324,7 @@ class Image:
         o.warm_start = warm_start
         o.max_sweep_rounds = max_sweep_rounds
         o.max_rounds = max_rounds
+        o.checked = checked
         o.stream = _torch_stream(stream)
         self.H, self.W, self.N, self.conn, self.kind, self.B = H, W, H * W, conn, kind, B
         if kind == "sum":
@@ -347,6 +351,20 @@ class Image:
 
     def __exit__(self, *exc):
         self.close()
+
+    def certify(self, D, sources=None) -> int:
+        """gapsp_certify: the number of entries of D (CUDA, K x N; row k =
+        d(sources[k], .), or rows 0.. when sources is None) that break the
+        distance equations; 0 proves the rows exact."""
+        K = int(D.shape[0])
+        src = None
+        if sources is not None:
+            src = sources if hasattr(sources, "data_ptr") else np.ascontiguousarray(sources, dtype=np.int32)
+        bad = ctypes.c_uint64()
+        rc = self._lib.gapsp_certify(self._h, _ptr(D), _ptr(src), K, ctypes.byref(bad))
+        if rc != 0:
+            raise GapspError(rc, "gapsp_certify")
+        return int(bad.value)
 
     def cancel(self):
         """Asks the all-pairs call running on this handle in another thread to

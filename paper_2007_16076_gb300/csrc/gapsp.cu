@@ -321,7 +321,7 @@ void free_fill_state(gapsp_handle* h) {
 void free_all(gapsp_handle* h) {
     cudaStream_t st = h->st;
     dfree(h->f, st); dfree(h->pgeo, st); dfree(h->tbase, st); dfree(h->bound, st); dfree(h->comp, st);
-    dfree(h->comp_size, st); dfree(h->status, st); dfree(h->changed, st);
+    dfree(h->comp_size, st); dfree(h->status, st); dfree(h->changed, st); dfree(h->bad, st);
     free_fill_state(h);
     dfree(h->src_dev, st);
     if (h->Dtmp || h->out_tmp) {
@@ -395,6 +395,7 @@ const char* gapsp_strerror(gapsp_status s) {
         case GAPSP_E_NOT_CONVERGED: return "propagation did not converge within its sweep limit";
         case GAPSP_E_TIMEOUT: return "round loop exceeded its round limit";
         case GAPSP_E_CANCELLED: return "cancelled";
+        case GAPSP_E_CHECK: return "result failed its certificate";
     }
     return "unknown status";
 }
@@ -434,6 +435,7 @@ static gapsp_status create_handle(const uint8_t* img, int L, int H, int W, const
     if (o.lookahead < -1 || o.lookahead > 1024) return GAPSP_E_INVALID;
     if (o.warm_start != 0 && o.warm_start != -1) return GAPSP_E_INVALID;
     if (o.max_sweep_rounds < 0 || o.max_rounds < 0) return GAPSP_E_INVALID;
+    if (o.checked != 0 && o.checked != 1) return GAPSP_E_INVALID;
     if (o.kind != GAPSP_MASK && !img) return GAPSP_E_INVALID;
     if (o.kind == GAPSP_MASK && !mask) return GAPSP_E_INVALID;
 
@@ -448,6 +450,7 @@ static gapsp_status create_handle(const uint8_t* img, int L, int H, int W, const
     h->warm = o.warm_start == 0;
     h->max_sweep_rounds = o.max_sweep_rounds;
     h->max_rounds = o.max_rounds;
+    h->checked = o.checked == 1;
     {
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -475,6 +478,7 @@ static gapsp_status create_handle(const uint8_t* img, int L, int H, int W, const
     if ((e = dalloc(&h->bound, N, h->st)) != cudaSuccess) return fail(e);
     if ((e = dalloc(&h->status, 1, h->st)) != cudaSuccess) return fail(e);
     if ((e = dalloc(&h->changed, 1, h->st)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(&h->bad, 1, h->st)) != cudaSuccess) return fail(e);
     if ((e = cudaEventCreate(&h->ev0)) != cudaSuccess) return fail(e);
     if ((e = cudaEventCreate(&h->ev1)) != cudaSuccess) return fail(e);
     // the kernels read grey levels (grey) or free flags (mask) from h->f
@@ -590,6 +594,21 @@ gapsp_status gapsp_rows(gapsp_handle* h, const int32_t* sources, int K, uint32_t
         CK(launch_propagate(a, h->conn, h->kind, (K + wpb - 1) / wpb, wpb, h->st));
     }
     h->launches += 1;
+    if (h->checked) {
+        int sw0 = 0;
+        CK(cudaMemcpyAsync(&sw0, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        uint64_t bad = 0;
+        if (sw0 == 0) {
+            const gapsp_status cs = certify_rows(h, dout, h->src_dev, K, h->st, &bad);
+            if (cs != GAPSP_OK) return cs;
+        }
+        if (bad) {
+            std::snprintf(t_detail, sizeof t_detail, "certificate: %llu entries of the rows break the distance equations",
+                          (unsigned long long)bad);
+            return GAPSP_E_CHECK;
+        }
+    }
     if (!out_dev) CK(cudaMemcpyAsync(out, dout, out_bytes, cudaMemcpyDeviceToHost, h->st));
     int sw = 0;
     CK(cudaMemcpyAsync(&sw, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
@@ -939,6 +958,19 @@ gapsp_status fill_poll(FillRun& r) {
     return GAPSP_OK;
 }
 
+gapsp_status certify_rows(gapsp_handle* h, const uint32_t* D, const int32_t* src, int K, cudaStream_t st,
+                          uint64_t* bad) {
+    CertifyArgs ca{D, K, src, h->H, h->W, h->N, h->conn, h->kind, h->f, h->bad};
+    unsigned long long hb = 0;
+    CK(cudaMemsetAsync(h->bad, 0, sizeof(unsigned long long), st));
+    CK(launch_certify(ca, st));
+    h->launches += 1;
+    CK(cudaMemcpyAsync(&hb, h->bad, sizeof(hb), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *bad = hb;
+    return GAPSP_OK;
+}
+
 bool fill_chunk_ready(const FillRun& r) {
     return cudaEventQuery(r.chunk_ev[r.polled & 1]) != cudaErrorNotReady;
 }
@@ -1004,6 +1036,16 @@ gapsp_status fill_finish(FillRun& r, gapsp_stats* st) {
             for (size_t p = 0; p < N; ++p)
                 if (comp[p] == (int32_t)p) same += (uint64_t)size[p] * (uint64_t)(size[p] - 1) / 2;
             st->prefilled_pairs = (uint64_t)N * (N - 1) / 2 - same;
+        }
+    }
+    if (h->checked && sw == 0) {
+        uint64_t bad = 0;
+        const gapsp_status cs = certify_rows(h, r.Dd, nullptr, h->N, s, &bad);
+        if (cs != GAPSP_OK) return cs;
+        if (bad) {
+            std::snprintf(t_detail, sizeof t_detail, "certificate: %llu entries of D break the distance equations",
+                          (unsigned long long)bad);
+            return GAPSP_E_CHECK;
         }
     }
     if (!r.d_dev) CK(cudaMemcpyAsync(r.D, r.Dd, N * N * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
@@ -1210,6 +1252,30 @@ gapsp_status gapsp_all_pairs(gapsp_handle* h, gapsp_order order, uint32_t* D, ga
 }
 
 const char* gapsp_last_error_detail(void) { return t_detail; }
+
+gapsp_status gapsp_certify(gapsp_handle* h, const uint32_t* D, const int32_t* sources, int K, uint64_t* bad) {
+    if (!h || !D || !bad || K < 0 || (!sources && K > h->N)) return GAPSP_E_INVALID;
+    *bad = 0;
+    if (K == 0) return GAPSP_OK;
+    if (!is_device_ptr(D)) return GAPSP_E_INVALID;
+    int32_t* dsrc = nullptr;
+    if (sources) {
+        std::vector<int32_t> hs(K);
+        CK(cudaMemcpyAsync(hs.data(), sources, (size_t)K * sizeof(int32_t), cudaMemcpyDefault, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        for (int k = 0; k < K; ++k)
+            if (hs[k] < 0 || hs[k] >= h->N) return GAPSP_E_INVALID;
+        CK(dalloc(&dsrc, (size_t)K, h->st));
+        const cudaError_t e = cudaMemcpyAsync(dsrc, hs.data(), (size_t)K * sizeof(int32_t), cudaMemcpyHostToDevice, h->st);
+        if (e != cudaSuccess) {
+            dfree(dsrc, h->st);
+            CK(e);
+        }
+    }
+    const gapsp_status gs = certify_rows(h, D, dsrc, K, h->st, bad);
+    dfree(dsrc, h->st);
+    return gs;
+}
 
 gapsp_status gapsp_cancel(gapsp_handle* h) {
     if (!h) return GAPSP_E_INVALID;

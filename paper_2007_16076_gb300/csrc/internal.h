@@ -210,6 +210,19 @@ struct CompArgs {
 cudaError_t launch_components(const CompArgs& a, cudaStream_t st);
 
 cudaError_t launch_unreach_convert(uint32_t* rows, size_t n, cudaStream_t st);
+
+// The certificate of a result (certify.cu): row k of D (rows x N, row-major)
+// holds d(src[k], .) (src NULL: k); bad counts the entries that break
+// d(p,p) = 0, d(p,r) = min over neighbours q of d(p,q) + w(q,r).
+struct CertifyArgs {
+    const uint32_t* D;
+    int rows;
+    const int32_t* src;
+    int H, W, N, conn, kind;
+    const uint8_t* f;           // levels (16-bit for kind 3) or free flags
+    unsigned long long* bad;
+};
+cudaError_t launch_certify(const CertifyArgs& a, cudaStream_t st);
 // F(p) = sum over the L channels (planes of N bytes) of the levels of p.
 cudaError_t launch_channel_sum(const uint8_t* planes, int L, int N, uint16_t* F, cudaStream_t st);
 

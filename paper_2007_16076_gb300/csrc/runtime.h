@@ -19,6 +19,8 @@ struct gapsp_handle {
     int prop_blocks = 0;
     int lookahead = 0;  // option: 0 auto, -1 off, else candidates per round
     bool warm = true;   // option: propagations start from complete neighbour rows
+    bool checked = false;  // option: certify every result (certify.cu)
+    unsigned long long* bad = nullptr;  // certificate's violation count
     int max_sweep_rounds = 0;  // option: 0 = N + 2
     int max_rounds = 0;        // option: 0 = N + 66
     std::atomic<int> cancel{0};  // gapsp_cancel: stop the all-pairs call in progress
@@ -129,6 +131,12 @@ void dfree(T*& p, cudaStream_t st) {
 // Pinned host words (four per call) from a process-wide pool.
 cudaError_t halloc(int** p);
 void hfree(int*& p);
+
+// Certificate of K rows of D on stream st (row k = d(src[k], .), src a
+// device array or NULL for rows 0..K-1): *bad receives the count of
+// entries that break the distance equations.
+gapsp_status certify_rows(gapsp_handle* h, const uint32_t* D, const int32_t* src, int K, cudaStream_t st,
+                          uint64_t* bad);
 
 // Propagation arguments common to every launch on this handle.
 PropArgs base_prop(const gapsp_handle* h);

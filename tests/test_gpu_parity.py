@@ -434,6 +434,10 @@ def test_full_size_256(gp, name, factory, order):
     idx = torch.from_numpy(rows).long().cuda()
     assert np.array_equal(_u32(D[idx]), ref)
     assert np.array_equal(_u32(D[:, idx]).T, ref)
+    # the whole array, certified on the device: every entry satisfies the
+    # distance equations, which only the exact distances do
+    with gp.Image(img, conn=w.conn, kind=w.kind, mask=w.mask) as im:
+        assert im.certify(D) == 0
     del D
     torch.cuda.empty_cache()
 
@@ -577,3 +581,43 @@ def test_channels_largest_levels(gp):
     with pytest.raises(gp.GapspError) as e:
         gp.Image(np.zeros((33, 8, 8), np.uint8), conn=8, kind="sum")
     assert e.value.code == 1
+
+
+# --------------------------------------------------------------------------
+# Certificate of a result (gapsp_certify, opts.checked)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind", ["grey", "mask", "l1", "sum"])
+@pytest.mark.parametrize("conn", [4, 8])
+def test_certify_detects_wrong_entries(gp, kind, conn):
+    """Exact arrays and rows certify with no violation; one entry made too
+    large or too small, or a wrong unreachable marker, is caught."""
+    import torch
+    H, W = 23, 19
+    mask = synth.disk_mask(H, W, 0.3, 1, 3, seed=conn) if kind == "mask" else None
+    if kind == "sum":
+        img = _channels(3, H, W, seed=conn)
+    else:
+        img = synth.blobs(H, W, 3, 3.0, 55.0, seed=conn)
+    with gp.Image(None if kind == "mask" else img, conn=conn, kind=kind, mask=mask, B=8, checked=1) as im:
+        D, _ = im.all_pairs("minfill")  # checked: certified before it returns
+        assert im.certify(D) == 0
+        src = np.array([0, 7, 100, H * W - 1], dtype=np.int32)
+        R = im.rows(src)
+        assert im.certify(R, src) == 0
+        N = H * W
+        free = np.arange(N) if mask is None else np.flatnonzero(mask.reshape(-1))
+        p = int(free[3])
+        Dh = _u32(D)
+        joined = np.flatnonzero((Dh[p] != 0xFFFFFFFF) & (np.arange(N) != p))
+        q = int(joined[-1])  # a pixel a path joins to p
+        for delta in (1, -1):
+            E = D.clone()
+            E[p, q] = int(Dh[p, q]) + delta
+            assert im.certify(E) >= 1
+        E = D.clone()
+        E[p, q] = -1  # UNREACH where a path exists
+        assert im.certify(E) >= 1
+        E = R.clone()
+        E[1, 7] = 3  # the source's own entry
+        assert im.certify(E, src) >= 1
