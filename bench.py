@@ -48,6 +48,8 @@ def _args():
                     help="length of the simulated serving run among the side measurements")
     ap.add_argument("--timed-only", action="store_true",
                     help="warm-up and timed steps only (for profiler runs); prints no JSON")
+    ap.add_argument("--options", default=None, metavar="B,LOOKAHEAD,FILL_ROWS",
+                    help="launch options instead of the autotuner's (for profiler runs)")
     return ap.parse_args()
 
 
@@ -598,7 +600,11 @@ def run_ours(a):
     # the launch options come from the autotuner (B is free for this image;
     # the fixed B = 32 is timed among the side measurements)
     t_tune = time.perf_counter()
-    tuned = _tune(gp, w)
+    if a.options:
+        B, la, fr = (int(x) for x in a.options.split(","))
+        tuned = {"B": B, "lookahead": la, "fill_rows": fr}
+    else:
+        tuned = _tune(gp, w)
     t_tune = time.perf_counter() - t_tune
     im = _image(gp, w, stream, **tuned)
     D = torch.empty((N, N), dtype=torch.int32, device="cuda")
@@ -703,7 +709,7 @@ def run_ours(a):
             "config": {"workload": w.name.replace("-B32", ""), "H": w.H, "W": w.W, "N": N,
                        "conn": w.conn, "B": tuned["B"], "lookahead": tuned["lookahead"],
                        "fill_rows": tuned["fill_rows"],
-                       "options_from": f"gapsp_tune ({t_tune:.1f} s, cache {TUNE_CACHE})",
+                       "options_from": "--options" if a.options else f"gapsp_tune ({t_tune:.1f} s, cache {TUNE_CACHE})",
                        "kind": w.kind, "order": "minfill", "parallelism": f"replicas{world}",
                        "l2": f"256 MiB buffer written between steps; D ({4 * N * N / 1e9:.2f} GB) "
                              "exceeds L2"},

@@ -96,7 +96,15 @@ typedef struct {
     uint64_t seed;     /* seed of the spiral orders' draws */
     size_t mem_budget; /* bytes of device memory a call may use (0 = no limit) */
     int sweep_phases;  /* warps per sweep direction in a propagation: 0 = auto, 1, 2 or 4 */
-    int fill_rows;     /* rows of marks per tree-fill block: 0 = auto, else 1..32 */
+    int fill_rows;     /* tree fill variant (D is the same for all):
+                          0 = marks claimed in global memory (the default);
+                          1..32 = rows of marks staged in shared memory per block;
+                          -1 = every round walks in lockstep, one warp per half
+                               tile and tree (slower; for comparison);
+                          -2 = as 0, but the first round walks in lockstep and
+                               writes one side of each pair, and one pass over D
+                               mirrors it (pays when the first round fills most
+                               pairs: many sources per round, B >= 128) */
     int checked;       /* 1: certify every result before returning it (gapsp_certify on the
                           whole D or on the rows; about one more read of the array);
                           a result that fails returns GAPSP_E_CHECK. 0: off */
@@ -282,10 +290,11 @@ uint64_t gapsp_kernel_launches(const gapsp_handle *h);
  * segments and depths (a'), 3 lookahead propagations (on the second stream,
  * overlapping the others), 4 tree fill (b), 5 init, 6 extrema pre-pass
  * helpers, 7 depth sums of the trees (N <= 16384, on a third stream), 8
- * fill-count update.
+ * fill-count update, 9 completion of a one-sided first round (the mirror
+ * pass).
  * ms and launches: caller-owned arrays of GAPSP_NUM_KERNELS entries.
  */
-#define GAPSP_NUM_KERNELS 9
+#define GAPSP_NUM_KERNELS 10
 gapsp_status gapsp_profile_enable(gapsp_handle *h, int enable);
 gapsp_status gapsp_profile_read(gapsp_handle *h, double *ms, uint64_t *launches);
 /* Like gapsp_profile_read, and also returns the individual launches in
@@ -330,7 +339,8 @@ gapsp_status gapsp_rows_noalloc(const uint8_t *img, int H, int W, int conn, gaps
  * the time and the counts of B > 1 change. Measures, on the image given, a
  * fill in `order` for every candidate of B in {16, 32, 64, 128, 256}, lookahead on
  * (0) or off (-1) and the tree fill with global marks (fill_rows 0) or rows
- * of marks staged in shared memory (8), and returns in *best the options
+ * of marks staged in shared memory (8), and for B >= 128 also the one-sided
+ * first round (fill_rows -2), and returns in *best the options
  * of *base (NULL: the defaults) with the fastest candidate's B, lookahead
  * and fill_rows; *best_ms (may be NULL) receives its device time.
  *   img, mask : as gapsp_create (host or device).

@@ -20,7 +20,7 @@ from . import _build
 UNREACH = 0xFFFFFFFF
 ORDERS = {"naive": 0, "spiral": 1, "minfill": 2, "extrema": 3, "repulsion": 4}
 KINDS = {"grey": 0, "mask": 1, "l1": 2, "sum": 3}
-KERNELS = ("select", "propagate", "tree", "lookahead", "fill", "init", "prepass", "depths", "recount")
+KERNELS = ("select", "propagate", "tree", "lookahead", "fill", "init", "prepass", "depths", "recount", "mirror")
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "memory budget exceeded",
           4: "CUDA runtime error", 5: "propagation did not converge", 6: "round limit exceeded",
           7: "cancelled", 8: "result failed its certificate"}

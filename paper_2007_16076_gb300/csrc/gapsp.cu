@@ -340,7 +340,7 @@ void free_all(gapsp_handle* h) {
 }
 
 enum { K_SELECT = 0, K_PROP = 1, K_TREE = 2, K_AHEAD = 3, K_FILL = 4, K_INIT = 5, K_PRE = 6, K_DEPTH = 7,
-       K_RECOUNT = 8 };
+       K_RECOUNT = 8, K_MIRROR = 9 };
 
 cudaEvent_t pool_get(gapsp_handle* h) {
     if (!h->pool.empty()) {
@@ -429,7 +429,7 @@ static gapsp_status create_handle(const uint8_t* img, int L, int H, int W, const
         return GAPSP_E_INVALID;
     if (o.B < 1 || o.B > 1024) return GAPSP_E_INVALID;
     if (o.sweep_phases < 0 || o.sweep_phases > 4 || o.sweep_phases == 3) return GAPSP_E_INVALID;
-    if (o.fill_rows < 0 || o.fill_rows > 32) return GAPSP_E_INVALID;
+    if (o.fill_rows < -2 || o.fill_rows > 32) return GAPSP_E_INVALID;
     if (o.prop_blocks != 0 && o.prop_blocks != 1 && o.prop_blocks != 2 && o.prop_blocks != 4)
         return GAPSP_E_INVALID;
     if (o.lookahead < -1 || o.lookahead > 1024) return GAPSP_E_INVALID;
@@ -717,6 +717,8 @@ gapsp_status fill_begin(FillRun& r) {
     // D starts as UNREACH everywhere when a mask may leave pairs unjoined,
     // and when propagations start warm from it
     InitArgs ia{h->N, Dd, h->cnt, h->comp, h->comp_size, h->kind == GAPSP_MASK || h->warm};
+    // (the mirror pass tells the missing side of a pair by its UNREACH)
+    r.one_side_first = h->fill_rows == -2 && ia.full_init;
     {
         ProfScope ps(h, K_INIT, s);
         CK(launch_init(ia, s));
@@ -809,7 +811,8 @@ gapsp_status fill_begin(FillRun& r) {
         ta.rows_per_block = rpb < 1 ? 1 : (rpb > 8 ? 8 : rpb);
         if (h->fill_rows) ta.rows_per_block = h->fill_rows;
         if ((size_t)ta.rows_per_block * row_bytes > 200 * 1024) ta.rows_per_block = rpb < 1 ? 1 : rpb;
-        if (!h->fill_rows) ta.rows_per_block = 0;  // marks claimed in global memory
+        if (h->fill_rows == 0 || h->fill_rows == -2) ta.rows_per_block = 0;  // marks claimed in global memory
+        if (h->fill_rows == -1) ta.rows_per_block = -1;                      // walks in lockstep
     }
     r.rounds = 0;
     r.finished = false;
@@ -898,9 +901,29 @@ gapsp_status fill_enqueue(FillRun& r, int chunk, bool graph) {
             ProfScope ps(h, K_TREE, s);
             CK(launch_tree(r.ta, h->B, s, true));
         }
+        // the first round, when it fills most pairs, writes one side of each
+        // (the walks in lockstep: whole runs of entries), and the mirror
+        // completes the other side before the next round's propagations read
+        // rows of the array
+        const bool one_side = r.one_side_first && r.rounds + i == 0;
         {
             ProfScope ps(h, K_FILL, s);
-            CK(launch_fill(r.ta, h->B, s, true));
+            if (one_side) {
+                TreeArgs t1 = r.ta;
+                t1.rows_per_block = -1;
+                t1.one_side = 1;
+                CK(launch_fill(t1, h->B, s, true));
+            } else {
+                CK(launch_fill(r.ta, h->B, s, true));
+            }
+        }
+        if (one_side) {
+            // no propagation of this round's lookahead may write the array
+            // meanwhile: only exact distances are there to mirror
+            if (r.K > 0) CK(cudaStreamWaitEvent(s, r.e_ahead[par], 0));
+            ProfScope ps(h, K_MIRROR, s);
+            CK(launch_mirror(r.ta.Dw, h->N, s));
+            h->launches += 1;
         }
         {
             ProfScope ps(h, K_RECOUNT, s);

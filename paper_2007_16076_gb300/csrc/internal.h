@@ -100,7 +100,8 @@ struct TreeArgs {
     const int32_t* tbase;       // [words]: top-left pixel of each tile
     int32_t* parent;            // [B][N] (N > 16384 only)
     ulonglong2* seg;            // [B][N]: x = mask of the tile segment; y = exit vertex + 1
-                                // (0 past the root) | tile of the exit << 32
+                                // (0 past the root, bits 0-16) | its tile (bits 17-26), and
+                                // the same for the next segment's exit (bits 27-53)
     int32_t* jmp;               // [2][B][N] scratch for the depth pointer jumping
     int32_t* acc;               // [2][B][N] scratch for the depth pointer jumping
     unsigned long long* marks;  // [N][words]
@@ -108,7 +109,8 @@ struct TreeArgs {
     const uint32_t* cnt_base;   // [N] fill count at the start (1 + pairs no path joins)
     uint32_t* Dw;               // writable array for new pairs
     unsigned long long* stats;  // StatSlot counters
-    int rows_per_block;
+    int rows_per_block;         // 0: marks in global memory; -1: walks in lockstep; else staged rows
+    int one_side;               // lockstep only: write D[a][b] (a the ancestor) and not D[b][a]
     // N <= 16384: the depth sums are left to k_depths; the tree hands it the
     // segment exits (+1) and segment sizes of each tree, and the tree count
     uint16_t* dep_exit;         // [B][N] or NULL (then the tree sums depths itself)
@@ -128,6 +130,8 @@ __host__ __device__ inline size_t fill_smem_bytes(int rows, int words) {
     return (size_t)rows * (fill_row_stride(words) * 8 + fill_chg_stride(words));
 }
 cudaError_t launch_recount(const TreeArgs& a, cudaStream_t st, bool pdl = false);
+// Completes the pairs a one-sided fill left: D[i][j] = D[j][i] where only one is known.
+cudaError_t launch_mirror(uint32_t* D, int N, cudaStream_t st);
 
 struct SelectArgs {
     int N, B, order;            // 0 naive / 1 spiral (sequence), 2 minfill, 3 extrema

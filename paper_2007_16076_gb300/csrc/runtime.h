@@ -162,6 +162,7 @@ struct FillRun {
     bool finished = false;
     bool graphed = false;  // its chunks run as a captured graph (gapsp_all_pairs_batch)
     int sm_share = 0;      // multiprocessors the fill plans its lookahead for (0: all)
+    bool one_side_first = false;  // the first round writes one side of its pairs, then mirrors them
     // lookahead: the next K candidates of each round are propagated on a
     // second stream while the round's tree and fill run
     int K = 0;

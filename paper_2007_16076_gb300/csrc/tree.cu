@@ -774,6 +774,173 @@ __global__ void __launch_bounds__(128, FILL_G_MINB) k_fill_g(TreeArgs a, int qua
     }
 }
 
+__device__ __forceinline__ unsigned long long warp_or64(unsigned long long v) {
+    const unsigned lo = __reduce_or_sync(FULL, (unsigned)v), hi = __reduce_or_sync(FULL, (unsigned)(v >> 32));
+    return (unsigned long long)hi << 32 | lo;
+}
+
+// The same fill with the walks of one warp in lockstep. A warp owns one tree
+// and the 32 pixels of half an 8x8 tile (4 rows of 8: lane l is bit
+// 32q + l of the tile's mark word), whose paths to the root soon merge. The
+// walks advance one segment at a time, farthest from the root first: each
+// step takes the lanes whose segment entry has the largest d(s, .) (and the
+// leader's tile), so lanes whose paths have merged reach the shared segments
+// together (d(s, .) falls strictly along a path) and take them in the same
+// instructions. The new pairs of a step are then written per ancestor a for
+// all its lanes at once: the column stores D[a][b] of the lanes form whole
+// runs of 8 entries, and the mirror bits (row a, columns b) one 64-bit OR,
+// the lanes' ballot shifted to the half tile. The first segment (inside the
+// lanes' own tile) is taken by all lanes together. With one_side set, only
+// D[a][b] is written (a pass of k_mirror completes D[b][a] afterwards).
+__global__ void __launch_bounds__(128, FILL_G_MINB) k_fill_l(TreeArgs a, int B) {
+    pdl_wait();
+    pdl_trigger();
+    const int nsel = *a.nsel;
+    if (nsel == 0) return;
+    const int lane = threadIdx.x & 31;
+    const long long warp = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int half = (int)(warp / B), j = (int)(warp - (long long)half * B);
+    const int t0 = half >> 1, q = half & 1;
+    if (j >= nsel || t0 >= a.words) return;  // uniform over the warp
+    const int tr = t0 / a.tiles_w, tc = t0 - tr * a.tiles_w;
+    const int r = tr * 8 + q * 4 + (lane >> 3), c = tc * 8 + (lane & 7);
+    const int s = a.sel[j];
+    const uint32_t srow = (uint32_t)s * (uint32_t)a.N;
+    bool on = r < a.H && c < a.W;
+    const int b = on ? r * a.W + c : 0;
+    uint32_t db = 0;
+    if (on) on = b != s && __ldcg(a.cnt + b) < (uint32_t)a.N;
+    if (on) {
+        db = __ldg(a.D + srow + b);
+        on = db != UNREACH;
+    }
+    if (!__any_sync(FULL, on)) return;
+    const uint32_t brow = (uint32_t)b * (uint32_t)a.N, mrow = (uint32_t)b * (uint32_t)a.words;
+    const int mshift = q * 32;
+    const ulonglong2* seg = a.seg + (size_t)j * a.N;
+    // the lane's current segment: tile t, ancestor bits m, row b's mark word
+    // w for t, the record's exits y and the key d(s, entry) + 1 (0: the walk
+    // is over; all ones: the first segment)
+    int t = t0;
+    unsigned long long m = 0, w = 0, y = 0;
+    uint32_t key = 0;
+    if (on) {
+        const ulonglong2 g = __ldg(seg + b);
+        m = g.x & ~(1ull << (mshift + lane));
+        y = g.y;
+        w = ld_cg64(a.marks + mrow + t0);
+        key = 0xFFFFFFFFu;
+    }
+    // the segment after it, fetched one step ahead
+    int tn = 0;
+    unsigned long long mn = 0, wn = 0, yn = 0;
+    uint32_t keyn = 0;
+    auto fetch = [&]() {
+        const int e1 = (int)(y & 0x1FFFFu) - 1;
+        keyn = 0;
+        if (key != 0 && e1 >= 0) {
+            tn = (int)((y >> 17) & 0x3FFu);
+            const ulonglong2 g = __ldg(seg + e1);
+            mn = g.x;
+            yn = g.y;
+            wn = ld_cg64(a.marks + mrow + tn);
+            keyn = __ldg(a.D + srow + e1) + 1;
+        }
+    };
+    fetch();
+    // every step advances at least one lane by one segment, and the keys of a
+    // lane fall strictly: at most 32 N steps
+    for (long long guard = 0; guard <= 32LL * a.N; ++guard) {
+        const uint32_t K = __reduce_max_sync(FULL, key);
+        if (K == 0) break;
+        const int lead = __ffs(__ballot_sync(FULL, key == K)) - 1;
+        const int tl = __shfl_sync(FULL, t, lead);
+        const bool go = key == K && t == tl;
+        unsigned long long nb = go ? m & ~w : 0ull;
+        if (nb) nb &= ~atomicOr(a.marks + mrow + t, nb);
+        unsigned long long U = warp_or64(nb);
+        if (U) {
+            const int base = __ldg(a.tbase + tl);
+            while (U) {
+                int ap[4], bit[4];
+                uint32_t dv[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    ap[k] = -1;
+                    if (U) {
+                        bit[k] = __ffsll((long long)U) - 1;
+                        U &= U - 1;
+                        ap[k] = base + (bit[k] >> 3) * a.W + (bit[k] & 7);
+                        dv[k] = __ldg(a.D + srow + ap[k]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (ap[k] < 0) continue;
+                    const bool has = (nb >> bit[k]) & 1;
+                    const unsigned bal = __ballot_sync(FULL, has);
+                    if (has) {
+                        const uint32_t val = db - dv[k];
+                        if (!a.one_side) __stcs(a.Dw + brow + ap[k], val);
+                        __stcs(a.Dw + (uint32_t)ap[k] * (uint32_t)a.N + b, val);
+                    }
+                    if (lane == 0)
+                        atomicOr(a.marks + (uint32_t)ap[k] * (uint32_t)a.words + t0, (unsigned long long)bal << mshift);
+                }
+            }
+        }
+        if (go) {
+            t = tn;
+            m = mn;
+            w = wn;
+            y = yn;
+            key = keyn;
+            fetch();
+        }
+    }
+}
+
+// After a fill round that wrote only D[a][b] of its pairs (a the ancestor):
+// every entry still UNREACH whose mirror is known takes the mirror's value
+// (the distance is symmetric). The array starts as UNREACH, and no launch
+// that writes anything but exact distances into it runs meanwhile, so a
+// known entry is exact and an entry written concurrently gets the same
+// value. Tiles of 64 x 64 entries in pairs (I, J), I <= J, through shared
+// memory: every entry is read once, only the missing ones are written.
+constexpr int MT = 64;
+
+__global__ void __launch_bounds__(256) k_mirror(uint32_t* D, int N) {
+    __shared__ uint32_t sa[MT][MT + 1], sb[MT][MT + 1];
+    const long long T = (N + MT - 1) / MT, pairs = T * (T + 1) / 2;
+    const int tx = threadIdx.x & (MT - 1), ty = threadIdx.x / MT;
+    auto start = [T](long long i) { return i * T - i * (i - 1) / 2; };  // first pair of tile row i
+    for (long long k = blockIdx.x; k < pairs; k += gridDim.x) {
+        const double u = 2.0 * T + 1.0;
+        long long I = (long long)((u - sqrt(u * u - 8.0 * (double)k)) * 0.5);
+        I = I < 0 ? 0 : (I >= T ? T - 1 : I);
+        while (I > 0 && start(I) > k) --I;
+        while (I + 1 < T && start(I + 1) <= k) ++I;
+        const long long J = I + (k - start(I));
+        const int i0 = (int)(I * MT), j0 = (int)(J * MT);
+#pragma unroll 4
+        for (int r = ty; r < MT; r += 256 / MT) {
+            const int i = i0 + r, j = j0 + tx, i2 = j0 + r, j2 = i0 + tx;
+            sa[r][tx] = (i < N && j < N) ? __ldcs(D + (size_t)i * N + j) : UNREACH;
+            sb[r][tx] = (I != J && i2 < N && j2 < N) ? __ldcs(D + (size_t)i2 * N + j2) : UNREACH;
+        }
+        __syncthreads();
+        const uint32_t (*mb)[MT + 1] = I != J ? sb : sa;  // the mirror of tile (I, J)
+#pragma unroll 4
+        for (int r = ty; r < MT; r += 256 / MT) {
+            const int i = i0 + r, j = j0 + tx, i2 = j0 + r, j2 = i0 + tx;
+            if (i < N && j < N && sa[r][tx] == UNREACH && mb[tx][r] != UNREACH) D[(size_t)i * N + j] = mb[tx][r];
+            if (I != J && i2 < N && j2 < N && sb[r][tx] == UNREACH && sa[tx][r] != UNREACH)
+                D[(size_t)i2 * N + j2] = sa[tx][r];
+        }
+        __syncthreads();
+    }
+}
+
 // Fill counts of the rows still open: cnt(x) = cnt at the start + the
 // number of marked pairs of row x (both bits of a pair are set, so row x
 // holds every filled pair {x, y}). One warp per row; rows already filled
@@ -903,7 +1070,19 @@ cudaError_t launch_depths(const TreeArgs& a, int B, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_mirror(uint32_t* D, int N, cudaStream_t st) {
+    const long long T = (N + MT - 1) / MT, pairs = T * (T + 1) / 2;
+    const long long grid = pairs < 152 * 6 ? pairs : 152 * 6;
+    k_mirror<<<(unsigned)grid, 256, 0, st>>>(D, N);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fill(const TreeArgs& a, int B, cudaStream_t st, bool pdl) {
+    if (a.rows_per_block < 0) {
+        // walks in lockstep: one warp per half tile and tree
+        const long long warps = 2LL * a.words * B;
+        return launch_ex(k_fill_l, (int)((warps + 3) / 4), 128, 0, st, pdl, 1, a, B);
+    }
     if (a.rows_per_block == 0) {
         // marks claimed in global memory: one warp per 8 rows x 4 trees
         const int quads = (B + 3) / 4;

@@ -7,7 +7,8 @@
 // cost more propagations),
 // whether rows are computed ahead (the lookahead launches), and how the tree
 // fill claims its pairs (marks in global memory, or rows of marks staged in
-// shared memory). Each candidate fills the caller's image once after a
+// shared memory; with B >= 128 also the first round written one-sided and
+// mirrored, which only pays when that round fills most pairs). Each candidate fills the caller's image once after a
 // warm-up fill, timed with events on a stream of its own; the fastest wins.
 // Results are kept in a text cache, one line per key (H, W, conn, kind,
 // order, multiprocessor count), so that each shape is measured once.
@@ -119,11 +120,12 @@ extern "C" gapsp_status gapsp_tune(const uint8_t* img, const uint8_t* mask, int 
         }
         const int Bs[] = {16, 32, 64, 128, 256};
         const int looks[] = {0, -1};
-        const int fills[] = {0, 8};
+        const int fills[] = {0, 8, -2};
         c.ms = -1.0;
         for (int B : Bs)
             for (int la : looks)
                 for (int fr : fills) {
+                    if (fr == -2 && B < 128) continue;
                     gapsp_opts t = o;
                     t.B = B;
                     t.lookahead = la;

@@ -347,7 +347,7 @@ def test_full_size_blobs128(gp, order):
 # one value per lane where the width is not a multiple of 4)
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("fill_rows", [0, 1, 8])
+@pytest.mark.parametrize("fill_rows", [0, -1, -2, 1, 8])
 @pytest.mark.parametrize("shape,conn,kind", [((29, 31), 8, "grey"), ((40, 24), 4, "mask"), ((136, 121), 8, "grey")])
 def test_fill_variants(gp, shape, conn, kind, fill_rows):
     """The tree fill with the marks claimed in global memory (fill_rows 0,
@@ -401,15 +401,17 @@ def _with_B(w, B):
     return w
 
 
-@pytest.mark.parametrize("name,factory,order", [("steps256", synth.steps_256, o) for o in
-                                               ("minfill", "naive", "spiral", "extrema", "repulsion")] +
-                         [("mask256", synth.mask_256, "minfill"),
-                          ("steps256_B256", lambda seed: _with_B(synth.steps_256(seed), 256), "minfill")])
-def test_full_size_256(gp, name, factory, order):
+@pytest.mark.parametrize("name,factory,order,fill_rows", [("steps256", synth.steps_256, o, 0) for o in
+                                                         ("minfill", "naive", "spiral", "extrema", "repulsion")] +
+                         [("mask256", synth.mask_256, "minfill", 0),
+                          ("steps256_B256", lambda seed: _with_B(synth.steps_256(seed), 256), "minfill", 0),
+                          ("steps256_B256", lambda seed: _with_B(synth.steps_256(seed), 256), "minfill", -2)])
+def test_full_size_256(gp, name, factory, order, fill_rows):
     """256x256, 8-connected, B = 32 (the benchmark's workload, every order;
-    and the obstacle mask): the counts against the oracle's stored
-    simulation, sampled rows and columns of D against Dijkstra, and symmetry
-    of the sampled entries."""
+    and the obstacle mask), and B = 256 with the default fill and with the
+    one-sided first round: the counts against the oracle's stored
+    simulation, sampled rows and columns of D against Dijkstra, and the
+    whole array certified."""
     import torch
     path = os.path.join(GOLDEN, f"counts_{name}.json")
     if not os.path.exists(path):
@@ -422,7 +424,7 @@ def test_full_size_256(gp, name, factory, order):
     N = w.N
     img = w.img if w.kind == "grey" else None
     D = torch.empty((N, N), dtype=torch.int32, device="cuda")
-    with gp.Image(img, conn=w.conn, kind=w.kind, mask=w.mask, B=w.B, seed=0) as im:
+    with gp.Image(img, conn=w.conn, kind=w.kind, mask=w.mask, B=w.B, seed=0, fill_rows=fill_rows) as im:
         _, st = im.all_pairs(order, out=D, want_log=True)
     for k in ("propagations", "prepass_propagations", "distance_ops", "new_pairs", "rounds"):
         assert st[k] == gold[k], k
@@ -446,16 +448,18 @@ def test_full_size_256(gp, name, factory, order):
 # Batched form: many images of uneven sizes side by side
 # --------------------------------------------------------------------------
 
-def test_all_pairs_batch_equals_alone(gp):
+@pytest.mark.parametrize("fill_rows", [0, -2])
+def test_all_pairs_batch_equals_alone(gp, fill_rows):
     """Each image of a batch gets the array and counts it gets alone
-    (images of uneven sizes, 4- and 8-connected, one mask)."""
+    (images of uneven sizes, 4- and 8-connected, one mask; the default fill
+    and the one-sided first round, whose mirror pass is captured too)."""
     rng = np.random.default_rng(4)
     specs = []
     for k in range(6):
         H, W = int(rng.integers(5, 30)), int(rng.integers(5, 30))
         specs.append((synth.blobs(H, W, 3, 2.5, 55.0, seed=k), None, 4 if k % 2 else 8))
     specs.append((None, synth.disk_mask(21, 26, 0.4, 2, 3, seed=9), 8))
-    ims = [gp.Image(img, conn=c, kind="grey" if m is None else "mask", mask=m, B=4)
+    ims = [gp.Image(img, conn=c, kind="grey" if m is None else "mask", mask=m, B=4, fill_rows=fill_rows)
            for img, m, c in specs]
     try:
         outs, stats = gp.all_pairs_batch(ims, "minfill")
@@ -508,7 +512,7 @@ def test_tune_picks_a_candidate_and_caches(gp, tmp_path):
     img = synth.scaled_blobs(40, 44, 8, seed=3).img
     cache = tmp_path / "tune.txt"
     t = gp.tune(img, conn=8, cache=cache)
-    assert t["B"] in (16, 32, 64, 128, 256) and t["lookahead"] in (0, -1) and t["fill_rows"] in (0, 8)
+    assert t["B"] in (16, 32, 64, 128, 256) and t["lookahead"] in (0, -1) and t["fill_rows"] in (0, 8, -2)
     assert t["ms"] > 0
     lines = cache.read_text().splitlines()
     assert len(lines) == 1 and lines[0].startswith("gapsp-tune-2 40 44 8 0 2 ")
