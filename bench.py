@@ -140,10 +140,11 @@ class Clocks:
 # the dominant kernel per workload, from an ncu capture, with the launch it
 # came from; None when no capture of the kernel as it stands exists.
 DRAM_BYTES = {
-    # k_fill_g at 256x256 step edges with the tuned options (B = 256), the
-    # launch of round 8 (ncu, one pass, cold caches, commit f232e2c): 2.54 GB
-    # read + 0.589 GB written, for 41422102 new pairs (8 B each) in that round
-    "steps256": {"kernel": "k_fill", "bytes": 3129.18e6, "launch": "round 8",
+    # k_fill_g at 256x256 step edges with the tuned options (B = 256, one-sided
+    # first round), the launch of round 8 (ncu, one pass, cold caches, commit
+    # b324177): 2.490 GB read + 0.590 GB written, for 41422102 new pairs (8 B
+    # each) in that round
+    "steps256": {"kernel": "k_fill", "bytes": 3080.22e6, "launch": "round 8",
                  "launch_algorithmic_bytes": 331.4e6},
 }
 
@@ -410,8 +411,10 @@ def roofline(w, st, prof, ms_per_step, peaks, dram=None) -> dict:
     device time `prof` ({kernel: (ms, launches)}) of `nfill` profiled fills.
 
     - step: the array itself, 4 N^2 bytes written once per fill, over the step time;
-    - fill (k_fill): 8 bytes per new pair (D[a][b] and D[b][a]) over the fill
-      launches' time: the kernel's algorithmic DRAM bytes;
+    - fill (k_fill_g; k_fill_l and the k_mirror pass that completes it, when
+      the first round is written one-sided): 8 bytes per new pair (D[a][b]
+      and D[b][a]) over the time of the fill launches and the mirror pass:
+      the kernels' algorithmic DRAM bytes;
     - propagate (k_propagate_*, the rounds' own launches and the lookahead
       launches): 2 conn relaxations per free pixel (every edge once from each
       end) for each of the method's own P + 2 propagations, over the time of
@@ -428,12 +431,15 @@ def roofline(w, st, prof, ms_per_step, peaks, dram=None) -> dict:
             "unit": "GB/s", "algorithmic_bytes": 4.0 * N * N, "peak_source": peak_src}
     step["frac"] = step["achieved"] / hbm
     fill_ms, fill_n = prof["fill"]
+    mirror_ms = prof.get("mirror", (0.0, 0))[0]
+    fill_ms += mirror_ms
     alg_fill = 8.0 * st["new_pairs"] * nfill
     fill = {"kernel": "k_fill", "bound": "hbm",
             "achieved": alg_fill / (fill_ms / 1e3) / 1e9 if fill_ms else 0.0, "peak": hbm,
             "unit": "GB/s", "peak_source": peak_src,
             "algorithmic_bytes_per_launch": alg_fill / max(fill_n, 1),
-            "avg_launch_ms": fill_ms / max(fill_n, 1), "traffic": None}
+            "avg_launch_ms": fill_ms / max(fill_n, 1), "traffic": None,
+            "mirror_ms_per_fill": mirror_ms / nfill}
     fill["frac"] = fill["achieved"] / hbm
     ghz = (peaks.get("sm_max_mhz") or 2070.0) / 1e3
     peak_relax = 152 * 128 * ghz * 1e9 / 2 / 1e12
