@@ -359,9 +359,12 @@ __global__ void __launch_bounds__(1024) k_treeC(TreeArgs a) {
 // k_treeC, with 32-bit parents and exits, and the depth sums done in place:
 // pointer jumping over the segment exits, each block owning its strip's
 // entries and reading the others' through distributed shared memory, one
-// cluster barrier per jump. Shared memory: the staged D rows (later the
+// cluster barrier per jump. Only the vertices that are some segment's exit
+// (the entries of segments) take part in the jumps; every other vertex adds
+// its exit's sum once at the end. An exit is kept as (owning block << 20 |
+// index in its strip) + 1. Shared memory: the staged D rows (later the
 // second exit buffer), the staged image, the parents (later the second
-// count buffer), the first count and exit buffers.
+// count buffer), the first count and exit buffers, the entry flags.
 struct TreeWLayout {
     int hs, smax, pmax;
     size_t o_par;  // byte offset of the parents
@@ -371,7 +374,7 @@ struct TreeWLayout {
         pmax = hs * W;
         o_par = ((size_t)smax * (4 + lvb) + 15) & ~(size_t)15;
     }
-    __host__ __device__ size_t bytes() const { return o_par + (size_t)pmax * 12 + 16; }
+    __host__ __device__ size_t bytes() const { return o_par + (size_t)pmax * 13 + 16; }
 };
 
 template <int C>
@@ -396,6 +399,7 @@ __global__ void __launch_bounds__(1024) k_treeW(TreeArgs a) {
     uint32_t* spar = reinterpret_cast<uint32_t*>(smw + L.o_par);
     uint32_t* accA = spar + L.pmax;
     uint32_t* jxA = accA + L.pmax;
+    uint8_t* entry = reinterpret_cast<uint8_t*>(jxA + L.pmax);  // is some segment's exit
     uint32_t* accB = spar;  // the parents are not needed once the segments are done
     uint32_t* jxB = srow;   // nor the staged rows once the parents are
     const uint32_t* drow = a.D + (size_t)s * N;
@@ -403,7 +407,8 @@ __global__ void __launch_bounds__(1024) k_treeW(TreeArgs a) {
     if (threadIdx.x == 0) { s_more[0] = 0; s_more[1] = 0; }
     for (int v = threadIdx.x; v < S; v += blockDim.x) srow[v] = __ldcg(drow + base + v);
     stage_levels(a, sf, base, S);
-    __syncthreads();
+    for (int i = threadIdx.x; i < P; i += blockDim.x) entry[i] = 0;
+    cl.sync();  // every strip's flags are clear before any block marks them
     // parents of the owned pixels (neighbours within the staged rows); parent
     // + 1, 0 for the root, all ones for unreached pixels
     const uint32_t* drow_l = srow - base;
@@ -431,17 +436,26 @@ __global__ void __launch_bounds__(1024) k_treeW(TreeArgs a) {
         const bool reached = sv != 0xFFFFFFFFu;
         reinterpret_cast<unsigned long long*>(seg + v)[0] = m;
         accA[i] = reached ? (uint32_t)__popcll(m) : 0u;
-        jxA[i] = reached ? (uint32_t)(x + 1) : 0u;
+        uint32_t jx = 0;
+        if (reached && x >= 0) {
+            const int re = min(row_of(a, x) / L.hs, C - 1);
+            const int li = x - re * span;
+            jx = ((uint32_t)re << 20 | (uint32_t)li) + 1u;
+            cl.map_shared_rank(entry, re)[li] = 1;
+        }
+        jxA[i] = jx;
     }
-    cl.sync();  // every strip's exits are complete (and its parents dead)
+    cl.sync();  // every strip's exits and entry flags are complete (and its parents dead)
     // the exits one and two segments ahead
+    auto pixel = [&](uint32_t jx) { return (int)((jx - 1) >> 20) * span + (int)((jx - 1) & 0xFFFFFu); };
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         const int v = p0 + i;
-        const int e1 = (int)jxA[i] - 1;
+        const uint32_t j1 = jxA[i];
+        const int e1 = j1 ? pixel(j1) : -1;
         int e2 = -1;
-        if (e1 >= 0) {
-            const int re = min(row_of(a, e1) / L.hs, C - 1);
-            e2 = (int)cl.map_shared_rank(jxA, re)[e1 - re * span] - 1;
+        if (j1) {
+            const uint32_t j2 = cl.map_shared_rank(jxA, (int)((j1 - 1) >> 20))[(j1 - 1) & 0xFFFFFu];
+            e2 = j2 ? pixel(j2) : -1;
         }
         unsigned long long y = 0;
         if (e1 >= 0) y = (unsigned long long)(e1 + 1) | ((unsigned long long)(tile_bit(a, e1) >> 8) << 17);
@@ -449,8 +463,9 @@ __global__ void __launch_bounds__(1024) k_treeW(TreeArgs a) {
         reinterpret_cast<unsigned long long*>(seg + v)[1] = y;
     }
     // depth sums: acc(v) = vertices from v up to the root, summed along the
-    // chain of segment exits by pointer jumping (A -> B -> A ...); the A
-    // buffers are only read until the first cluster barrier below
+    // chain of segment exits by pointer jumping (A -> B -> A ...) over the
+    // entries (an entry's exit is an entry too); the A buffers of the other
+    // vertices keep their segment's count and exit for the last step
     int cur = 0;
     for (int pass = 0; pass < 32; ++pass) {
         uint32_t* ac = cur ? accB : accA;
@@ -459,12 +474,11 @@ __global__ void __launch_bounds__(1024) k_treeW(TreeArgs a) {
         uint32_t* jn = cur ? jxA : jxB;
         int any = 0;
         for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            if (!entry[i]) continue;
             const uint32_t j1 = jc[i];
             uint32_t c = ac[i], j2 = 0;
             if (j1) {
-                const int e = (int)j1 - 1;
-                const int re = min(row_of(a, e) / L.hs, C - 1);
-                const int li = e - re * span;
+                const int re = (int)((j1 - 1) >> 20), li = (int)((j1 - 1) & 0xFFFFFu);
                 c += cl.map_shared_rank(ac, re)[li];
                 j2 = cl.map_shared_rank(jc, re)[li];
             }
@@ -485,7 +499,15 @@ __global__ void __launch_bounds__(1024) k_treeW(TreeArgs a) {
     const uint32_t* af = cur ? accB : accA;
     unsigned long long ops = 0;
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        const uint32_t c = af[i];
+        uint32_t c;
+        if (entry[i]) {
+            c = af[i];
+        } else {
+            // a segment's count plus its exit's sum (A still holds both)
+            const uint32_t j1 = jxA[i];
+            c = accA[i];
+            if (j1) c += cl.map_shared_rank(af, (int)((j1 - 1) >> 20))[(j1 - 1) & 0xFFFFFu];
+        }
         if (c > 1) ops += (unsigned long long)(c - 1);  // unreached vertices hold 0, the root 1
     }
     for (int o = 16; o > 0; o >>= 1) ops += __shfl_down_sync(FULL, ops, o);
@@ -905,14 +927,24 @@ __global__ void __launch_bounds__(128, FILL_G_MINB) k_fill_l(TreeArgs a, int B) 
 // (the distance is symmetric). The array starts as UNREACH, and no launch
 // that writes anything but exact distances into it runs meanwhile, so a
 // known entry is exact and an entry written concurrently gets the same
-// value. Tiles of 64 x 64 entries in pairs (I, J), I <= J, through shared
-// memory: every entry is read once, only the missing ones are written.
+// value. Tiles of 64 x 64 entries in pairs (I, J), I <= J: each thread loads
+// four 16-byte chunks of each tile (rows t/16 + 16q, chunk t%16), keeps them
+// in registers and puts them in shared memory (row pitch 65) for the
+// transposed reads; a chunk is stored back only when one of its entries
+// changed. Tiles on the array's edge (or N not a multiple of 4) go entry by
+// entry.
 constexpr int MT = 64;
 
+__device__ __forceinline__ bool take_mirror(uint32_t& v, uint32_t m) {
+    const bool c = v == UNREACH && m != UNREACH;
+    if (c) v = m;
+    return c;
+}
+
 __global__ void __launch_bounds__(256) k_mirror(uint32_t* D, int N) {
-    __shared__ uint32_t sa[MT][MT + 1], sb[MT][MT + 1];
+    __shared__ uint32_t sa[MT * (MT + 1)], sb[MT * (MT + 1)];
     const long long T = (N + MT - 1) / MT, pairs = T * (T + 1) / 2;
-    const int tx = threadIdx.x & (MT - 1), ty = threadIdx.x / MT;
+    const int t = threadIdx.x, c4 = t & 15, rq = t >> 4;
     auto start = [T](long long i) { return i * T - i * (i - 1) / 2; };  // first pair of tile row i
     for (long long k = blockIdx.x; k < pairs; k += gridDim.x) {
         const double u = 2.0 * T + 1.0;
@@ -922,20 +954,60 @@ __global__ void __launch_bounds__(256) k_mirror(uint32_t* D, int N) {
         while (I + 1 < T && start(I + 1) <= k) ++I;
         const long long J = I + (k - start(I));
         const int i0 = (int)(I * MT), j0 = (int)(J * MT);
-#pragma unroll 4
+        const bool diag = I == J;
+        const uint32_t* mb = diag ? sa : sb;  // the mirror of tile (I, J)
+        if ((N & 3) == 0 && j0 + MT <= N) {
+            uint4 a[4], b[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = rq + 16 * q;
+                a[q] = __ldcs(reinterpret_cast<const uint4*>(D + (size_t)(i0 + r) * N + j0) + c4);
+                if (!diag) b[q] = __ldcs(reinterpret_cast<const uint4*>(D + (size_t)(j0 + r) * N + i0) + c4);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t* x = sa + (rq + 16 * q) * (MT + 1) + 4 * c4;
+                x[0] = a[q].x; x[1] = a[q].y; x[2] = a[q].z; x[3] = a[q].w;
+                if (!diag) {
+                    uint32_t* y = sb + (rq + 16 * q) * (MT + 1) + 4 * c4;
+                    y[0] = b[q].x; y[1] = b[q].y; y[2] = b[q].z; y[3] = b[q].w;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = rq + 16 * q;
+                const uint32_t* m = mb + 4 * c4 * (MT + 1) + r;  // column r of the mirror, rows 4 c4 ..
+                bool ch = take_mirror(a[q].x, m[0]);
+                ch |= take_mirror(a[q].y, m[MT + 1]);
+                ch |= take_mirror(a[q].z, m[2 * (MT + 1)]);
+                ch |= take_mirror(a[q].w, m[3 * (MT + 1)]);
+                if (ch) *(reinterpret_cast<uint4*>(D + (size_t)(i0 + r) * N + j0) + c4) = a[q];
+                if (!diag) {
+                    const uint32_t* n = sa + 4 * c4 * (MT + 1) + r;
+                    bool cb = take_mirror(b[q].x, n[0]);
+                    cb |= take_mirror(b[q].y, n[MT + 1]);
+                    cb |= take_mirror(b[q].z, n[2 * (MT + 1)]);
+                    cb |= take_mirror(b[q].w, n[3 * (MT + 1)]);
+                    if (cb) *(reinterpret_cast<uint4*>(D + (size_t)(j0 + r) * N + i0) + c4) = b[q];
+                }
+            }
+            __syncthreads();
+            continue;
+        }
+        const int tx = t & (MT - 1), ty = t / MT;
         for (int r = ty; r < MT; r += 256 / MT) {
             const int i = i0 + r, j = j0 + tx, i2 = j0 + r, j2 = i0 + tx;
-            sa[r][tx] = (i < N && j < N) ? __ldcs(D + (size_t)i * N + j) : UNREACH;
-            sb[r][tx] = (I != J && i2 < N && j2 < N) ? __ldcs(D + (size_t)i2 * N + j2) : UNREACH;
+            sa[r * (MT + 1) + tx] = (i < N && j < N) ? __ldcs(D + (size_t)i * N + j) : UNREACH;
+            sb[r * (MT + 1) + tx] = (!diag && i2 < N && j2 < N) ? __ldcs(D + (size_t)i2 * N + j2) : UNREACH;
         }
         __syncthreads();
-        const uint32_t (*mb)[MT + 1] = I != J ? sb : sa;  // the mirror of tile (I, J)
-#pragma unroll 4
         for (int r = ty; r < MT; r += 256 / MT) {
             const int i = i0 + r, j = j0 + tx, i2 = j0 + r, j2 = i0 + tx;
-            if (i < N && j < N && sa[r][tx] == UNREACH && mb[tx][r] != UNREACH) D[(size_t)i * N + j] = mb[tx][r];
-            if (I != J && i2 < N && j2 < N && sb[r][tx] == UNREACH && sa[tx][r] != UNREACH)
-                D[(size_t)i2 * N + j2] = sa[tx][r];
+            uint32_t v = sa[r * (MT + 1) + tx];
+            if (i < N && j < N && take_mirror(v, mb[tx * (MT + 1) + r])) D[(size_t)i * N + j] = v;
+            uint32_t w = sb[r * (MT + 1) + tx];
+            if (!diag && i2 < N && j2 < N && take_mirror(w, sa[tx * (MT + 1) + r])) D[(size_t)i2 * N + j2] = w;
         }
         __syncthreads();
     }
@@ -1072,7 +1144,7 @@ cudaError_t launch_depths(const TreeArgs& a, int B, cudaStream_t st) {
 
 cudaError_t launch_mirror(uint32_t* D, int N, cudaStream_t st) {
     const long long T = (N + MT - 1) / MT, pairs = T * (T + 1) / 2;
-    const long long grid = pairs < 152 * 6 ? pairs : 152 * 6;
+    const long long grid = pairs < 152 * 4 ? pairs : 152 * 4;
     k_mirror<<<(unsigned)grid, 256, 0, st>>>(D, N);
     return cudaGetLastError();
 }
