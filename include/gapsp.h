@@ -337,7 +337,7 @@ gapsp_status gapsp_rows_noalloc(const uint8_t *img, int H, int W, int conn, gaps
  * Autotuner for the launch parameters of one image's fill. The paper has no
  * counterpart: its method is the same for every choice, and D is too; only
  * the time and the counts of B > 1 change. Measures, on the image given, a
- * fill in `order` for every candidate of B in {16, 32, 64, 128, 256}, lookahead on
+ * fill in `order` for every candidate of B in {16, 32, ..., 1024}, lookahead on
  * (0) or off (-1) and the tree fill with global marks (fill_rows 0) or rows
  * of marks staged in shared memory (8), and for B >= 128 also the one-sided
  * first round (fill_rows -2), and returns in *best the options

@@ -2,9 +2,9 @@
 // them (declared in include/gapsp.h).
 //
 // The candidates are the parameters that shape the work on the GPU without
-// changing D: sources per round B in {16, 32, 64, 128, 256} (how many trees a
-// round builds and fills: wider rounds make the chain of rounds shorter and
-// cost more propagations),
+// changing D: sources per round B in {16, ..., 1024} (how many trees a round
+// builds and fills: wider rounds make the chain of rounds shorter and cost
+// more propagations),
 // whether rows are computed ahead (the lookahead launches), and how the tree
 // fill claims its pairs (marks in global memory, or rows of marks staged in
 // shared memory; with B >= 128 also the first round written one-sided and
@@ -118,7 +118,7 @@ extern "C" gapsp_status gapsp_tune(const uint8_t* img, const uint8_t* mask, int 
             cudaStreamDestroy(st);
             return GAPSP_E_NOMEM;
         }
-        const int Bs[] = {16, 32, 64, 128, 256};
+        const int Bs[] = {16, 32, 64, 128, 256, 512, 1024};
         const int looks[] = {0, -1};
         const int fills[] = {0, 8, -2};
         c.ms = -1.0;

@@ -29,6 +29,8 @@ WORKLOADS = {
     "steps256": lambda: synth.steps_256(0),
     # the benchmark's tuned configuration of the same image (B = 256)
     "steps256_B256": lambda: _with_B(synth.steps_256(0), 256),
+    # and with B = 512, where the first round's sources cover every pair
+    "steps256_B512": lambda: _with_B(synth.steps_256(0), 512),
     "mask256": lambda: synth.mask_256(0),
     # just above 16384 pixels, width not a multiple of 4: the code paths of
     # the larger images at a size the oracle simulates in minutes

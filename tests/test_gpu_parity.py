@@ -405,11 +405,12 @@ def _with_B(w, B):
                                                          ("minfill", "naive", "spiral", "extrema", "repulsion")] +
                          [("mask256", synth.mask_256, "minfill", 0),
                           ("steps256_B256", lambda seed: _with_B(synth.steps_256(seed), 256), "minfill", 0),
-                          ("steps256_B256", lambda seed: _with_B(synth.steps_256(seed), 256), "minfill", -2)])
+                          ("steps256_B256", lambda seed: _with_B(synth.steps_256(seed), 256), "minfill", -2),
+                          ("steps256_B512", lambda seed: _with_B(synth.steps_256(seed), 512), "minfill", -2)])
 def test_full_size_256(gp, name, factory, order, fill_rows):
-    """256x256, 8-connected, B = 32 (the benchmark's workload, every order;
-    and the obstacle mask), and B = 256 with the default fill and with the
-    one-sided first round: the counts against the oracle's stored
+    """256x256, 8-connected, B = 32 (every order; and the obstacle mask),
+    B = 256 with the default fill and with the one-sided first round, and
+    B = 512 (one round covers every pair): the counts against the oracle's stored
     simulation, sampled rows and columns of D against Dijkstra, and the
     whole array certified."""
     import torch
@@ -512,7 +513,7 @@ def test_tune_picks_a_candidate_and_caches(gp, tmp_path):
     img = synth.scaled_blobs(40, 44, 8, seed=3).img
     cache = tmp_path / "tune.txt"
     t = gp.tune(img, conn=8, cache=cache)
-    assert t["B"] in (16, 32, 64, 128, 256) and t["lookahead"] in (0, -1) and t["fill_rows"] in (0, 8, -2)
+    assert t["B"] in (16, 32, 64, 128, 256, 512, 1024) and t["lookahead"] in (0, -1) and t["fill_rows"] in (0, 8, -2)
     assert t["ms"] > 0
     lines = cache.read_text().splitlines()
     assert len(lines) == 1 and lines[0].startswith("gapsp-tune-2 40 44 8 0 2 ")
