@@ -30,9 +30,11 @@ enum StatSlot {
     S_SLOTS = 8
 };
 
-// Marks: one 64-bit word per (row, 8x8 pixel tile). Bit (r%8)*8 + (c%8) of
-// word (r/8)*tiles_w + c/8 of row b says whether the pair {b, (r,c)} is
-// filled.
+// Marks: one 64-bit word per (row, 8x8 pixel tile), stored tile-major (the
+// words of one tile for all rows, then the next tile), so that the words of
+// neighbouring rows for the same tile are adjacent. Bit (r%8)*8 + (c%8) of
+// row b's word for tile (r/8)*tiles_w + c/8 says whether the pair
+// {b, (r,c)} is filled.
 
 // Programmatic dependent launch: a kernel launched after another on the
 // same stream with the programmatic-serialization attribute may start while

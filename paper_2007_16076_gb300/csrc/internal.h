@@ -104,7 +104,7 @@ struct TreeArgs {
                                 // the same for the next segment's exit (bits 27-53)
     int32_t* jmp;               // [2][B][N] scratch for the depth pointer jumping
     int32_t* acc;               // [2][B][N] scratch for the depth pointer jumping
-    unsigned long long* marks;  // [N][words]
+    unsigned long long* marks;  // [words][N]: tile t's word of row b at t * N + b
     uint32_t* cnt;              // [N]
     const uint32_t* cnt_base;   // [N] fill count at the start (1 + pairs no path joins)
     uint32_t* Dw;               // writable array for new pairs

@@ -610,8 +610,8 @@ __global__ void __launch_bounds__(256, 4) k_fill(TreeArgs a) {
     const int rs = fill_row_stride(words), cs = fill_chg_stride(words);
     uint8_t* chg = reinterpret_cast<uint8_t*>(srow + (size_t)a.rows_per_block * rs);
     for (int i = threadIdx.x; i < nu * words; i += blockDim.x) {
-        const int r = i / words, w = i - r * words;
-        srow[r * rs + w] = ld_cg64(a.marks + (size_t)s_rows[r] * words + w);
+        const int w = i / nu, r = i - w * nu;  // neighbouring threads: neighbouring rows, one tile
+        srow[r * rs + w] = ld_cg64(a.marks + (size_t)w * a.N + s_rows[r]);
         chg[r * cs + w] = 0;
     }
     __syncthreads();
@@ -665,7 +665,7 @@ __global__ void __launch_bounds__(256, 4) k_fill(TreeArgs a) {
                 for (int k = 0; k < 8; ++k) {
                     if (ap[k] < 0) continue;
                     const uint32_t val = db - dv[k];
-                    atomicOr(a.marks + (size_t)ap[k] * words + tb, bbit);
+                    atomicOr(a.marks + (size_t)tb * a.N + ap[k], bbit);
                     // streaming stores: D is far larger than L2, keep the
                     // trees and marks resident instead
                     __stcs(a.Dw + (size_t)ap[k] * a.N + b, val);
@@ -697,8 +697,8 @@ __global__ void __launch_bounds__(256, 4) k_fill(TreeArgs a) {
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nu * words; i += blockDim.x) {
-        const int r = i / words, w = i - r * words;
-        if (chg[r * cs + w]) atomicOr(a.marks + (size_t)s_rows[r] * words + w, srow[r * rs + w]);
+        const int w = i / nu, r = i - w * nu;
+        if (chg[r * cs + w]) atomicOr(a.marks + (size_t)w * a.N + s_rows[r], srow[r * rs + w]);
     }
 }
 
@@ -734,14 +734,14 @@ __global__ void __launch_bounds__(128, FILL_G_MINB) k_fill_g(TreeArgs a, int qua
     const uint32_t db = __ldg(a.D + srow + b);
     if (b == s || db == UNREACH) return;
     const ulonglong2* seg = a.seg + (size_t)j * a.N;
-    const uint32_t mrow = (uint32_t)b * (uint32_t)a.words;
+    unsigned long long* const mrow = a.marks + b;  // row b's word of tile t at mrow[t * N]
     const uint32_t gb = __ldg(a.pgeo + b);
     const int tb = (int)(gb >> 8);
     const unsigned long long bbit = 1ull << (gb & 63);
     auto take = [&](int t, unsigned long long m, unsigned long long w) {
         unsigned long long nb = m & ~w;
         if (!nb) return;
-        nb &= ~atomicOr(a.marks + mrow + t, nb);
+        nb &= ~atomicOr(mrow + (uint32_t)t * (uint32_t)a.N, nb);
         if (!nb) return;
         const int base = __ldg(a.tbase + t);
         while (nb) {
@@ -761,7 +761,7 @@ __global__ void __launch_bounds__(128, FILL_G_MINB) k_fill_g(TreeArgs a, int qua
             for (int k = 0; k < 4; ++k) {
                 if (ap[k] < 0) continue;
                 const uint32_t val = db - dv[k];
-                atomicOr(a.marks + (uint32_t)ap[k] * (uint32_t)a.words + tb, bbit);
+                atomicOr(a.marks + (uint32_t)tb * (uint32_t)a.N + ap[k], bbit);
                 __stcs(a.Dw + (uint32_t)ap[k] * (uint32_t)a.N + b, val);
                 __stcs(a.Dw + brow + ap[k], val);
             }
@@ -770,7 +770,7 @@ __global__ void __launch_bounds__(128, FILL_G_MINB) k_fill_g(TreeArgs a, int qua
     ulonglong2 g = __ldg(seg + b);
     unsigned long long m = g.x & ~bbit;  // b's ancestors inside b's tile
     int t = tb;
-    unsigned long long w = ld_cg64(a.marks + mrow + t);
+    unsigned long long w = ld_cg64(mrow + (uint32_t)t * (uint32_t)a.N);
     for (int guard = 0; guard <= a.N; ++guard) {
         const unsigned long long y = g.y;
         const int e1 = (int)(y & 0x1FFFFu) - 1, t1 = (int)((y >> 17) & 0x3FFu);
@@ -779,11 +779,11 @@ __global__ void __launch_bounds__(128, FILL_G_MINB) k_fill_g(TreeArgs a, int qua
         ulonglong2 g2 = make_ulonglong2(0ull, 0ull);
         if (e1 >= 0) {
             m1 = __ldg(reinterpret_cast<const unsigned long long*>(seg + e1));
-            w1 = ld_cg64(a.marks + mrow + t1);
+            w1 = ld_cg64(mrow + (uint32_t)t1 * (uint32_t)a.N);
         }
         if (e2 >= 0) {
             g2 = __ldg(seg + e2);
-            w2 = ld_cg64(a.marks + mrow + t2);
+            w2 = ld_cg64(mrow + (uint32_t)t2 * (uint32_t)a.N);
         }
         take(t, m, w);
         if (e1 < 0) break;
@@ -837,7 +837,8 @@ __global__ void __launch_bounds__(128, FILL_G_MINB) k_fill_l(TreeArgs a, int B) 
         on = db != UNREACH;
     }
     if (!__any_sync(FULL, on)) return;
-    const uint32_t brow = (uint32_t)b * (uint32_t)a.N, mrow = (uint32_t)b * (uint32_t)a.words;
+    const uint32_t brow = (uint32_t)b * (uint32_t)a.N;
+    unsigned long long* const mrow = a.marks + b;  // row b's word of tile t at mrow[t * N]
     const int mshift = q * 32;
     const ulonglong2* seg = a.seg + (size_t)j * a.N;
     // the lane's current segment: tile t, ancestor bits m, row b's mark word
@@ -850,7 +851,7 @@ __global__ void __launch_bounds__(128, FILL_G_MINB) k_fill_l(TreeArgs a, int B) 
         const ulonglong2 g = __ldg(seg + b);
         m = g.x & ~(1ull << (mshift + lane));
         y = g.y;
-        w = ld_cg64(a.marks + mrow + t0);
+        w = ld_cg64(mrow + (uint32_t)t0 * (uint32_t)a.N);
         key = 0xFFFFFFFFu;
     }
     // the segment after it, fetched one step ahead
@@ -865,7 +866,7 @@ __global__ void __launch_bounds__(128, FILL_G_MINB) k_fill_l(TreeArgs a, int B) 
             const ulonglong2 g = __ldg(seg + e1);
             mn = g.x;
             yn = g.y;
-            wn = ld_cg64(a.marks + mrow + tn);
+            wn = ld_cg64(mrow + (uint32_t)tn * (uint32_t)a.N);
             keyn = __ldg(a.D + srow + e1) + 1;
         }
     };
@@ -879,7 +880,7 @@ __global__ void __launch_bounds__(128, FILL_G_MINB) k_fill_l(TreeArgs a, int B) 
         const int tl = __shfl_sync(FULL, t, lead);
         const bool go = key == K && t == tl;
         unsigned long long nb = go ? m & ~w : 0ull;
-        if (nb) nb &= ~atomicOr(a.marks + mrow + t, nb);
+        if (nb) nb &= ~atomicOr(mrow + (uint32_t)t * (uint32_t)a.N, nb);
         unsigned long long U = warp_or64(nb);
         if (U) {
             const int base = __ldg(a.tbase + tl);
@@ -907,7 +908,7 @@ __global__ void __launch_bounds__(128, FILL_G_MINB) k_fill_l(TreeArgs a, int B) 
                         __stcs(a.Dw + (uint32_t)ap[k] * (uint32_t)a.N + b, val);
                     }
                     if (lane == 0)
-                        atomicOr(a.marks + (uint32_t)ap[k] * (uint32_t)a.words + t0, (unsigned long long)bal << mshift);
+                        atomicOr(a.marks + (uint32_t)t0 * (uint32_t)a.N + ap[k], (unsigned long long)bal << mshift);
                 }
             }
         }
@@ -1015,8 +1016,10 @@ __global__ void __launch_bounds__(256) k_mirror(uint32_t* D, int N) {
 
 // Fill counts of the rows still open: cnt(x) = cnt at the start + the
 // number of marked pairs of row x (both bits of a pair are set, so row x
-// holds every filled pair {x, y}). One warp per row; rows already filled
-// (cnt = N) cannot change. Recounting every open row costs one streaming
+// holds every filled pair {x, y}). A block takes 32 consecutive rows, its
+// eight warps an eighth of the tiles each: a warp reads the same tile's
+// words of the 32 rows at once. Rows already filled (cnt = N) cannot
+// change. Recounting every open row costs one streaming
 // read of its marks, where flagging the rows that changed cost the fill a
 // store per new pair. The increments are summed into S_NEW, which thus
 // counts every new pair twice.
@@ -1025,15 +1028,24 @@ __global__ void k_recount(TreeArgs a) {
     pdl_wait();
     if (threadIdx.x == 0) s_sum = 0;
     __syncthreads();
-    const int x = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (x < a.N && __ldcg(a.cnt + x) < (uint32_t)a.N) {
-        const unsigned long long* row = a.marks + (size_t)x * a.words;
-        unsigned c = 0;
-        for (int w = lane; w < a.words; w += 32) c += __popcll(__ldcg(row + w));
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(FULL, c, o);
-        if (lane == 0) {
-            const uint32_t nc = a.cnt_base[x] + c;
+    __shared__ unsigned s_part[8][32];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int x = blockIdx.x * 32 + lane;
+    const bool open = x < a.N && __ldcg(a.cnt + x) < (uint32_t)a.N;
+    unsigned c = 0;
+    if (__syncthreads_or(open)) {
+        if (open) {
+            const unsigned long long* col = a.marks + x;
+#pragma unroll 4
+            for (int w = wp; w < a.words; w += 8) c += __popcll(__ldcg(col + (size_t)w * a.N));
+        }
+        s_part[wp][lane] = c;
+        __syncthreads();
+        if (wp == 0 && open) {
+            unsigned t = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) t += s_part[k][lane];
+            const uint32_t nc = a.cnt_base[x] + t;
             atomicAdd(&s_sum, (unsigned long long)(nc - a.cnt[x]));
             a.cnt[x] = nc;
         }
@@ -1074,7 +1086,7 @@ cudaError_t launch_ex(void (*kern)(KArgs...), int grid, int block, size_t smem, 
 }
 
 cudaError_t launch_recount(const TreeArgs& a, cudaStream_t st, bool pdl) {
-    return launch_ex(k_recount, (a.N + 7) / 8, 256, 0, st, pdl, 1, a);
+    return launch_ex(k_recount, (a.N + 31) / 32, 256, 0, st, pdl, 1, a);
 }
 
 cudaError_t launch_tree(const TreeArgs& a, int B, cudaStream_t st, bool pdl) {
