@@ -140,12 +140,6 @@ class Clocks:
 # the dominant kernel per workload, from an ncu capture, with the launch it
 # came from; None when no capture of the kernel as it stands exists.
 DRAM_BYTES = {
-    # k_fill_g at 256x256 step edges with the tuned options (B = 256, one-sided
-    # first round), the launch of round 8 (ncu, one pass, cold caches, commit
-    # b324177): 2.490 GB read + 0.590 GB written, for 41422102 new pairs (8 B
-    # each) in that round
-    "steps256": {"kernel": "k_fill", "bytes": 3080.22e6, "launch": "round 8",
-                 "launch_algorithmic_bytes": 331.4e6},
 }
 
 THROTTLE = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
@@ -499,6 +493,13 @@ def _extras(a, gp, torch, w, im, D, flush, stream) -> dict:
         ms, (_, so) = _timed_call(torch, stream, flush, lambda: i32.all_pairs("minfill", out=D))
     ex["minfill_B32_default_options"] = {"ms": ms, "entries_per_s": entries / (ms / 1e3),
                                          "propagations": so["propagations"], "rounds": so["rounds"]}
+    # several rounds at B = 256 (one-sided first round), for the step-edge
+    # image where B = 512 fills everything in one round
+    with _image(gp, w, stream, B=256, fill_rows=-2) as i256:
+        i256.all_pairs("minfill", out=D)
+        ms, (_, so) = _timed_call(torch, stream, flush, lambda: i256.all_pairs("minfill", out=D))
+    ex["minfill_B256"] = {"ms": ms, "entries_per_s": entries / (ms / 1e3),
+                          "propagations": so["propagations"], "rounds": so["rounds"]}
     for order in ("naive", "spiral", "extrema", "repulsion"):
         ms, (_, so) = _timed_call(torch, stream, flush, lambda: im.all_pairs(order, out=D))
         ex[order] = {"ms": ms, "entries_per_s": entries / (ms / 1e3),

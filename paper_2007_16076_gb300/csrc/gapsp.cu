@@ -1265,9 +1265,9 @@ gapsp_status gapsp_all_pairs(gapsp_handle* h, gapsp_order order, uint32_t* D, ga
     r.s = h->st;
     h->cancel.store(0);
     gapsp_status gs = fill_begin(r);
-    if (gs == GAPSP_OK) gs = fill_enqueue(r, kChunk);
+    if (gs == GAPSP_OK) gs = fill_enqueue(r, next_chunk(r));
     while (gs == GAPSP_OK && !r.finished) {
-        if ((gs = fill_enqueue(r, kChunk)) == GAPSP_OK) gs = fill_poll(r);
+        if ((gs = fill_enqueue(r, next_chunk(r))) == GAPSP_OK) gs = fill_poll(r);
     }
     if (gs == GAPSP_OK) gs = fill_finish(r, st);
     if (gs != GAPSP_OK) fill_drain(r);

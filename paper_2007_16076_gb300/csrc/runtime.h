@@ -202,6 +202,10 @@ struct FillRun {
 // done cost little, large enough that the host stays ahead of the device.
 constexpr int kChunk = 8;
 static_assert(kChunk % kDepRing == 0, "a chunk of rounds is a whole number of turns of the depth ring");
+// Rounds of the next chunk of a fill that is not captured in a graph: 1, 1,
+// 2, 4, then kChunk, so that a fill done in its first rounds (a round with
+// many sources can fill every pair) queues few rounds past its end.
+inline int next_chunk(const FillRun& r) { return r.chunks < 2 ? 1 : r.chunks < 4 ? 1 << (r.chunks - 1) : kChunk; }
 
 // Set-up of a fill: checks D, allocates what is missing, initialises the
 // state on r.s, runs the extrema pre-pass of the ranked orders.

@@ -165,8 +165,8 @@ void gapsp_server::begin(Request* r) {
     if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
         f.sm_share = std::max(1, sms / (int)busy.size());  // the slots share the device
     cudaGetLastError();
-    if ((gs = fill_begin(f)) == GAPSP_OK && (gs = fill_enqueue(f, kChunk)) == GAPSP_OK)
-        gs = fill_enqueue(f, kChunk);
+    if ((gs = fill_begin(f)) == GAPSP_OK && (gs = fill_enqueue(f, next_chunk(f))) == GAPSP_OK)
+        gs = fill_enqueue(f, next_chunk(f));
     if (gs != GAPSP_OK) {
         fill_drain(f);
         return finish(r, gs);
@@ -195,7 +195,7 @@ bool gapsp_server::advance(Request* r) {
         finish(r, gs);
         return true;
     }
-    if (gs == GAPSP_OK) gs = fill_enqueue(f, kChunk);
+    if (gs == GAPSP_OK) gs = fill_enqueue(f, next_chunk(f));
     if (gs != GAPSP_OK) {
         fill_drain(f);
         finish(r, gs);
