@@ -820,8 +820,11 @@ __global__ void __launch_bounds__(128, FILL_G_MINB) k_fill_l(TreeArgs a, int B) 
     const int nsel = *a.nsel;
     if (nsel == 0) return;
     const int lane = threadIdx.x & 31;
-    const long long warp = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int half = (int)(warp / B), j = (int)(warp - (long long)half * B);
+    // a block: one tree, four neighbouring half tiles (whose paths share
+    // records and source-row entries through L1); blocks of the same half
+    // tiles and all trees follow each other
+    const int hg = blockIdx.x / B, j = blockIdx.x - hg * B;
+    const int half = hg * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int t0 = half >> 1, q = half & 1;
     if (j >= nsel || t0 >= a.words) return;  // uniform over the warp
     const int tr = t0 / a.tiles_w, tc = t0 - tr * a.tiles_w;
@@ -1164,8 +1167,8 @@ cudaError_t launch_mirror(uint32_t* D, int N, cudaStream_t st) {
 cudaError_t launch_fill(const TreeArgs& a, int B, cudaStream_t st, bool pdl) {
     if (a.rows_per_block < 0) {
         // walks in lockstep: one warp per half tile and tree
-        const long long warps = 2LL * a.words * B;
-        return launch_ex(k_fill_l, (int)((warps + 3) / 4), 128, 0, st, pdl, 1, a, B);
+        const long long groups = (2LL * a.words + 3) / 4;
+        return launch_ex(k_fill_l, (int)(groups * B), 128, 0, st, pdl, 1, a, B);
     }
     if (a.rows_per_block == 0) {
         // marks claimed in global memory: one warp per 8 rows x 4 trees
