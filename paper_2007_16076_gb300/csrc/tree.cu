@@ -804,12 +804,13 @@ __device__ __forceinline__ unsigned long long warp_or64(unsigned long long v) {
 // The same fill with the walks of one warp in lockstep. A warp owns one tree
 // and the 32 pixels of half an 8x8 tile (4 rows of 8: lane l is bit
 // 32q + l of the tile's mark word), whose paths to the root soon merge. The
-// walks advance one segment at a time, farthest from the root first: each
-// step takes the lanes whose segment entry has the largest d(s, .) (and the
-// leader's tile), so lanes whose paths have merged reach the shared segments
-// together (d(s, .) falls strictly along a path) and take them in the same
-// instructions. The new pairs of a step are then written per ancestor a for
-// all its lanes at once: the column stores D[a][b] of the lanes form whole
+// walks advance one segment at a time, and a lane advances only while its
+// segment entry is farther from the root than every lane's next entry
+// (d(s, .) falls strictly along a path): a lane whose entry another lane
+// will still reach waits there for it, so lanes whose paths merge take the
+// shared segments in the same instructions, while lanes on separate paths
+// advance side by side. The new pairs of a step are then written, tile by
+// tile, per ancestor a for all its lanes at once: the column stores D[a][b] of the lanes form whole
 // runs of 8 entries, and the mirror bits (row a, columns b) one 64-bit OR,
 // the lanes' ballot shifted to the half tile. The first segment (inside the
 // lanes' own tile) is taken by all lanes together. With one_side set, only
@@ -877,16 +878,23 @@ __global__ void __launch_bounds__(128, FILL_G_MINB) k_fill_l(TreeArgs a, int B) 
     // every step advances at least one lane by one segment, and the keys of a
     // lane fall strictly: at most 32 N steps
     for (long long guard = 0; guard <= 32LL * a.N; ++guard) {
-        const uint32_t K = __reduce_max_sync(FULL, key);
-        if (K == 0) break;
-        const int lead = __ffs(__ballot_sync(FULL, key == K)) - 1;
-        const int tl = __shfl_sync(FULL, t, lead);
-        const bool go = key == K && t == tl;
+        if (!__any_sync(FULL, key != 0)) break;
+        // a lane goes when its entry is farther from the root than every
+        // lane's next entry: a lane that another one will still join waits
+        // for it (the other's next entry is at or before its own), and lanes
+        // on separate paths go side by side
+        const uint32_t T = __reduce_max_sync(FULL, keyn);
+        const bool go = key != 0 && key > T;
         unsigned long long nb = go ? m & ~w : 0ull;
         if (nb) nb &= ~atomicOr(mrow + (uint32_t)t * (uint32_t)a.N, nb);
-        unsigned long long U = warp_or64(nb);
-        if (U) {
-            const int base = __ldg(a.tbase + tl);
+        // the new pairs, tile by tile: the union of the lanes' new bits once
+        for (unsigned gl = __ballot_sync(FULL, nb != 0); gl;) {
+            const int tg = __shfl_sync(FULL, t, __ffs(gl) - 1);
+            const bool in = nb != 0 && t == tg;
+            gl &= ~__ballot_sync(FULL, in);
+            const unsigned long long mine = in ? nb : 0ull;
+            unsigned long long U = warp_or64(mine);
+            const int base = __ldg(a.tbase + tg);
             while (U) {
                 int ap[4], bit[4];
                 uint32_t dv[4];
@@ -903,7 +911,7 @@ __global__ void __launch_bounds__(128, FILL_G_MINB) k_fill_l(TreeArgs a, int B) 
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     if (ap[k] < 0) continue;
-                    const bool has = (nb >> bit[k]) & 1;
+                    const bool has = (mine >> bit[k]) & 1;
                     const unsigned bal = __ballot_sync(FULL, has);
                     if (has) {
                         const uint32_t val = db - dv[k];
