@@ -100,11 +100,12 @@ typedef struct {
                           0 = marks claimed in global memory (the default);
                           1..32 = rows of marks staged in shared memory per block;
                           -1 = every round walks in lockstep, one warp per half
-                               tile and tree (slower; for comparison);
+                               tile and tree;
                           -2 = as 0, but the first round walks in lockstep and
                                writes one side of each pair, and one pass over D
                                mirrors it (pays when the first round fills most
-                               pairs: many sources per round, B >= 128) */
+                               pairs: many sources per round, B >= 128);
+                          -3 = as -1, with the first round as in -2 */
     int checked;       /* 1: certify every result before returning it (gapsp_certify on the
                           whole D or on the rows; about one more read of the array);
                           a result that fails returns GAPSP_E_CHECK. 0: off */
@@ -338,9 +339,9 @@ gapsp_status gapsp_rows_noalloc(const uint8_t *img, int H, int W, int conn, gaps
  * counterpart: its method is the same for every choice, and D is too; only
  * the time and the counts of B > 1 change. Measures, on the image given, a
  * fill in `order` for every candidate of B in {16, 32, ..., 1024}, lookahead on
- * (0) or off (-1) and the tree fill with global marks (fill_rows 0) or rows
- * of marks staged in shared memory (8), and for B >= 128 also the one-sided
- * first round (fill_rows -2), and returns in *best the options
+ * (0) or off (-1; only below B = 256, where the rounds leave multiprocessors
+ * free) and the tree fill variants (fill_rows 0 and -1; 8 for B <= 32; -2
+ * and -3 for B >= 128), and returns in *best the options
  * of *base (NULL: the defaults) with the fastest candidate's B, lookahead
  * and fill_rows; *best_ms (may be NULL) receives its device time.
  *   img, mask : as gapsp_create (host or device).

@@ -429,7 +429,7 @@ static gapsp_status create_handle(const uint8_t* img, int L, int H, int W, const
         return GAPSP_E_INVALID;
     if (o.B < 1 || o.B > 1024) return GAPSP_E_INVALID;
     if (o.sweep_phases < 0 || o.sweep_phases > 4 || o.sweep_phases == 3) return GAPSP_E_INVALID;
-    if (o.fill_rows < -2 || o.fill_rows > 32) return GAPSP_E_INVALID;
+    if (o.fill_rows < -3 || o.fill_rows > 32) return GAPSP_E_INVALID;
     if (o.prop_blocks != 0 && o.prop_blocks != 1 && o.prop_blocks != 2 && o.prop_blocks != 4)
         return GAPSP_E_INVALID;
     if (o.lookahead < -1 || o.lookahead > 1024) return GAPSP_E_INVALID;
@@ -718,7 +718,7 @@ gapsp_status fill_begin(FillRun& r) {
     // and when propagations start warm from it
     InitArgs ia{h->N, Dd, h->cnt, h->comp, h->comp_size, h->kind == GAPSP_MASK || h->warm};
     // (the mirror pass tells the missing side of a pair by its UNREACH)
-    r.one_side_first = h->fill_rows == -2 && ia.full_init;
+    r.one_side_first = (h->fill_rows == -2 || h->fill_rows == -3) && ia.full_init;
     {
         ProfScope ps(h, K_INIT, s);
         CK(launch_init(ia, s));
@@ -812,7 +812,7 @@ gapsp_status fill_begin(FillRun& r) {
         if (h->fill_rows) ta.rows_per_block = h->fill_rows;
         if ((size_t)ta.rows_per_block * row_bytes > 200 * 1024) ta.rows_per_block = rpb < 1 ? 1 : rpb;
         if (h->fill_rows == 0 || h->fill_rows == -2) ta.rows_per_block = 0;  // marks claimed in global memory
-        if (h->fill_rows == -1) ta.rows_per_block = -1;                      // walks in lockstep
+        if (h->fill_rows == -1 || h->fill_rows == -3) ta.rows_per_block = -1;  // walks in lockstep
     }
     r.rounds = 0;
     r.finished = false;

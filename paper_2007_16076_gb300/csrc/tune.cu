@@ -5,11 +5,13 @@
 // changing D: sources per round B in {16, ..., 1024} (how many trees a round
 // builds and fills: wider rounds make the chain of rounds shorter and cost
 // more propagations),
-// whether rows are computed ahead (the lookahead launches), and how the tree
-// fill claims its pairs (marks in global memory, or rows of marks staged in
-// shared memory; with B >= 128 also the first round written one-sided and
-// mirrored, which only pays when that round fills most pairs). Each candidate fills the caller's image once after a
-// warm-up fill, timed with events on a stream of its own; the fastest wins.
+// whether rows are computed ahead (the lookahead launches), and the tree
+// fill variant: walks one lane at a time with marks in global memory (0) or
+// in lockstep (-1), rows of marks staged in shared memory (8, for B <= 32),
+// and for B >= 128 the first round written one-sided and mirrored (-2, -3),
+// which only pays when that round fills most pairs. Each candidate fills the
+// caller's image once after a warm-up fill, timed with events on a stream of
+// its own; the fastest wins.
 // Results are kept in a text cache, one line per key (H, W, conn, kind,
 // order, multiprocessor count), so that each shape is measured once.
 #include <cstdio>
@@ -120,12 +122,15 @@ extern "C" gapsp_status gapsp_tune(const uint8_t* img, const uint8_t* mask, int 
         }
         const int Bs[] = {16, 32, 64, 128, 256, 512, 1024};
         const int looks[] = {0, -1};
-        const int fills[] = {0, 8, -2};
+        const int fills[] = {0, -1, 8, -2, -3};
         c.ms = -1.0;
         for (int B : Bs)
             for (int la : looks)
                 for (int fr : fills) {
-                    if (fr == -2 && B < 128) continue;
+                    // staged rows only pay with few trees per round, the
+                    // one-sided first round only with many; from B = 256 on,
+                    // no multiprocessor is left for lookahead launches
+                    if ((fr == 8 && B > 32) || (fr <= -2 && B < 128) || (la == -1 && B >= 256)) continue;
                     gapsp_opts t = o;
                     t.B = B;
                     t.lookahead = la;

@@ -92,7 +92,7 @@ def test_invalid_arguments_rejected_without_gpu(lib_path):
     o.warm_start = 1  # 0 (on) or -1 (off) only
     assert lib.gapsp_create(img, 2, 2, None, ctypes.byref(o), ctypes.byref(h)) == 1
     o.warm_start = 0
-    for fr in (-3, 33):  # fill variants -2..32 only
+    for fr in (-4, 33):  # fill variants -3..32 only
         o.fill_rows = fr
         assert lib.gapsp_create(img, 2, 2, None, ctypes.byref(o), ctypes.byref(h)) == 1
     assert not h

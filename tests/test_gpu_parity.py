@@ -347,7 +347,7 @@ def test_full_size_blobs128(gp, order):
 # one value per lane where the width is not a multiple of 4)
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("fill_rows", [0, -1, -2, 1, 8])
+@pytest.mark.parametrize("fill_rows", [0, -1, -2, -3, 1, 8])
 @pytest.mark.parametrize("shape,conn,kind", [((29, 31), 8, "grey"), ((40, 24), 4, "mask"), ((136, 121), 8, "grey")])
 def test_fill_variants(gp, shape, conn, kind, fill_rows):
     """The tree fill with the marks claimed in global memory (fill_rows 0,
@@ -513,7 +513,7 @@ def test_tune_picks_a_candidate_and_caches(gp, tmp_path):
     img = synth.scaled_blobs(40, 44, 8, seed=3).img
     cache = tmp_path / "tune.txt"
     t = gp.tune(img, conn=8, cache=cache)
-    assert t["B"] in (16, 32, 64, 128, 256, 512, 1024) and t["lookahead"] in (0, -1) and t["fill_rows"] in (0, 8, -2)
+    assert t["B"] in (16, 32, 64, 128, 256, 512, 1024) and t["lookahead"] in (0, -1) and t["fill_rows"] in (0, 8, -1, -2, -3)
     assert t["ms"] > 0
     lines = cache.read_text().splitlines()
     assert len(lines) == 1 and lines[0].startswith("gapsp-tune-2 40 44 8 0 2 ")
