@@ -140,6 +140,12 @@ class Clocks:
 # the dominant kernel per workload, from an ncu capture, with the launch it
 # came from; None when no capture of the kernel as it stands exists.
 DRAM_BYTES = {
+    # k_fill_l, the one round of the 256x256 step-edge fill with the tuned
+    # options (B = 512, one-sided: 4 B per new pair), ncu one pass, cold
+    # caches, commit 01c95e1: 6.979 GB read + 9.273 GB written for 2147450880
+    # new pairs; the mirror pass after it: 17.275 + 8.623 GB in 5.17 ms
+    "steps256": {"kernel": "k_fill", "bytes": 16251.58e6, "launch": "round 0 (k_fill_l, one side)",
+                 "launch_algorithmic_bytes": 8589.80e6},
 }
 
 THROTTLE = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
@@ -677,12 +683,10 @@ def run_ours(a):
     prof = _profile(im, D, flush)
     roof = roofline(w, st, prof, ms_per_step, _peaks(), DRAM_BYTES.get(a.workload))
 
-    extras = {} if a.no_extras else _extras(a, gp, torch, w, im, D, flush, stream)
-
     # end to end through the C ABI with host buffers: create from a host image,
-    # fill into pinned host memory, destroy
-    del D
-    torch.cuda.empty_cache()
+    # fill into pinned host memory, destroy (before the side measurements,
+    # which leave the process's host and device allocators in another state:
+    # measured after them, the same calls took twice as long)
     host_D = torch.empty((N, N), dtype=torch.int32, pin_memory=True)
     host_img = np.ascontiguousarray(w.img if w.kind != "mask" else w.mask)
     hw = type(w)(w.name, np.ascontiguousarray(w.img), w.conn, w.kind,
@@ -702,6 +706,10 @@ def run_ours(a):
            "note": "gapsp_create(host image, the tuned options) + gapsp_all_pairs(pinned host D) + "
                    "gapsp_destroy"}
     del host_D
+
+    extras = {} if a.no_extras else _extras(a, gp, torch, w, im, D, flush, stream)
+    del D
+    torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1:
