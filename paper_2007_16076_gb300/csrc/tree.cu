@@ -815,6 +815,7 @@ __device__ __forceinline__ unsigned long long warp_or64(unsigned long long v) {
 // the lanes' ballot shifted to the half tile. The first segment (inside the
 // lanes' own tile) is taken by all lanes together. With one_side set, only
 // D[a][b] is written (a pass of k_mirror completes D[b][a] afterwards).
+template <bool ONE_SIDE>
 __global__ void __launch_bounds__(128, FILL_G_MINB) k_fill_l(TreeArgs a, int B) {
     pdl_wait();
     pdl_trigger();
@@ -841,10 +842,15 @@ __global__ void __launch_bounds__(128, FILL_G_MINB) k_fill_l(TreeArgs a, int B) 
         on = db != UNREACH;
     }
     if (!__any_sync(FULL, on)) return;
-    const uint32_t brow = (uint32_t)b * (uint32_t)a.N;
     unsigned long long* const mrow = a.marks + b;  // row b's word of tile t at mrow[t * N]
     const int mshift = q * 32;
     const ulonglong2* seg = a.seg + (size_t)j * a.N;
+    const uint32_t* const drow = a.D + srow;  // d(s, .)
+    uint32_t* const dcol = a.Dw + b;          // D[x][b] at dcol[x * N]
+    uint32_t* const drowb = a.Dw + (size_t)b * a.N;
+    // the mirror bits of this half tile: the low or high half of the words
+    // of tile t0 (row x's at mmir[2 x])
+    unsigned* const mmir = reinterpret_cast<unsigned*>(a.marks + (size_t)t0 * a.N) + q;
     // the lane's current segment: tile t, ancestor bits m, row b's mark word
     // w for t, the record's exits y and the key d(s, entry) + 1 (0: the walk
     // is over; all ones: the first segment)
@@ -893,33 +899,40 @@ __global__ void __launch_bounds__(128, FILL_G_MINB) k_fill_l(TreeArgs a, int B) 
             const bool in = nb != 0 && t == tg;
             gl &= ~__ballot_sync(FULL, in);
             const unsigned long long mine = in ? nb : 0ull;
-            unsigned long long U = warp_or64(mine);
+            const unsigned long long U = warp_or64(mine);
             const int base = __ldg(a.tbase + tg);
-            while (U) {
-                int ap[4], bit[4];
-                uint32_t dv[4];
+            // the bits of each half of the tile (tile rows 0-3, 4-7) with
+            // 32-bit operations
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    ap[k] = -1;
-                    if (U) {
-                        bit[k] = __ffsll((long long)U) - 1;
-                        U &= U - 1;
-                        ap[k] = base + (bit[k] >> 3) * a.W + (bit[k] & 7);
-                        dv[k] = __ldg(a.D + srow + ap[k]);
-                    }
-                }
+            for (int h = 0; h < 2; ++h) {
+                unsigned Uh = (unsigned)(U >> (32 * h));
+                const unsigned mh = (unsigned)(mine >> (32 * h));
+                const int bh = base + 4 * h * a.W;
+                while (Uh) {
+                    int ap[4], bit[4];
+                    uint32_t dv[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (ap[k] < 0) continue;
-                    const bool has = (mine >> bit[k]) & 1;
-                    const unsigned bal = __ballot_sync(FULL, has);
-                    if (has) {
-                        const uint32_t val = db - dv[k];
-                        if (!a.one_side) __stcs(a.Dw + brow + ap[k], val);
-                        __stcs(a.Dw + (uint32_t)ap[k] * (uint32_t)a.N + b, val);
+                    for (int k = 0; k < 4; ++k) {
+                        ap[k] = -1;
+                        if (Uh) {
+                            bit[k] = __ffs(Uh) - 1;
+                            Uh &= Uh - 1;
+                            ap[k] = bh + (bit[k] >> 3) * a.W + (bit[k] & 7);
+                            dv[k] = __ldg(drow + ap[k]);
+                        }
                     }
-                    if (lane == 0)
-                        atomicOr(a.marks + (uint32_t)t0 * (uint32_t)a.N + ap[k], (unsigned long long)bal << mshift);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (ap[k] < 0) continue;
+                        const bool has = (mh >> bit[k]) & 1u;
+                        const unsigned bal = __ballot_sync(FULL, has);
+                        if (has) {
+                            const uint32_t val = db - dv[k];
+                            if (!ONE_SIDE) __stcs(drowb + ap[k], val);
+                            __stcs(dcol + (uint32_t)ap[k] * (uint32_t)a.N, val);
+                        }
+                        if (lane == 0) atomicOr(mmir + 2 * ap[k], bal);
+                    }
                 }
             }
         }
@@ -1176,7 +1189,8 @@ cudaError_t launch_fill(const TreeArgs& a, int B, cudaStream_t st, bool pdl) {
     if (a.rows_per_block < 0) {
         // walks in lockstep: one warp per half tile and tree
         const long long groups = (2LL * a.words + 3) / 4;
-        return launch_ex(k_fill_l, (int)(groups * B), 128, 0, st, pdl, 1, a, B);
+        if (a.one_side) return launch_ex(k_fill_l<true>, (int)(groups * B), 128, 0, st, pdl, 1, a, B);
+        return launch_ex(k_fill_l<false>, (int)(groups * B), 128, 0, st, pdl, 1, a, B);
     }
     if (a.rows_per_block == 0) {
         // marks claimed in global memory: one warp per 8 rows x 4 trees
