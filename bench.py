@@ -381,9 +381,10 @@ def run_reference(a):
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * w.N * w.N / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
-            "config": {"workload": w.name, "H": w.H, "W": w.W, "N": w.N, "conn": w.conn, "B": w.B,
+            "config": {"workload": w.name.replace("-B32", ""), "H": w.H, "W": w.W, "N": w.N, "conn": w.conn,
                        "kind": w.kind, "order": "minfill",
-                       "note": "oracle Dijkstra rows, bounded sample per step"},
+                       "note": "oracle Dijkstra rows (the array itself; no sources per round), "
+                               "bounded sample per step"},
             "cpu_baseline": {**base, "value": v},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
