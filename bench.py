@@ -534,6 +534,13 @@ def _extras(a, gp, torch, w, im, D, flush, stream) -> dict:
             msr, _ = _timed_call(torch, stream, flush, lambda: io.rows(srco, out=Do))
             rec["naive_full_rows_ms"] = msr
             rec["naive_full_rows_entries_per_s"] = float(wo.N) ** 2 / (msr / 1e3)
+        # the same image with the autotuner's options
+        t_o = _tune(gp, wo)
+        with _image(gp, wo, stream, **t_o) as io:
+            io.all_pairs("minfill", out=Do)
+            ms, (_, so) = _timed_call(torch, stream, flush, lambda: io.all_pairs("minfill", out=Do))
+        rec["tuned"] = {**t_o, "ms": ms, "entries_per_s": float(wo.N) ** 2 / (ms / 1e3),
+                        "propagations": so["propagations"], "rounds": so["rounds"]}
         others[wo.name] = rec
     ex["other_workloads"] = others
     # batched form: 64 images of uneven sizes filled side by side, against

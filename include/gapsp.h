@@ -91,7 +91,7 @@ typedef enum {
 
 typedef struct {
     int conn;          /* 4 or 8 (0 = 8) */
-    gapsp_kind kind;   /* GAPSP_GREY or GAPSP_MASK */
+    gapsp_kind kind;   /* GAPSP_GREY, GAPSP_MASK or GAPSP_L1 (GAPSP_SUM: gapsp_create_channels) */
     int B;             /* sources per round, 1..1024 (0 = 32) */
     uint64_t seed;     /* seed of the spiral orders' draws */
     size_t mem_budget; /* bytes of device memory a call may use (0 = no limit) */
