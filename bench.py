@@ -142,9 +142,9 @@ class Clocks:
 DRAM_BYTES = {
     # k_fill_l, the one round of the 256x256 step-edge fill with the tuned
     # options (B = 512, one-sided: 4 B per new pair), ncu one pass, cold
-    # caches, commit 01c95e1: 6.979 GB read + 9.273 GB written for 2147450880
-    # new pairs; the mirror pass after it: 17.275 + 8.623 GB in 5.17 ms
-    "steps256": {"kernel": "k_fill", "bytes": 16251.58e6, "launch": "round 0 (k_fill_l, one side)",
+    # caches, commit fd8ee5c: 6.976 GB read + 9.271 GB written for 2147450880
+    # new pairs; the mirror pass after it: 17.274 + 8.624 GB in 5.19 ms
+    "steps256": {"kernel": "k_fill", "bytes": 16246.78e6, "launch": "round 0 (k_fill_l, one side)",
                  "launch_algorithmic_bytes": 8589.80e6},
 }
 
