@@ -449,11 +449,12 @@ def test_full_size_256(gp, name, factory, order, fill_rows):
 # Batched form: many images of uneven sizes side by side
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("fill_rows", [0, -2])
+@pytest.mark.parametrize("fill_rows", [0, -1, -2, -3])
 def test_all_pairs_batch_equals_alone(gp, fill_rows):
     """Each image of a batch gets the array and counts it gets alone
-    (images of uneven sizes, 4- and 8-connected, one mask; the default fill
-    and the one-sided first round, whose mirror pass is captured too)."""
+    (images of uneven sizes, 4- and 8-connected, one mask; every fill variant
+    that walks the marks in global memory, the one-sided first round's mirror
+    pass captured too)."""
     rng = np.random.default_rng(4)
     specs = []
     for k in range(6):
