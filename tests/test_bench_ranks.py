@@ -76,3 +76,33 @@ def test_clock_records_rejected():
         assert bench.clocks_rejected({**ok, "reasons": [r]})
     assert bench.clocks_rejected({**ok, "sm_mhz": 1200.0})  # locked well below the maximum
     assert not bench.clocks_rejected({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]})
+
+
+def test_roofline_arithmetic():
+    """The roofline entries from a fill's counts and per-kernel times: the
+    fill's algorithmic bytes (8 per new pair) over the fill and mirror-pass
+    time, the step's 4 N^2 bytes over the step time, the propagation's
+    relaxations over its launches, and the dominant kernel picked by time."""
+    import bench
+
+    class W:  # a 4 x 4 grey image, 8-connected
+        N, conn, kind, mask = 16, 8, "grey", None
+
+    st = {"new_pairs": 120, "propagations": 3, "prepass_propagations": 2}
+    peaks = {"hbm_gbs": 1000.0, "sm_max_mhz": 2000.0}
+    prof = {"_fills": 2, "fill": (4.0, 8), "mirror": (1.0, 2), "propagate": (1.0, 6), "lookahead": (0.0, 0),
+            "tree": (0.5, 8)}
+    r = bench.roofline(W, st, dict(prof), ms_per_step=10.0, peaks=peaks,
+                       dram={"kernel": "k_fill", "bytes": 1e4, "launch": "round 0"})
+    fill = r["kernels"]["fill"]
+    # 8 B x 120 pairs x 2 fills over (4 + 1) ms of fill and mirror
+    assert fill["achieved"] == pytest.approx(8 * 120 * 2 / 5e-3 / 1e9)
+    assert fill["frac"] == pytest.approx(fill["achieved"] / 1000.0)
+    assert fill["mirror_ms_per_fill"] == pytest.approx(0.5)
+    assert fill["traffic"] == 1e4 and fill["traffic_launch"] == "round 0"
+    assert r["step_hbm"]["achieved"] == pytest.approx(4 * 16 * 16 / 10e-3 / 1e9)
+    prop = r["kernels"]["propagate"]
+    # 2 conn relaxations per free pixel for each of the P + 2 propagations, both fills
+    assert prop["achieved"] == pytest.approx(2 * 8 * 16 * 5 * 2 / 1e-3 / 1e12)
+    assert r["kernel"] == "k_fill"  # 5 ms of fill against 1 ms of propagation
+    assert r["kernel_ms_per_fill"]["mirror"] == pytest.approx(0.5)
