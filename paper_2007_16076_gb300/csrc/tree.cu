@@ -810,11 +810,12 @@ __device__ __forceinline__ unsigned long long warp_or64(unsigned long long v) {
 // will still reach waits there for it, so lanes whose paths merge take the
 // shared segments in the same instructions, while lanes on separate paths
 // advance side by side. The new pairs of a step are then written, tile by
-// tile, per ancestor a for all its lanes at once: the column stores D[a][b] of the lanes form whole
-// runs of 8 entries, and the mirror bits (row a, columns b) one 64-bit OR,
-// the lanes' ballot shifted to the half tile. The first segment (inside the
-// lanes' own tile) is taken by all lanes together. With one_side set, only
-// D[a][b] is written (a pass of k_mirror completes D[b][a] afterwards).
+// tile, per ancestor a for all its lanes at once: the column stores D[a][b]
+// of the lanes form whole runs of 8 entries, and the mirror bits (row a,
+// columns b) one OR of the lanes' ballot into the half of the word that
+// holds the half tile. The first segment (inside the lanes' own tile) is
+// taken by all lanes together. With ONE_SIDE, only D[a][b] is written (a
+// pass of k_mirror completes D[b][a] afterwards).
 template <bool ONE_SIDE>
 __global__ void __launch_bounds__(128, FILL_G_MINB) k_fill_l(TreeArgs a, int B) {
     pdl_wait();
