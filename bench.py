@@ -53,8 +53,8 @@ def _args():
     return ap.parse_args()
 
 
-# name -> synth factory (every one 8-connected, B = 32)
-WORKLOADS = {"steps256": "steps_256", "mask256": "mask_256", "blobs128": "batched_128"}
+# name -> synth factory (8-connected, B = 32; the 32x32 image 4-connected, B = 1)
+WORKLOADS = {"steps256": "steps_256", "mask256": "mask_256", "blobs128": "batched_128", "plain32": "plain_32"}
 # smaller cases for profiling only (not measured among the side workloads)
 PROFILE_WORKLOADS = {"steps160": "steps_160"}
 
@@ -541,6 +541,13 @@ def _extras(a, gp, torch, w, im, D, flush, stream) -> dict:
             ms, (_, so) = _timed_call(torch, stream, flush, lambda: io.all_pairs("minfill", out=Do))
         rec["tuned"] = {**t_o, "ms": ms, "entries_per_s": float(wo.N) ** 2 / (ms / 1e3),
                         "propagations": so["propagations"], "rounds": so["rounds"]}
+        if wo.B == 1:
+            # the paper's own loop (one source per round) in its other orders
+            with _image(gp, wo, stream) as io:
+                for order in ("naive", "spiral"):
+                    io.all_pairs(order, out=Do)
+                    ms, (_, so) = _timed_call(torch, stream, flush, lambda: io.all_pairs(order, out=Do))
+                    rec[order] = {"ms": ms, "propagations": so["propagations"], "rounds": so["rounds"]}
         others[wo.name] = rec
     ex["other_workloads"] = others
     # batched form: 64 images of uneven sizes filled side by side, against
