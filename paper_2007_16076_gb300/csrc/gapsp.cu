@@ -817,6 +817,7 @@ gapsp_status fill_begin(FillRun& r) {
     r.rounds = 0;
     r.finished = false;
     r.chunks = r.polled = 0;
+    r.t_poll = host_seconds();
     CK(cudaEventCreateWithFlags(&r.chunk_ev[0], cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&r.chunk_ev[1], cudaEventDisableTiming));
     if (h->dep_exit) {
@@ -956,6 +957,7 @@ gapsp_status fill_enqueue(FillRun& r, int chunk, bool graph) {
         return GAPSP_OK;
     }
     const int par = r.chunks & 1;
+    r.chunk_rounds[par] = chunk;
     CK(cudaMemcpyAsync(h->h_done + par, h->done, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(h->h_done + 2 + par, h->status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaEventRecord(r.chunk_ev[par], s));
@@ -972,6 +974,11 @@ gapsp_status fill_poll(FillRun& r) {
     const int par = r.polled & 1;
     CK(cudaEventSynchronize(r.chunk_ev[par]));
     ++r.polled;
+    // the host time since the previous poll, per round of this chunk: the
+    // pace of the rounds, which sets the size of the next chunks
+    const double now = host_seconds();
+    if (r.chunk_rounds[par] > 0) r.round_s = (now - r.t_poll) / r.chunk_rounds[par];
+    r.t_poll = now;
     r.finished = h->h_done[par] != 0;
     const gapsp_status dev = status_from_word(h->h_done[2 + par]);
     if (dev != GAPSP_OK) return dev;

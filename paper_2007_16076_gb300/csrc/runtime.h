@@ -3,6 +3,7 @@
 // all-pairs fill in progress with the steps that advance it. Not part of
 // the public C ABI.
 #pragma once
+#include <chrono>
 #include <atomic>
 #include <vector>
 
@@ -145,6 +146,11 @@ size_t fill_state_bytes(const gapsp_handle* h);
 
 // One fill in progress: the state of gapsp_all_pairs between its steps, so
 // that several fills (one per image) can advance side by side.
+// Host clock in seconds (steady).
+inline double host_seconds() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
 struct FillRun {
     gapsp_handle* h = nullptr;
     gapsp_order order = GAPSP_MINFILL;
@@ -174,6 +180,9 @@ struct FillRun {
     // "done" flag it waits for, so that the device never waits for the host
     cudaEvent_t chunk_ev[2] = {nullptr, nullptr};
     int chunks = 0, polled = 0;
+    int chunk_rounds[2] = {0, 0};  // rounds of the chunks in flight, by parity
+    double t_poll = 0.0;           // host clock (s) at the previous poll (or the fill's start)
+    double round_s = 0.0;          // host time per round of the last chunk polled
     // depth sums (N <= 16384) on a third, low-priority stream: a round's
     // trees are handed over in a buffer of the round's parity, which the
     // tree launch two rounds later waits for
@@ -204,8 +213,13 @@ constexpr int kChunk = 8;
 static_assert(kChunk % kDepRing == 0, "a chunk of rounds is a whole number of turns of the depth ring");
 // Rounds of the next chunk of a fill that is not captured in a graph: 1, 1,
 // 2, 4, then kChunk, so that a fill done in its first rounds (a round with
-// many sources can fill every pair) queues few rounds past its end.
-inline int next_chunk(const FillRun& r) { return r.chunks < 2 ? 1 : r.chunks < 4 ? 1 << (r.chunks - 1) : kChunk; }
+// many sources can fill every pair) queues few rounds past its end; and at
+// most 2 once rounds take over half a millisecond (two such rounds keep the
+// device busy while the host polls, and fewer rounds run past the end).
+inline int next_chunk(const FillRun& r) {
+    const int grow = r.chunks < 2 ? 1 : r.chunks < 4 ? 1 << (r.chunks - 1) : kChunk;
+    return r.round_s > 0.5e-3 && grow > 2 ? 2 : grow;
+}
 
 // Set-up of a fill: checks D, allocates what is missing, initialises the
 // state on r.s, runs the extrema pre-pass of the ranked orders.
